@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Benchmark of the GMG-preconditioned FGMRES slab solve on one GB300 (or N replicas).
+
+Step = one flexible-GMRES solve (V(2,2) additive-Vanka V-cycle per iteration) of the dG(k)
+Q2/P1disc slab Newton system to 1e-8 relative residual, from x = 0, with the hierarchy assembled
+and factored once beforehand (assembly and factorisation times are reported under "setup").
+The headline `value` is seconds per solve with mixed-precision cell inverses (the faster of FP32
+and BF16 storage); the plain FP64 path is timed in the same run ("fp64_s").
+
+Prints ONE JSON line (rank 0). `--impl reference` times the CPU oracle (the plain FP64 reference
+implementation written from the paper) on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DEFAULT_WORKLOAD = "c2_2d_k2"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--precisions", default="f64,f32,bf16")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-child", default=None, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+def workload(name):
+    import synth
+
+    return synth.WORKLOADS[name]
+
+
+def describe(wl, sizes):
+    fine = sizes[-1]
+    return {"workload": f"{wl.name}: {wl.dim}D channel {'x'.join(map(str, wl.fine_cells))} fine cells "
+                        f"({'obstacle' if wl.obstacle_lo != wl.obstacle_hi else 'no obstacle'}), "
+                        f"{wl.n_levels} levels, Q2/P1disc x dG({wl.k})",
+            "dofs": fine["n_dofs"], "cells": fine["n_cells"], "n_local": fine["n_local"],
+            "levels": wl.n_levels, "rtol": None, "smoother": f"additive Vanka V({wl.nu1},{wl.nu2}) omega={wl.omega}",
+            "krylov": f"FGMRES({wl.restart})", "nu": wl.nu, "tau": wl.tau}
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU oracle leg (run in a spawned child process so that it never shares the CUDA context)
+# ---------------------------------------------------------------------------------------------
+def oracle_child(spec_path):
+    spec = json.load(open(spec_path))
+    import numpy as np
+
+    import synth
+    from oracle import solvers
+
+    wl = synth.WORKLOADS[spec["workload"]]
+    t0 = time.perf_counter()
+    H = solvers.Hierarchy(wl, synth.linearisation_point(wl))
+    setup = time.perf_counter() - t0
+    b = H.fine.dofs_from_lattice(synth.random_rhs(wl))
+    times, iters = [], []
+    for _ in range(spec["solves"]):
+        t0 = time.perf_counter()
+        x, info = H.solve(b, rtol=spec["rtol"], maxit=spec["maxit"])
+        times.append(time.perf_counter() - t0)
+        iters.append(info["iters"])
+    json.dump({"setup_s": setup, "solve_s": times, "iters": iters, "converged": bool(info["converged"])},
+              open(spec["out"], "w"))
+
+
+def run_oracle(wl_name, rtol, solves, maxit=1000, threads=1):
+    with tempfile.TemporaryDirectory() as td:
+        spec = {"workload": wl_name, "rtol": rtol, "solves": solves, "maxit": maxit, "out": os.path.join(td, "o.json")}
+        sp = os.path.join(td, "spec.json")
+        json.dump(spec, open(sp, "w"))
+        env = dict(os.environ)
+        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            env[v] = str(threads)
+        env["CUDA_VISIBLE_DEVICES"] = ""
+        p = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-child", sp], env=env,
+                           capture_output=True, text=True)
+        if p.returncode != 0:
+            raise RuntimeError("oracle child failed:\n" + p.stderr[-3000:])
+        return json.load(open(spec["out"]))
+
+
+# ---------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        self.path = tempfile.mktemp(suffix=".csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), hw=parts[5], hwt=parts[6], swt=parts[7],
+                                 pcap=parts[8]))
+            except ValueError:
+                continue
+        os.remove(self.path)
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"), ("swt", "sw_thermal_slowdown"),
+                              ("pcap", "sw_power_cap")):
+                if r[key].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows), "sm_max_mhz": max(r["smax"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return None
+
+
+# ---------------------------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------------------------
+def gpu_leg(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2107_10561_gb300 import Hierarchy, make_params
+    from paper_2107_10561_gb300 import build as _build
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    _build.build()
+    wl = workload(args.workload)
+    state = synth.linearisation_point(wl)
+    rhs_lat = synth.random_rhs(wl, seed_offset=rank)
+    results = {}
+    hs = {}
+    for prec in args.precisions.split(","):
+        p = make_params(wl.dim, wl.k, wl.n_levels, wl.coarse_cells, wl.length, wl.obstacle_lo, wl.obstacle_hi,
+                        wl.tau, wl.nu, wl.gamma1, wl.gamma2, prec, "additive", wl.omega, wl.nu1, wl.nu2)
+        h = Hierarchy(p)
+        idx = h.dof_lattice_index()
+        X = torch.from_numpy(np.ascontiguousarray(state.reshape(-1)[idx])).cuda()
+        b = torch.from_numpy(np.ascontiguousarray(rhs_lat.reshape(-1)[idx])).cuda()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        torch.cuda.synchronize()
+        e0.record()
+        h.assemble_jacobian(X)
+        e1.record()
+        h.factor_cells()
+        e2.record()
+        torch.cuda.synchronize()
+        setup = {"assemble_ms": e0.elapsed_time(e1), "factor_ms": e1.elapsed_time(e2)}
+        x = torch.zeros_like(b)
+        for _ in range(args.warmup):
+            x.zero_()
+            info = h.gmres_solve(b, x, rtol=args.rtol, restart=wl.restart)
+        hs[prec] = (h, b, x)
+        results[prec] = {"setup": setup, "iters": info["iters"], "rel_res_true": info["rel_res_true"]}
+    sizes = [hs[next(iter(hs))][0].sizes(g) for g in range(wl.n_levels)]
+
+    # timed region, every precision, K solves each
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    time.sleep(0.3)
+    stream = torch.cuda.current_stream()
+    for prec, (h, b, x) in hs.items():
+        h.profile_enable(True)
+        launches0 = Hierarchy.kernel_launches()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            x.zero_()
+            info = h.gmres_solve(b, x, rtol=args.rtol, restart=wl.restart)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / args.steps
+        if dist:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        r = results[prec]
+        r["ms_per_solve"] = ms
+        r["launches_per_step"] = (Hierarchy.kernel_launches() - launches0) / args.steps
+        r["iters_timed"] = info["iters"]
+        r["rel_res_true_timed"] = info["rel_res_true"]
+        r["kernels"] = {k: h.profile_read(k) for k in ("vanka_local", "jacobian_spmv", "vanka_combine", "transfer",
+                                                       "coarse", "krylov")}
+        h.profile_enable(False)
+    clocks = sampler.stop()
+
+    # end-to-end through the host-buffer entry point (H2D of b, D2H of x inside the timed region)
+    mixed = [p for p in results if p != "f64"]
+    head = min(mixed, key=lambda p: results[p]["ms_per_solve"]) if mixed else "f64"
+    h, b, x = hs[head]
+    bh = b.cpu().pin_memory()
+    xh = torch.zeros_like(bh).pin_memory()
+    h.gmres_solve_host(bh, xh, rtol=args.rtol, restart=wl.restart)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        h.gmres_solve_host(bh, xh, rtol=args.rtol, restart=wl.restart)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    return wl, sizes, results, head, clocks, e2e_s, dist
+
+
+def main():
+    args = parse()
+    if args.oracle_child:
+        oracle_child(args.oracle_child)
+        return
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        wl = workload(args.workload)
+        samples = max(1, args.steps)
+        o = run_oracle(args.workload, args.rtol, samples)
+        t = statistics.mean(o["solve_s"])
+        line = {"impl": "reference", "metric": "GMG-GMRES s to 1e-8 rel. res (mixed vs FP64, one GB300); Vanka sweep GB/s",
+                "value": t, "unit": "s", "n_gpus": args.gpus, "steps": samples, "warmup": 0,
+                "ms_per_step": 1e3 * t, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic",
+                "config": {"workload": args.workload, "rtol": args.rtol},
+                "cpu_baseline": {"value": t, "unit": "s", "cores": 1, "kind": "oracle",
+                                 "sample": f"{samples} full FP64 oracle FGMRES solves ({o['iters']} iterations) after "
+                                           f"an untimed {o['setup_s']:.1f} s oracle setup"},
+                "e2e": {"value": t, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    wl, sizes, results, head, clocks, e2e_s, dist = gpu_leg(args, rank, world, local_rank)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    pk = peaks()
+    hbm = pk["hbm_gbs"] if pk else 6800.0
+    r = results[head]
+    vl = r["kernels"]["vanka_local"]
+    achieved = vl["bytes"] / (vl["ms"] * 1e-3) / 1e9 if vl["ms"] > 0 else None
+    cfg = describe(wl, sizes)
+    cfg["rtol"] = args.rtol
+    inv_bytes = {"f64": 8, "f32": 4, "bf16": 2}
+    l2_note = (f"inputs larger than L2: finest J {sizes[-1]['nnz'] * 12 / 1e6:.0f} MB, finest inverses "
+               f"{sizes[-1]['n_cells'] * sizes[-1]['n_local'] ** 2 * inv_bytes[head] / 1e6:.0f} MB ({head})")
+    cfg["l2"] = l2_note
+    cfg["parallelism"] = f"replicas x{world}" if world > 1 else "single GPU"
+    line = {
+        "metric": "GMG-GMRES s to 1e-8 rel. res (mixed vs FP64, one GB300); Vanka sweep GB/s",
+        "value": r["ms_per_solve"] / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": r["ms_per_solve"], "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": f"f64 Krylov/SpMV/coarse + {head} cell inverses (f32 accumulate)" if head != "f64" else "f64",
+        "data": "synthetic", "config": cfg,
+        "fp64_s": results["f64"]["ms_per_solve"] / 1e3 if "f64" in results else None,
+        "speedup_vs_fp64": (results["f64"]["ms_per_solve"] / r["ms_per_solve"]) if "f64" in results else None,
+        "by_precision": {p: {"s_per_solve": v["ms_per_solve"] / 1e3, "iters": v["iters_timed"],
+                             "rel_res_true": v["rel_res_true_timed"], "setup_ms": v["setup"],
+                             "vanka_sweep_gbs": (v["kernels"]["vanka_local"]["bytes"] / (v["kernels"]["vanka_local"]["ms"] * 1e-3) / 1e9)
+                             if v["kernels"]["vanka_local"]["ms"] > 0 else None,
+                             "spmv_gbs": (v["kernels"]["jacobian_spmv"]["bytes"] / (v["kernels"]["jacobian_spmv"]["ms"] * 1e-3) / 1e9)
+                             if v["kernels"]["jacobian_spmv"]["ms"] > 0 else None,
+                             "kernel_ms_per_solve": {k: kv["ms"] / args.steps for k, kv in v["kernels"].items()}}
+                         for p, v in results.items()},
+        "gpu_launches": int(r["launches_per_step"] * args.steps),
+        "roofline": {"kernel": "k_vanka_local (y_T = J_T^{-1} t_T, all levels, timed solves)", "bound": "hbm",
+                     "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": (achieved / hbm) if achieved else None, "traffic": None,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if pk else "fallback 6800 GB/s",
+                     "bytes_per_launch": vl["bytes"] / max(vl["launches"], 1),
+                     "avg_launch_us": 1e3 * vl["ms"] / max(vl["launches"], 1)},
+        "clocks": clocks,
+        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": sizes[-1]["n_dofs"] * 8,
+                "d2h_bytes_per_step": sizes[-1]["n_dofs"] * 8,
+                "path": f"stm_gmres_solve_host ({head}), pinned host b and x"},
+    }
+    if not args.no_cpu_baseline and world == 1:
+        try:
+            o = run_oracle(args.workload, args.rtol, 1)
+            line["cpu_baseline"] = {"value": o["solve_s"][0], "unit": "s", "cores": 1, "kind": "oracle",
+                                    "sample": f"one full FP64 oracle FGMRES solve of the same workload "
+                                              f"({o['iters'][0]} iterations, single-threaded numpy/scipy) after an "
+                                              f"untimed {o['setup_s']:.1f} s oracle setup"}
+        except Exception as e:  # reported, never silently replaced
+            line["cpu_baseline"] = {"value": None, "error": str(e)[-300:]}
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,199 @@
+/*
+ * libstm — space-time multigrid for one dG(k) time slab of the incompressible Navier–Stokes
+ * equations, discretised with the inf-sup stable Q2/P1^disc pair, on one GPU.
+ *
+ * The library solves the Newton system J d = r of one time slab (Eq. linNewEq, Eq. LinSysMG of
+ * Anselmann & Bause, arXiv 2107.10561) by flexible GMRES right-preconditioned with one geometric
+ * multigrid V-cycle (Algorithm 1) whose smoother is the cell-based space-time Vanka smoother
+ * (Sec. 4.2, Eq. LocVanka, with the damping factor of Sec. 5.3) built from precomputed dense
+ * cell inverses on every level (Sec. 4.3).
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers named *_dev are device pointers (e.g. torch CUDA tensors), FP64, contiguous, owned
+ *    by the caller; *_host pointers are host memory owned by the caller. The library never keeps
+ *    a caller pointer after a call returns. Everything else (matrices, inverses, work vectors) is
+ *    allocated by stm_build_hierarchy and freed by stm_destroy.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream). Calls enqueue
+ *    work on it and return without synchronising, except where a comment says otherwise.
+ *  - Vector layout (Eq. totdofs): for each time node l = 0..k: velocity component 1 (R entries),
+ *    ..., component d (R entries), then the pressure (n_p entries per active cell, cell-major).
+ *    Q2 nodes are numbered lexicographically (x fastest) over the level's full node lattice with
+ *    the nodes of removed obstacle cells compressed out; active cells likewise.
+ *  - Cell-local layout (Eq. locdofs): per time node l, velocity component 1..d over the 3^d
+ *    cell nodes (x fastest), then the n_p Legendre pressure modes; n = (k+1)(d 3^d + n_p).
+ *  - Levels are numbered 0 (coarsest) .. n_levels-1 (finest).
+ *  - Errors are reported by return code only (never abort, never throw); stm_last_error()
+ *    returns a thread-local message for the last failing call on the calling thread.
+ */
+#ifndef STM_H
+#define STM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct stm_hierarchy stm_hierarchy;
+
+typedef enum {
+  STM_OK = 0,
+  STM_ERR_INVALID_ARG = 1,   /* bad parameter, level index, size or NULL pointer            */
+  STM_ERR_CUDA = 2,          /* a CUDA runtime call failed (message names it)               */
+  STM_ERR_OOM = 3,           /* device or host allocation failed                            */
+  STM_ERR_SINGULAR_CELL = 4, /* a cell matrix (or the coarse matrix) had a zero/non-finite pivot */
+  STM_ERR_NOT_CONVERGED = 5, /* FGMRES hit max_iter before reaching rtol; x holds last iterate */
+  STM_ERR_NONFINITE = 6,     /* NaN/Inf met in a residual norm                              */
+  STM_ERR_STATE = 7          /* call order violated (e.g. vcycle before factor_cells)       */
+} stm_status;
+
+typedef enum { STM_F64 = 0, STM_F32 = 1, STM_BF16 = 2 } stm_precision;
+
+typedef enum {
+  STM_VANKA_ADDITIVE = 0,       /* d += omega W sum_T R_T^T J_T^{-1} R_T (r - J d), W = diag(1/m_i) */
+  STM_VANKA_COLOURED = 1,       /* 2^d colours; per colour: t = r - J d, d_T += omega J_T^{-1} t_T  */
+  STM_VANKA_PAPER_OVERWRITE = 2 /* Sec. 4.2 literal: one residual, each DoF keeps the update of
+                                   its highest-index cell ("last update in the loop wins")         */
+} stm_smoother;
+
+/* Problem and method parameters (r = 2 fixed: Q2/P1disc, Eq. Def:Vh0).
+ * Geometry: box [0,length[0]] x [0,length[1]] (x [0,length[2]]), uniform level-1 grid of
+ * coarse_cells cells, refined n_levels-1 times by bisection; the level-1 cells with
+ * obstacle_lo[m] <= index[m] < obstacle_hi[m] for all m are removed (lo == hi: no obstacle).
+ * x = 0 is the inflow part of Gamma_D, x = length[0] the do-nothing outflow Gamma_o, every other
+ * boundary face (channel walls, obstacle surface) belongs to Gamma_D (Sec. 2.1). */
+typedef struct {
+  int dim;               /* 2 or 3                                                        */
+  int k;                 /* dG(k) time degree, 0..2 (Sec. 2.4)                            */
+  int n_levels;          /* G >= 2                                                        */
+  int coarse_cells[3];   /* level-1 grid                                                  */
+  double length[3];      /* box size                                                      */
+  int obstacle_lo[3], obstacle_hi[3];
+  double tau, nu;        /* slab length and viscosity                                     */
+  double gamma1, gamma2; /* Nitsche penalties (Eq. Def:B_GamD; the paper uses 35, 35)     */
+  int inv_precision;     /* stm_precision of the stored cell inverses                     */
+  int smoother;          /* stm_smoother                                                  */
+  double omega;          /* damping omega_d of the local update (Sec. 5.3)                */
+  int nu1, nu2;          /* pre-/post-smoothing steps of the V-cycle                      */
+} stm_params;
+
+/* Host setup of all levels (numbering, cell->DoF maps, colours, multiplicities, CSR patterns of
+ * J_g, transfer matrices) and upload to the current CUDA device. Synchronous.
+ * Cites: mesh hierarchy V^1 c ... c V^G of Sec. 4.1; local DoF sets of Eq. locdofs. */
+stm_status stm_build_hierarchy(const stm_params* params, stm_hierarchy** out);
+
+/* Sizes of one level: n_dofs = (k+1)(d R + n_p C), n_cells = C, n_local = n, nnz of J_g. */
+stm_status stm_sizes(const stm_hierarchy* h, int level, long long* n_dofs, long long* n_cells,
+                     int* n_local, long long* nnz);
+
+/* For every global DoF of `level`, its index into the flattened lattice state of that level:
+ * shape [k+1][d*P + n_p*Cf] with P = prod(2 c_m + 1) lattice points and Cf = prod(c_m) cells,
+ * velocity entry l*W + comp*P + lattice_index, pressure entry l*W + d*P + full_cell*n_p + mode.
+ * out_host: n_dofs int64 values, caller-owned. Synchronous. */
+stm_status stm_dof_lattice_index(const stm_hierarchy* h, int level, long long* out_host);
+
+/* Assemble the slab Jacobian J_g on every level (Problem 3.1 linearised as in Eq. linNewEq,
+ * forms of Eqs. Def:Ah and Def:B_GamD, time blocks of Eq. newton_system_matrix_dG_1) at the
+ * linearisation point whose finest-level DoF vector is X_dev (only its velocity is used; coarse
+ * levels take its values at their own nodes, which are fine nodes). nu overrides params.nu.
+ * Invalidates previous cell factors. */
+stm_status stm_assemble_jacobian(stm_hierarchy* h, const double* X_dev, double nu, void* stream);
+
+/* For every level g >= 1 and every cell T: J_T = J_g[idx_T, idx_T] (the rows and columns of the
+ * assembled matrix, Sec. 4.4), explicit inverse by Gauss-Jordan elimination with partial pivoting
+ * in FP64, stored in params.inv_precision (Sec. 4.3). Level 0: explicit FP64 inverse of J_0 for
+ * the direct coarse solve (Algorithm 1). Synchronises once to read the pivot flags; on
+ * STM_ERR_SINGULAR_CELL, *bad_level / *bad_cell name the first failing cell (cell -1: coarse). */
+stm_status stm_factor_cells(stm_hierarchy* h, void* stream, int* bad_level, long long* bad_cell);
+
+/* y = J_g x (transpose = 0) or y = J_g^T x (transpose = 1); x, y: n_dofs of `level`. */
+stm_status stm_spmv(stm_hierarchy* h, int level, const double* x_dev, double* y_dev, int transpose,
+                    void* stream);
+
+/* One smoothing step d <- S(d, r) on level g >= 1 with params.smoother and params.omega
+ * (Eq. LocVanka with damping; residual r - J_g d recomputed inside). transpose = 1 smooths for
+ * J_g^T with the transposed cell inverses. */
+stm_status stm_vanka_sweep(stm_hierarchy* h, int level, const double* r_dev, double* d_dev,
+                           int transpose, void* stream);
+
+/* Restriction coarse = P^T fine (level g -> g-1) and prolongation fine += P coarse
+ * (g-1 -> g); P interpolates the coarse Q2/P1disc function (Sec. 4.1, MGTransferPrebuilt). */
+stm_status stm_restrict(stm_hierarchy* h, int level, const double* fine_dev, double* coarse_dev,
+                        void* stream);
+stm_status stm_prolongate_add(stm_hierarchy* h, int level, const double* coarse_dev,
+                              double* fine_dev, void* stream);
+
+/* Direct coarse solve d = J_0^{-1} r (or J_0^{-T} r). */
+stm_status stm_coarse_solve(stm_hierarchy* h, const double* r_dev, double* d_dev, int transpose,
+                            void* stream);
+
+/* One V(nu1,nu2)-cycle (Algorithm 1) on the finest level with zero initial guess: d = M^{-1} r. */
+stm_status stm_vcycle(stm_hierarchy* h, const double* r_dev, double* d_dev, int transpose,
+                      void* stream);
+
+typedef struct {
+  int restart;   /* Krylov dimension m of FGMRES(m), e.g. 30                         */
+  int max_iter;  /* total iteration limit (the paper treats 1000 as divergence)      */
+  int transpose; /* 1: solve J^T x = b (adjoint) with the transposed preconditioner  */
+  int use_x0;    /* 1: x_dev holds the initial guess on entry; 0: start from x = 0   */
+  double rtol;   /* stop when ||b - J x||_2 <= rtol ||b||_2 (recurrence estimate)   */
+} stm_gmres_opts;
+
+typedef struct {
+  int iters;           /* FGMRES iterations (preconditioner applications)             */
+  int restarts;        /* completed restart cycles                                    */
+  int converged;       /* 1 if the recurrence residual reached rtol                   */
+  double rel_res_true; /* ||b - J x||_2 / ||b||_2 recomputed at exit                  */
+  double rel_res_est;  /* last recurrence estimate                                    */
+} stm_solve_info;
+
+/* Right-preconditioned flexible GMRES (Sec. 3) on the finest level, preconditioned by one
+ * V-cycle per iteration, classical Gram-Schmidt with re-orthogonalisation. Synchronises once
+ * per iteration to read the new Hessenberg column for the stopping test. Returns
+ * STM_ERR_NOT_CONVERGED (x = last iterate, info filled) if max_iter is reached. */
+stm_status stm_gmres_solve(stm_hierarchy* h, const double* b_dev, double* x_dev,
+                           const stm_gmres_opts* opts, stm_solve_info* info, void* stream);
+
+/* Same solve with HOST buffers: b_host is copied to the device, the solution is copied back
+ * into x_host (use_x0: x_host holds the initial guess). Synchronous on return. */
+stm_status stm_gmres_solve_host(stm_hierarchy* h, const double* b_host, double* x_host,
+                                const stm_gmres_opts* opts, stm_solve_info* info, void* stream);
+
+/* Copies of internal data for verification (synchronous, caller-owned host buffers):
+ * the CSR of J_g (rowptr: n_dofs+1, colidx/val: nnz) and the cell inverses of level g >= 1 as
+ * FP64, row-major per cell ([n_cells][n][n], converted from the stored precision). */
+stm_status stm_copy_jacobian(const stm_hierarchy* h, int level, long long* rowptr_host,
+                             int* colidx_host, double* val_host);
+stm_status stm_copy_cell_inverses(const stm_hierarchy* h, int level, double* inv_host);
+
+/* Measurement support (not part of the method). Kernel classes whose launches can be timed with
+ * CUDA events recorded on the launching stream, and the algorithmic bytes each launch moves:
+ *   VANKA_LOCAL   y_T = J_T^{-1} t_T over the cells of one launch: C (n^2 s + 20 n) bytes
+ *                 (inverse in storage width s, int32 index map, gathered t, written y);
+ *   JACOBIAN_SPMV residual / product with J_g: 8 nnz + 24 N bytes (values, x, y, b; column
+ *                 indices are representation overhead and not counted);
+ *   VANKA_COMBINE second pass of the additive/overwrite smoother; TRANSFER P and P^T products;
+ *   COARSE        dense coarse solve; KRYLOV Gram-Schmidt, norms and updates of FGMRES. */
+typedef enum {
+  STM_KCLASS_VANKA_LOCAL = 0,
+  STM_KCLASS_JACOBIAN_SPMV = 1,
+  STM_KCLASS_VANKA_COMBINE = 2,
+  STM_KCLASS_TRANSFER = 3,
+  STM_KCLASS_COARSE = 4,
+  STM_KCLASS_KRYLOV = 5
+} stm_kernel_class;
+
+/* Turn event timing of kernel launches on (1) or off (0); turning it on clears the records. */
+stm_status stm_profile_enable(stm_hierarchy* h, int enable);
+/* Synchronises the device and returns, for one kernel class, the summed event time (ms), the
+ * number of timed launches and the summed algorithmic bytes since profiling was enabled. */
+stm_status stm_profile_read(stm_hierarchy* h, int kernel_class, double* total_ms, long long* launches,
+                            double* bytes);
+/* Number of kernel launches issued by this library in this process so far. */
+long long stm_kernel_launches(void);
+
+void stm_destroy(stm_hierarchy* h);
+const char* stm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STM_H */

@@ -1,0 +1,522 @@
+// C-ABI entry points of libstm (declared in include/stm.h).
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+struct stm_hierarchy {
+  stm::Hierarchy H;
+};
+
+namespace stm {
+const char* last_error_cstr();
+}
+
+using namespace stm;
+
+#define STM_TRY(x)               \
+  do {                           \
+    stm_status s_ = (x);         \
+    if (s_ != STM_OK) return s_; \
+  } while (0)
+
+static stm_status bad_arg(const char* msg) {
+  set_error(msg);
+  return STM_ERR_INVALID_ARG;
+}
+
+static cudaStream_t S(void* p) { return reinterpret_cast<cudaStream_t>(p); }
+
+extern "C" {
+
+const char* stm_last_error(void) { return last_error_cstr(); }
+
+stm_status stm_build_hierarchy(const stm_params* params, stm_hierarchy** out) {
+  if (!params || !out) return bad_arg("stm_build_hierarchy: NULL argument");
+  *out = nullptr;
+  const stm_params& p = *params;
+  if (p.dim != 2 && p.dim != 3) return bad_arg("dim must be 2 or 3");
+  if (p.k < 0 || p.k > 2) return bad_arg("k must be 0, 1 or 2");
+  if (p.n_levels < 2 || p.n_levels > 12) return bad_arg("n_levels must be in [2, 12]");
+  for (int m = 0; m < p.dim; ++m) {
+    if (p.coarse_cells[m] < 1) return bad_arg("coarse_cells must be >= 1");
+    if (!(p.length[m] > 0.0)) return bad_arg("length must be > 0");
+    if (p.obstacle_lo[m] < 0 || p.obstacle_hi[m] > p.coarse_cells[m] || p.obstacle_lo[m] > p.obstacle_hi[m])
+      return bad_arg("obstacle range outside the coarse grid");
+  }
+  if (p.inv_precision < STM_F64 || p.inv_precision > STM_BF16) return bad_arg("inv_precision");
+  if (p.smoother < STM_VANKA_ADDITIVE || p.smoother > STM_VANKA_PAPER_OVERWRITE) return bad_arg("smoother");
+  if (!(p.tau > 0.0) || !(p.nu >= 0.0) || p.nu1 < 0 || p.nu2 < 0) return bad_arg("tau, nu, nu1, nu2");
+  stm_hierarchy* h = new (std::nothrow) stm_hierarchy();
+  if (!h) {
+    set_error("host allocation failed");
+    return STM_ERR_OOM;
+  }
+  h->H.p = p;
+  stm_status st = build_levels(h->H);
+  if (st != STM_OK) {
+    free_hierarchy(h->H);
+    delete h;
+    return st;
+  }
+  *out = h;
+  return STM_OK;
+}
+
+void stm_destroy(stm_hierarchy* h) {
+  if (!h) return;
+  free_hierarchy(h->H);
+  delete h;
+}
+
+stm_status stm_sizes(const stm_hierarchy* h, int level, long long* n_dofs, long long* n_cells, int* n_local,
+                     long long* nnz) {
+  if (!h) return bad_arg("NULL hierarchy");
+  if (level < 0 || level >= (int)h->H.L.size()) return bad_arg("level out of range");
+  const Level& L = h->H.L[level];
+  if (n_dofs) *n_dofs = L.N;
+  if (n_cells) *n_cells = L.C;
+  if (n_local) *n_local = L.n;
+  if (nnz) *nnz = L.nnz;
+  return STM_OK;
+}
+
+stm_status stm_dof_lattice_index(const stm_hierarchy* h, int level, long long* out) {
+  if (!h || !out) return bad_arg("NULL argument");
+  if (level < 0 || level >= (int)h->H.L.size()) return bad_arg("level out of range");
+  const Level& L = h->H.L[level];
+  const long long W = L.dim * L.P_lat + (long long)L.np * L.Cfull;
+  long long e = 0;
+  for (int a = 0; a < L.K; ++a) {
+    for (int l = 0; l < L.dim; ++l)
+      for (int nd = 0; nd < L.R; ++nd) out[e++] = a * W + l * L.P_lat + L.h_node_lat[nd];
+    for (int c = 0; c < L.C; ++c)
+      for (int q = 0; q < L.np; ++q) out[e++] = a * W + L.dim * L.P_lat + (long long)L.h_cell_full[c] * L.np + q;
+  }
+  return STM_OK;
+}
+
+stm_status stm_assemble_jacobian(stm_hierarchy* h, const double* X, double nu, void* stream) {
+  if (!h || !X) return bad_arg("NULL argument");
+  Hierarchy& H = h->H;
+  STM_TRY(inject_linearisation(H, X, S(stream)));
+  for (int g = 0; g < (int)H.L.size(); ++g) STM_TRY(assemble_level(H, g, nu, S(stream)));
+  H.assembled = true;
+  H.factored = false;
+  return STM_OK;
+}
+
+stm_status stm_factor_cells(stm_hierarchy* h, void* stream, int* bad_level, long long* bad_cell) {
+  if (!h) return bad_arg("NULL hierarchy");
+  Hierarchy& H = h->H;
+  if (!H.assembled) {
+    set_error("factor_cells before assemble_jacobian");
+    return STM_ERR_STATE;
+  }
+  if (bad_level) *bad_level = -1;
+  if (bad_cell) *bad_cell = -1;
+  cudaStream_t s = S(stream);
+  for (int g = 1; g < (int)H.L.size(); ++g) {
+    STM_CUDA(cudaMemsetAsync(H.dflag, 0, sizeof(int) * 2, s));
+    STM_CUDA(cudaMemsetAsync(H.dbad, 0xff, sizeof(long long), s));
+    STM_TRY(factor_level(H, g, s));
+    int flag = 0;
+    long long bad = -1;
+    STM_CUDA(cudaMemcpyAsync(&flag, H.dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    STM_CUDA(cudaMemcpyAsync(&bad, H.dbad, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    STM_CUDA(cudaStreamSynchronize(s));
+    if (flag) {
+      if (bad_level) *bad_level = g;
+      if (bad_cell) *bad_cell = bad;
+      set_error("singular cell matrix (zero or non-finite pivot)");
+      return STM_ERR_SINGULAR_CELL;
+    }
+  }
+  STM_CUDA(cudaMemsetAsync(H.dflag + 1, 0, sizeof(int), s));
+  STM_TRY(factor_coarse(H, s));
+  int cflag = 0;
+  STM_CUDA(cudaMemcpyAsync(&cflag, H.dflag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+  STM_CUDA(cudaStreamSynchronize(s));
+  if (cflag) {
+    if (bad_level) *bad_level = 0;
+    set_error("singular coarse matrix");
+    return STM_ERR_SINGULAR_CELL;
+  }
+  H.factored = true;
+  return STM_OK;
+}
+
+static stm_status need_level(const Hierarchy& H, int level, int lo) {
+  if (level < lo || level >= (int)H.L.size()) return bad_arg("level out of range");
+  return STM_OK;
+}
+
+stm_status stm_spmv(stm_hierarchy* h, int level, const double* x, double* y, int transpose, void* stream) {
+  if (!h || !x || !y) return bad_arg("NULL argument");
+  STM_TRY(need_level(h->H, level, 0));
+  if (!h->H.assembled) {
+    set_error("spmv before assemble_jacobian");
+    return STM_ERR_STATE;
+  }
+  return jacobian_apply(h->H, level, x, nullptr, y, 0, transpose, S(stream));
+}
+
+stm_status stm_vanka_sweep(stm_hierarchy* h, int level, const double* r, double* d, int transpose, void* stream) {
+  if (!h || !r || !d) return bad_arg("NULL argument");
+  STM_TRY(need_level(h->H, level, 1));
+  if (!h->H.factored) {
+    set_error("vanka_sweep before factor_cells");
+    return STM_ERR_STATE;
+  }
+  return vanka_step(h->H, level, r, d, transpose, false, S(stream));
+}
+
+stm_status stm_restrict(stm_hierarchy* h, int level, const double* fine, double* coarse, void* stream) {
+  if (!h || !fine || !coarse) return bad_arg("NULL argument");
+  STM_TRY(need_level(h->H, level, 1));
+  Level& L = h->H.L[level];
+  return csr_apply(L.Rt_rowptr, L.Rt_col, L.Rt_val, h->H.L[level - 1].N, fine, nullptr, coarse, 0, S(stream));
+}
+
+stm_status stm_prolongate_add(stm_hierarchy* h, int level, const double* coarse, double* fine, void* stream) {
+  if (!h || !fine || !coarse) return bad_arg("NULL argument");
+  STM_TRY(need_level(h->H, level, 1));
+  Level& L = h->H.L[level];
+  return csr_apply(L.P_rowptr, L.P_col, L.P_val, L.N, coarse, nullptr, fine, 2, S(stream));
+}
+
+stm_status stm_coarse_solve(stm_hierarchy* h, const double* r, double* d, int transpose, void* stream) {
+  if (!h || !r || !d) return bad_arg("NULL argument");
+  if (!h->H.factored) {
+    set_error("coarse_solve before factor_cells");
+    return STM_ERR_STATE;
+  }
+  return coarse_apply(h->H, r, d, transpose, S(stream));
+}
+
+stm_status stm_vcycle(stm_hierarchy* h, const double* r, double* d, int transpose, void* stream) {
+  if (!h || !r || !d) return bad_arg("NULL argument");
+  if (!h->H.factored) {
+    set_error("vcycle before factor_cells");
+    return STM_ERR_STATE;
+  }
+  return vcycle(h->H, r, d, transpose, S(stream));
+}
+
+// ---------------------------------------------------------------------------------------------
+// Flexible GMRES (Sec. 3), right preconditioned, CGS with one re-orthogonalisation
+// ---------------------------------------------------------------------------------------------
+__global__ void k_scale_host(double* y, const double* x, double f, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = x[i] * f;
+}
+
+static stm_status ensure_krylov(Hierarchy& H, int m) {
+  const long long N = H.L.back().N;
+  if (H.restart_cap >= m && H.V) return STM_OK;
+  void* ptrs[] = {H.V, H.Z, H.w, H.hcol, H.part, H.yvec};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  H.nblk_dot = 304;
+  STM_CUDA(cudaMalloc(&H.V, sizeof(double) * (size_t)(m + 1) * N));
+  STM_CUDA(cudaMalloc(&H.Z, sizeof(double) * (size_t)m * N));
+  STM_CUDA(cudaMalloc(&H.w, sizeof(double) * (size_t)N));
+  STM_CUDA(cudaMalloc(&H.hcol, sizeof(double) * (size_t)(2 * m + 8)));
+  STM_CUDA(cudaMalloc(&H.part, sizeof(double) * (size_t)(m + 2) * H.nblk_dot));
+  STM_CUDA(cudaMalloc(&H.yvec, sizeof(double) * (size_t)(m + 2)));
+  H.restart_cap = m;
+  return STM_OK;
+}
+
+static stm_status gmres_core(Hierarchy& H, const double* b, double* x, const stm_gmres_opts& o, stm_solve_info* info,
+                             cudaStream_t s) {
+  const int m = o.restart;
+  const long long N = H.L.back().N;
+  const int tr = o.transpose ? 1 : 0;
+  const int G = (int)H.L.size();
+  STM_TRY(ensure_krylov(H, m));
+  const int nb = H.nblk_dot;
+  const int sblocks = (int)std::min<long long>((N + 255) / 256, 152 * 8LL);
+  stm_solve_info inf{};
+  auto host_norm = [&](const double* v, double* out) -> stm_status {
+    STM_TRY(vec_norm_sq(v, N, H.hcol, H.part, nb, s));
+    double t = 0.0;
+    STM_CUDA(cudaMemcpyAsync(&t, H.hcol, sizeof(double), cudaMemcpyDeviceToHost, s));
+    STM_CUDA(cudaStreamSynchronize(s));
+    *out = std::sqrt(t);
+    return STM_OK;
+  };
+  double bnorm = 0.0;
+  STM_TRY(host_norm(b, &bnorm));
+  if (!std::isfinite(bnorm)) {
+    set_error("non-finite right-hand side");
+    return STM_ERR_NONFINITE;
+  }
+  if (!o.use_x0 || bnorm == 0.0) STM_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * N, s));
+  if (bnorm == 0.0) {
+    inf.converged = 1;
+    if (info) *info = inf;
+    return STM_OK;
+  }
+  const double tol = o.rtol * bnorm;
+  std::vector<double> Hm((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), hc(m + 2), y(m);
+  int it = 0;
+  bool converged = false;
+  double est = 1.0;
+  for (;;) {
+    // r = b - J x  -> V[0]
+    STM_TRY(jacobian_apply(H, G - 1, x, b, H.V, 1, tr, s));
+    double beta = 0.0;
+    STM_TRY(host_norm(H.V, &beta));
+    if (!std::isfinite(beta)) {
+      set_error("non-finite residual norm");
+      return STM_ERR_NONFINITE;
+    }
+    est = beta / bnorm;
+    if (beta <= tol || it >= o.max_iter) {
+      converged = beta <= tol;
+      inf.rel_res_true = beta / bnorm;
+      break;
+    }
+    k_scale_host<<<sblocks, 256, 0, s>>>(H.V, H.V, 1.0 / beta, N); note_launch();
+    std::fill(Hm.begin(), Hm.end(), 0.0);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int jd = 0;
+    bool stop = false;
+    for (int j = 0; j < m; ++j) {
+      double* vj = H.V + (size_t)j * N;
+      double* zj = H.Z + (size_t)j * N;
+      STM_TRY(vcycle(H, vj, zj, tr, s));
+      STM_TRY(jacobian_apply(H, G - 1, zj, nullptr, H.w, 0, tr, s));
+      // classical Gram-Schmidt, twice
+      ProfScope ps(&H, STM_KCLASS_KRYLOV, s, 8.0 * N * (4.0 * (j + 1) + 4.0));
+      STM_TRY(batched_dots(H.V, j + 1, H.w, N, H.hcol, H.part, nb, s));
+      STM_TRY(batched_update(H.V, j + 1, H.hcol, H.w, N, s));
+      STM_TRY(batched_dots(H.V, j + 1, H.w, N, H.hcol + m + 2, H.part, nb, s));
+      STM_TRY(batched_update(H.V, j + 1, H.hcol + m + 2, H.w, N, s));
+      STM_TRY(vec_axpby_dev(H.hcol, H.hcol + m + 2, j + 1, s));
+      STM_TRY(vec_norm_sq(H.w, N, H.hcol + j + 1, H.part, nb, s));
+      STM_CUDA(cudaMemcpyAsync(hc.data(), H.hcol, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, s));
+      STM_CUDA(cudaStreamSynchronize(s));
+      const double hn = std::sqrt(hc[j + 1]);
+      if (!std::isfinite(hn)) {
+        set_error("non-finite Arnoldi norm");
+        return STM_ERR_NONFINITE;
+      }
+      for (int i = 0; i <= j; ++i) Hm[(size_t)i * m + j] = hc[i];
+      Hm[(size_t)(j + 1) * m + j] = hn;
+      if (hn > 0.0) k_scale_host<<<sblocks, 256, 0, s>>>(H.V + (size_t)(j + 1) * N, H.w, 1.0 / hn, N); note_launch();
+      for (int i = 0; i < j; ++i) {
+        const double a = Hm[(size_t)i * m + j], bb = Hm[(size_t)(i + 1) * m + j];
+        Hm[(size_t)i * m + j] = cs[i] * a + sn[i] * bb;
+        Hm[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
+      }
+      const double a = Hm[(size_t)j * m + j], bb = Hm[(size_t)(j + 1) * m + j];
+      const double rho = std::hypot(a, bb);
+      cs[j] = a / rho;
+      sn[j] = bb / rho;
+      Hm[(size_t)j * m + j] = rho;
+      Hm[(size_t)(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++it;
+      jd = j + 1;
+      est = std::fabs(g[j + 1]) / bnorm;
+      if (std::fabs(g[j + 1]) <= tol || it >= o.max_iter || hn == 0.0) {
+        converged = std::fabs(g[j + 1]) <= tol || hn == 0.0;
+        stop = true;
+        break;
+      }
+    }
+    // y = H^{-1} g (upper triangular), x += Z y
+    for (int i = jd - 1; i >= 0; --i) {
+      double t = g[i];
+      for (int k2 = i + 1; k2 < jd; ++k2) t -= Hm[(size_t)i * m + k2] * y[k2];
+      y[i] = t / Hm[(size_t)i * m + i];
+    }
+    STM_CUDA(cudaMemcpyAsync(H.yvec, y.data(), sizeof(double) * jd, cudaMemcpyHostToDevice, s));
+    STM_TRY(gemv_accumulate(H.Z, jd, H.yvec, x, N, s));
+    if (stop) {
+      STM_TRY(jacobian_apply(H, G - 1, x, b, H.w, 1, tr, s));
+      double rn = 0.0;
+      STM_TRY(host_norm(H.w, &rn));
+      inf.rel_res_true = rn / bnorm;
+      break;
+    }
+    ++inf.restarts;
+  }
+  inf.iters = it;
+  inf.converged = converged ? 1 : 0;
+  inf.rel_res_est = est;
+  if (info) *info = inf;
+  if (!converged) {
+    set_error("FGMRES reached max_iter");
+    return STM_ERR_NOT_CONVERGED;
+  }
+  return STM_OK;
+}
+
+stm_status stm_gmres_solve(stm_hierarchy* h, const double* b, double* x, const stm_gmres_opts* opts,
+                           stm_solve_info* info, void* stream) {
+  if (!h || !b || !x || !opts) return bad_arg("NULL argument");
+  if (opts->restart < 1 || opts->restart > 200 || opts->max_iter < 0 || !(opts->rtol >= 0.0))
+    return bad_arg("restart in [1,200], max_iter >= 0, rtol >= 0");
+  if (!h->H.factored) {
+    set_error("gmres_solve before factor_cells");
+    return STM_ERR_STATE;
+  }
+  return gmres_core(h->H, b, x, *opts, info, S(stream));
+}
+
+stm_status stm_gmres_solve_host(stm_hierarchy* h, const double* b_host, double* x_host, const stm_gmres_opts* opts,
+                                stm_solve_info* info, void* stream) {
+  if (!h || !b_host || !x_host || !opts) return bad_arg("NULL argument");
+  if (!h->H.factored) {
+    set_error("gmres_solve before factor_cells");
+    return STM_ERR_STATE;
+  }
+  Hierarchy& H = h->H;
+  const long long N = H.L.back().N;
+  cudaStream_t s = S(stream);
+  if (!H.bbuf) STM_CUDA(cudaMalloc(&H.bbuf, sizeof(double) * N));
+  if (!H.xbuf) STM_CUDA(cudaMalloc(&H.xbuf, sizeof(double) * N));
+  STM_CUDA(cudaMemcpyAsync(H.bbuf, b_host, sizeof(double) * N, cudaMemcpyHostToDevice, s));
+  if (opts->use_x0) STM_CUDA(cudaMemcpyAsync(H.xbuf, x_host, sizeof(double) * N, cudaMemcpyHostToDevice, s));
+  stm_status st = stm_gmres_solve(h, H.bbuf, H.xbuf, opts, info, stream);
+  if (st != STM_OK && st != STM_ERR_NOT_CONVERGED) return st;
+  STM_CUDA(cudaMemcpyAsync(x_host, H.xbuf, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+  STM_CUDA(cudaStreamSynchronize(s));
+  return st;
+}
+
+stm_status stm_copy_jacobian(const stm_hierarchy* h, int level, long long* rowptr, int* colidx, double* val) {
+  if (!h || !rowptr || !colidx || !val) return bad_arg("NULL argument");
+  STM_TRY(need_level(h->H, level, 0));
+  const Level& L = h->H.L[level];
+  STM_CUDA(cudaDeviceSynchronize());
+  STM_CUDA(cudaMemcpy(rowptr, L.rowptr, sizeof(long long) * (L.N + 1), cudaMemcpyDeviceToHost));
+  STM_CUDA(cudaMemcpy(colidx, L.colidx, sizeof(int) * L.nnz, cudaMemcpyDeviceToHost));
+  STM_CUDA(cudaMemcpy(val, L.val, sizeof(double) * L.nnz, cudaMemcpyDeviceToHost));
+  return STM_OK;
+}
+
+stm_status stm_copy_cell_inverses(const stm_hierarchy* h, int level, double* out) {
+  if (!h || !out) return bad_arg("NULL argument");
+  STM_TRY(need_level(h->H, level, 1));
+  const Hierarchy& H = h->H;
+  if (!H.factored) {
+    set_error("copy_cell_inverses before factor_cells");
+    return STM_ERR_STATE;
+  }
+  const Level& L = H.L[level];
+  const size_t nn2 = (size_t)L.n * L.n, tot = nn2 * L.C;
+  const int prec = H.p.inv_precision;
+  const size_t es = prec == STM_F64 ? 8 : prec == STM_F32 ? 4 : 2;
+  std::vector<unsigned char> raw(tot * es);
+  STM_CUDA(cudaDeviceSynchronize());
+  STM_CUDA(cudaMemcpy(raw.data(), L.inv, tot * es, cudaMemcpyDeviceToHost));
+  for (size_t c = 0; c < (size_t)L.C; ++c)
+    for (int j = 0; j < L.n; ++j)
+      for (int i = 0; i < L.n; ++i) {
+        const size_t e = c * nn2 + (size_t)j * L.n + i;  // stored column-major
+        double v;
+        if (prec == STM_F64) {
+          std::memcpy(&v, &raw[e * 8], 8);
+        } else if (prec == STM_F32) {
+          float f;
+          std::memcpy(&f, &raw[e * 4], 4);
+          v = f;
+        } else {
+          uint16_t b16;
+          std::memcpy(&b16, &raw[e * 2], 2);
+          uint32_t u = (uint32_t)b16 << 16;
+          float f;
+          std::memcpy(&f, &u, 4);
+          v = f;
+        }
+        out[c * nn2 + (size_t)i * L.n + j] = v;
+      }
+  return STM_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Measurement support: launch counter and per-class event timing
+// ---------------------------------------------------------------------------------------------
+namespace stm {
+std::atomic<long long> g_launches{0};
+
+static cudaEvent_t pool_get(Profiler& P) {
+  if (!P.pool.empty()) {
+    cudaEvent_t e = P.pool.back();
+    P.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+ProfScope::ProfScope(Hierarchy* H_, int cls_, cudaStream_t s_, double bytes_) : H(H_), cls(cls_), s(s_), bytes(bytes_) {
+  if (H && H->prof.on) {
+    a = pool_get(H->prof);
+    cudaEventRecord(a, s);
+  }
+}
+
+ProfScope::~ProfScope() {
+  if (a) {
+    cudaEvent_t b = pool_get(H->prof);
+    cudaEventRecord(b, s);
+    H->prof.recs.push_back(ProfRec{a, b, cls, bytes});
+  }
+}
+
+static void profile_drain(Profiler& P) {
+  for (ProfRec& r : P.recs) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      P.total_ms[r.cls] += ms;
+      P.count[r.cls] += 1;
+      P.bytes[r.cls] += r.bytes;
+    }
+    P.pool.push_back(r.a);
+    P.pool.push_back(r.b);
+  }
+  P.recs.clear();
+}
+}  // namespace stm
+
+extern "C" {
+
+stm_status stm_profile_enable(stm_hierarchy* h, int enable) {
+  if (!h) return bad_arg("NULL hierarchy");
+  Profiler& P = h->H.prof;
+  STM_CUDA(cudaDeviceSynchronize());
+  profile_drain(P);
+  if (enable) {
+    for (int c = 0; c < STM_KCLASS_COUNT; ++c) P.total_ms[c] = 0.0, P.count[c] = 0, P.bytes[c] = 0.0;
+  }
+  P.on = enable != 0;
+  return STM_OK;
+}
+
+stm_status stm_profile_read(stm_hierarchy* h, int kernel_class, double* total_ms, long long* launches, double* bytes) {
+  if (!h) return bad_arg("NULL hierarchy");
+  if (kernel_class < 0 || kernel_class >= STM_KCLASS_COUNT) return bad_arg("kernel_class out of range");
+  Profiler& P = h->H.prof;
+  STM_CUDA(cudaDeviceSynchronize());
+  profile_drain(P);
+  if (total_ms) *total_ms = P.total_ms[kernel_class];
+  if (launches) *launches = P.count[kernel_class];
+  if (bytes) *bytes = P.bytes[kernel_class];
+  return STM_OK;
+}
+
+long long stm_kernel_launches(void) { return g_launches.load(); }
+
+}  // extern "C"

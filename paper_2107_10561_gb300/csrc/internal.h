@@ -1,0 +1,188 @@
+// Internal data structures of libstm (not part of the C-ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <atomic>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "stm.h"
+
+namespace stm {
+constexpr int STM_KCLASS_COUNT = 6;
+
+constexpr int kMaxDim = 3;
+constexpr int kQ1 = 4;  // Gauss points per direction (exact for every integrand of the forms)
+
+// Thread-local error message and helpers -----------------------------------------------------
+void set_error(const std::string& msg);
+stm_status cuda_fail(cudaError_t e, const char* what);
+#define STM_CUDA(call)                                          \
+  do {                                                          \
+    cudaError_t e_ = (call);                                    \
+    if (e_ != cudaSuccess) return ::stm::cuda_fail(e_, #call);  \
+  } while (0)
+
+// Launch accounting and optional per-class CUDA-event timing --------------------------------
+extern std::atomic<long long> g_launches;
+inline void note_launch(long long n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+struct ProfRec {
+  cudaEvent_t a, b;
+  int cls;
+  double bytes;
+};
+struct Profiler {
+  bool on = false;
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> pool;
+  double total_ms[STM_KCLASS_COUNT] = {};
+  long long count[STM_KCLASS_COUNT] = {};
+  double bytes[STM_KCLASS_COUNT] = {};
+};
+
+// Reference tables of a uniform level (all cells congruent): computed on the host --------------
+// Layout of the packed device buffer `ref` (doubles):
+//   W[nq]                       quadrature weight x |T|
+//   phi[nq][nv]                 Q2 basis values
+//   gphi[nq][nv][d]             physical gradients
+//   M[nv][nv], Kst[nv][nv]      mass, stiffness
+//   Div[d][np][nv]              (d_m phi_j, xi_q)
+//   per face f in 0..2d-1:  S[nv][nv], G[nv][nv] (<grad phi_j . n, phi_i>), Pf[np][nv]
+struct RefOffsets {
+  int nq, nv, np;
+  int W, phi, gphi, M, Kst, Div, face0, face_stride, fS, fG, fPf;
+  int total;
+};
+
+struct Level {
+  // geometry and sizes
+  int dim = 2, K = 2;         // K = k + 1 time nodes
+  int cells[3] = {1, 1, 1};   // cells per axis (cells[2] = 1 in 2D)
+  double h[3] = {1, 1, 1};
+  double hT = 1;              // cell diameter (Nitsche h)
+  int lat[3] = {1, 1, 1};     // lattice points per axis
+  int C = 0, R = 0, S = 0, nv = 9, np = 3, nt = 0, n = 0;
+  long long block = 0, N = 0, nnz = 0, P_lat = 0, Cfull = 0;
+
+  // host copies needed for later set-up steps
+  std::vector<int> h_cell_full;   // active cell -> full cell index
+  std::vector<int> h_cell_xyz;    // [C][3]
+  std::vector<int> h_node_lat;    // node -> lattice index
+  std::vector<int> h_lat_node;    // lattice index -> node (-1: unused)
+  std::vector<int> h_cell_nodes;  // [C][nv]
+  std::vector<int> h_full_active; // full cell -> active index (-1: removed)
+
+  // device data -----------------------------------------------------------------------------
+  int* idx = nullptr;             // [C][n] global DoF of each local DoF
+  int* cell_nodes = nullptr;      // [C][nv]
+  unsigned char* bmask = nullptr; // [C] bit f set: face f on Gamma_D
+  unsigned char* rank = nullptr;  // [C][nv][nv] rank of node j in the neighbour list of node i
+  unsigned char* cellrank = nullptr; // [C][nv] rank of the cell among the cells of node i
+  int* nn = nullptr;              // [R] number of neighbour nodes
+  int* ncell = nullptr;           // [R] number of cells containing the node
+  long long* rowptr = nullptr;    // [N+1]
+  int* colidx = nullptr;          // [nnz]
+  double* val = nullptr;          // [nnz]
+  double* valT = nullptr;         // [nnz] values of J^T on the same (symmetric) pattern, lazy
+  long long* tpos = nullptr;      // not kept (transpose built on demand)
+  double* ref = nullptr;          // packed reference tables
+  RefOffsets ro{};
+  int* inj = nullptr;             // [R] node -> finest-level node holding its linearisation value
+  double* wnod = nullptr;         // [K][d][R] linearisation velocity at this level's nodes
+
+  // smoother data (levels >= 1)
+  void* inv = nullptr;            // [C][n*n] column-major per cell, storage precision
+  double* wmult = nullptr;        // [N] 1/m_i
+  int* own_ptr = nullptr;         // [N+1]
+  int* own_pos = nullptr;         // [sum m_i] flat positions c*n + alpha
+  int* last_owner = nullptr;      // [N] flat position of the highest-index owning cell
+  int* colour_cells = nullptr;    // cells sorted by colour
+  int colour_off[9] = {0};
+  double* Y = nullptr;            // [C][n] per-cell local corrections (scratch)
+
+  // transfer from level g-1 (coarse) to this level: P [N x N_c], P^T [N_c x N]
+  long long* P_rowptr = nullptr; int* P_col = nullptr; double* P_val = nullptr;
+  long long* Rt_rowptr = nullptr; int* Rt_col = nullptr; double* Rt_val = nullptr;
+
+  // work vectors of the V-cycle
+  double *d = nullptr, *r = nullptr, *t = nullptr;
+};
+
+struct Hierarchy {
+  stm_params p{};
+  std::vector<Level> L;
+  double Mt[3][3] = {}, D[3][3] = {}, T[3][3][3] = {};
+  bool assembled = false, factored = false;
+  // coarse direct solver: explicit FP64 inverse of J_0, row-major [N0][N0]
+  double* cinv = nullptr;
+  long long N0 = 0;
+  int* dflag = nullptr;           // device flags: [0] singular flag, [1..2] bad cell (int64 split)
+  long long* dbad = nullptr;
+  // FGMRES work space (finest level)
+  int restart_cap = 0;
+  double* V = nullptr;            // [(m+1)][N]
+  double* Z = nullptr;            // [m][N]
+  double* w = nullptr;            // [N]
+  double* hcol = nullptr;         // [m+2] device Hessenberg column / scratch
+  double* part = nullptr;         // partial sums of batched dots
+  double* yvec = nullptr;         // [m]
+  double* bbuf = nullptr;         // host-API staging for b and x
+  double* xbuf = nullptr;
+  int nblk_dot = 0;
+  Profiler prof;
+};
+
+// Records CUDA events around the launches made in its lifetime when profiling is on.
+struct ProfScope {
+  Hierarchy* H;
+  int cls;
+  cudaStream_t s;
+  double bytes;
+  cudaEvent_t a = nullptr;
+  ProfScope(Hierarchy* H_, int cls_, cudaStream_t s_, double bytes_);
+  ~ProfScope();
+};
+
+// Host set-up (hierarchy.cpp)
+stm_status build_levels(Hierarchy& H);
+void free_hierarchy(Hierarchy& H);
+void time_matrices(int k, double tau, double Mt[3][3], double D[3][3], double T[3][3][3]);
+
+// Kernel launchers (kernels_*.cu) -----------------------------------------------------------
+stm_status launch_fill_colidx(Level& Lv, const int* nbr_ptr, const int* nbr_idx,
+                              const int* node_cells, cudaStream_t s);
+stm_status inject_linearisation(Hierarchy& H, const double* X_fine, cudaStream_t s);
+stm_status assemble_level(Hierarchy& H, int g, double nu, cudaStream_t s);
+stm_status factor_level(Hierarchy& H, int g, cudaStream_t s);
+stm_status factor_coarse(Hierarchy& H, cudaStream_t s);
+stm_status ensure_transpose(Hierarchy& H, int g, cudaStream_t s);
+
+// y = alpha*A x + beta_y*y (+ b): mode 0: y = A x; 1: y = b - A x; 2: y += A x
+stm_status csr_apply(const long long* rowptr, const int* col, const double* val, long long nrows,
+                     const double* x, const double* b, double* y, int mode, cudaStream_t s);
+stm_status jacobian_apply(Hierarchy& H, int g, const double* x, const double* b, double* y,
+                          int mode, int transpose, cudaStream_t s);
+stm_status vanka_step(Hierarchy& H, int g, const double* r, double* d, int transpose,
+                      bool d_is_zero, cudaStream_t s);
+stm_status coarse_apply(Hierarchy& H, const double* r, double* d, int transpose, cudaStream_t s);
+stm_status vcycle(Hierarchy& H, const double* r, double* d, int transpose, cudaStream_t s);
+
+// BLAS-1 style helpers on device vectors (kernels_krylov.cu)
+stm_status vec_fill(double* x, double v, long long n, cudaStream_t s);
+stm_status vec_copy(double* y, const double* x, long long n, cudaStream_t s);
+stm_status vec_scale_to(double* y, const double* x, const double* scale_dev, int inv, long long n, cudaStream_t s);
+stm_status batched_dots(const double* V, int nv, const double* w, long long n, double* out,
+                        double* part, int nblk, cudaStream_t s);
+stm_status batched_update(const double* V, int nv, const double* h, double* w, long long n,
+                          cudaStream_t s);
+stm_status gemv_accumulate(const double* Z, int nz, const double* y, double* x, long long n,
+                           cudaStream_t s);
+stm_status vec_axpby_dev(double* hacc, const double* h2, int n, cudaStream_t s);
+stm_status vec_norm_sq(const double* x, long long n, double* out, double* part, int nblk,
+                       cudaStream_t s);
+
+}  // namespace stm

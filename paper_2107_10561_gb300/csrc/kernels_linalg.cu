@@ -1,0 +1,299 @@
+// Sparse and dense FP64 linear algebra of the V-cycle and of FGMRES:
+//  * CSR products with J_g (residual t = r - J d, Alg. 1 and Eq. LocVanka), with P and P^T (Sec. 4.1);
+//  * J_g^T on the same, structurally symmetric pattern (values permuted once per assembly);
+//  * the coarse solve d = J_0^{-1} r as a dense matrix-vector product with the explicit inverse;
+//  * Gram-Schmidt building blocks of flexible GMRES (batched dots / updates, norms).
+#include "internal.h"
+
+namespace stm {
+
+static int sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 152;
+  }
+  return n;
+}
+
+// One warp per row. mode 0: y = A x; 1: y = b - A x; 2: y += A x.
+__global__ void __launch_bounds__(256) k_csr(const long long* __restrict__ rowptr, const int* __restrict__ col,
+                                             const double* __restrict__ val, long long nrows,
+                                             const double* __restrict__ x, const double* __restrict__ b,
+                                             double* __restrict__ y, int mode) {
+  const int lane = threadIdx.x & 31;
+  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long row = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < nrows; row += warps) {
+    const long long e0 = rowptr[row], e1 = rowptr[row + 1];
+    double s = 0.0;
+    for (long long e = e0 + lane; e < e1; e += 32) s += __ldg(val + e) * __ldg(x + __ldg(col + e));
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (lane == 0) {
+      if (mode == 0) y[row] = s;
+      else if (mode == 1) y[row] = b[row] - s;
+      else y[row] += s;
+    }
+  }
+}
+
+stm_status csr_apply(const long long* rowptr, const int* col, const double* val, long long nrows,
+                     const double* x, const double* b, double* y, int mode, cudaStream_t s) {
+  const int blocks = (int)std::min<long long>((nrows + 7) / 8, (long long)sms() * 16);
+  k_csr<<<blocks, 256, 0, s>>>(rowptr, col, val, nrows, x, b, y, mode); note_launch();
+  STM_CUDA(cudaGetLastError());
+  return STM_OK;
+}
+
+// valT[p] = value of the mirrored entry (col, row) of entry p = (row, col) (binary search in row col).
+__global__ void k_transpose_values(const long long* __restrict__ rowptr, const int* __restrict__ col,
+                                   const double* __restrict__ val, double* __restrict__ valT, long long nrows,
+                                   int* flag) {
+  const int lane = threadIdx.x & 31;
+  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long row = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < nrows; row += warps) {
+    for (long long e = rowptr[row] + lane; e < rowptr[row + 1]; e += 32) {
+      const int j = col[e];
+      long long lo = rowptr[j], hi = rowptr[j + 1] - 1;
+      double v = 0.0;
+      bool found = false;
+      while (lo <= hi) {
+        const long long mid = (lo + hi) >> 1;
+        const int cm = col[mid];
+        if (cm == (int)row) { v = val[mid]; found = true; break; }
+        if (cm < (int)row) lo = mid + 1; else hi = mid - 1;
+      }
+      if (!found) atomicExch(flag, 1);
+      valT[e] = v;
+    }
+  }
+}
+
+stm_status ensure_transpose(Hierarchy& H, int g, cudaStream_t s) {
+  Level& L = H.L[g];
+  if (L.valT) return STM_OK;
+  STM_CUDA(cudaMalloc(&L.valT, sizeof(double) * L.nnz));
+  STM_CUDA(cudaMemsetAsync(H.dflag + 2, 0, sizeof(int), s));
+  const int blocks = (int)std::min<long long>((L.N + 7) / 8, (long long)sms() * 16);
+  k_transpose_values<<<blocks, 256, 0, s>>>(L.rowptr, L.colidx, L.val, L.valT, L.N, H.dflag + 2); note_launch();
+  STM_CUDA(cudaGetLastError());
+  int flag = 0;
+  STM_CUDA(cudaMemcpyAsync(&flag, H.dflag + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+  STM_CUDA(cudaStreamSynchronize(s));
+  if (flag) {
+    set_error("J pattern is not structurally symmetric");
+    return STM_ERR_STATE;
+  }
+  return STM_OK;
+}
+
+stm_status jacobian_apply(Hierarchy& H, int g, const double* x, const double* b, double* y, int mode,
+                          int transpose, cudaStream_t s) {
+  Level& L = H.L[g];
+  const double* v = L.val;
+  if (transpose) {
+    stm_status st = ensure_transpose(H, g, s);
+    if (st != STM_OK) return st;
+    v = L.valT;
+  }
+  ProfScope ps(&H, STM_KCLASS_JACOBIAN_SPMV, s, 8.0 * (double)L.nnz + 24.0 * (double)L.N);
+  return csr_apply(L.rowptr, L.colidx, v, L.N, x, b, y, mode, s);
+}
+
+// Dense coarse solve: d = Cinv r (row-major) or d = Cinv^T r.
+__global__ void k_dense_gemv(const double* __restrict__ A, long long n, const double* __restrict__ x,
+                             double* __restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long row = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < n; row += warps) {
+    const double* a = A + row * n;
+    double s = 0.0;
+    for (long long j = lane; j < n; j += 32) s += a[j] * x[j];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (lane == 0) y[row] = s;
+  }
+}
+__global__ void k_dense_gemv_t(const double* __restrict__ A, long long n, const double* __restrict__ x,
+                               double* __restrict__ y) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (long long i = 0; i < n; ++i) s += A[i * n + j] * x[i];
+    y[j] = s;
+  }
+}
+
+stm_status coarse_apply(Hierarchy& H, const double* r, double* d, int transpose, cudaStream_t s) {
+  const long long n = H.N0;
+  ProfScope ps(&H, STM_KCLASS_COARSE, s, 8.0 * (double)n * (double)n + 16.0 * (double)n);
+  if (!transpose) {
+    const int blocks = (int)std::min<long long>((n + 7) / 8, (long long)sms() * 16);
+    k_dense_gemv<<<blocks, 256, 0, s>>>(H.cinv, n, r, d); note_launch();
+  } else {
+    const int blocks = (int)std::min<long long>((n + 127) / 128, (long long)sms() * 8);
+    k_dense_gemv_t<<<blocks, 128, 0, s>>>(H.cinv, n, r, d); note_launch();
+  }
+  STM_CUDA(cudaGetLastError());
+  return STM_OK;
+}
+
+// Algorithm 1 (V-cycle), iterative form of the recursion, zero initial guess on every level.
+stm_status vcycle(Hierarchy& H, const double* r_fine, double* d_fine, int transpose, cudaStream_t s) {
+  const int G = (int)H.L.size();
+  const int nu1 = H.p.nu1, nu2 = H.p.nu2;
+  // descend
+  const double* r = r_fine;
+  for (int g = G - 1; g >= 1; --g) {
+    Level& L = H.L[g];
+    double* d = (g == G - 1) ? d_fine : L.d;
+    STM_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * L.N, s));
+    for (int it = 0; it < nu1; ++it) {
+      stm_status st = vanka_step(H, g, r, d, transpose, it == 0, s);
+      if (st != STM_OK) return st;
+    }
+    // t = r - J d, restrict to the next coarser level
+    stm_status st = (nu1 > 0) ? jacobian_apply(H, g, d, r, L.t, 1, transpose, s) : vec_copy(L.t, r, L.N, s);
+    if (st != STM_OK) return st;
+    Level& Lc = H.L[g - 1];
+    {
+      ProfScope ps(&H, STM_KCLASS_TRANSFER, s, 0.0);
+      st = csr_apply(L.Rt_rowptr, L.Rt_col, L.Rt_val, Lc.N, L.t, nullptr, Lc.r, 0, s);
+    }
+    if (st != STM_OK) return st;
+    r = Lc.r;
+  }
+  // coarse solve
+  {
+    Level& L0 = H.L[0];
+    double* d0 = (G == 1) ? d_fine : L0.d;
+    stm_status st = coarse_apply(H, r, d0, transpose, s);
+    if (st != STM_OK) return st;
+  }
+  // ascend
+  for (int g = 1; g < G; ++g) {
+    Level& L = H.L[g];
+    double* d = (g == G - 1) ? d_fine : L.d;
+    const double* rg = (g == G - 1) ? r_fine : L.r;
+    stm_status st;
+    {
+      ProfScope ps(&H, STM_KCLASS_TRANSFER, s, 0.0);
+      st = csr_apply(L.P_rowptr, L.P_col, L.P_val, L.N, H.L[g - 1].d, nullptr, d, 2, s);
+    }
+    if (st != STM_OK) return st;
+    for (int it = 0; it < nu2; ++it) {
+      st = vanka_step(H, g, rg, d, transpose, false, s);
+      if (st != STM_OK) return st;
+    }
+  }
+  return STM_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Krylov helpers
+// ---------------------------------------------------------------------------------------------
+__global__ void k_fill(double* x, double v, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) x[i] = v;
+}
+stm_status vec_fill(double* x, double v, long long n, cudaStream_t s) {
+  k_fill<<<(int)std::min<long long>((n + 255) / 256, sms() * 8LL), 256, 0, s>>>(x, v, n); note_launch();
+  STM_CUDA(cudaGetLastError());
+  return STM_OK;
+}
+stm_status vec_copy(double* y, const double* x, long long n, cudaStream_t s) {
+  STM_CUDA(cudaMemcpyAsync(y, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  return STM_OK;
+}
+// y = x * scale[0] (inv = 0) or y = x / scale[0] (inv = 1)
+__global__ void k_scale_to(double* y, const double* x, const double* sc, int inv, long long n) {
+  const double f = inv ? 1.0 / sc[0] : sc[0];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) y[i] = x[i] * f;
+}
+stm_status vec_scale_to(double* y, const double* x, const double* sc, int inv, long long n, cudaStream_t s) {
+  k_scale_to<<<(int)std::min<long long>((n + 255) / 256, sms() * 8LL), 256, 0, s>>>(y, x, sc, inv, n); note_launch();
+  STM_CUDA(cudaGetLastError());
+  return STM_OK;
+}
+
+// part[v][blk] = partial sum of V[v] . w over the block's chunk; then out[v] = sum_blk part (fixed order)
+__global__ void k_dots_partial(const double* __restrict__ V, int nv, const double* __restrict__ w, long long n,
+                               double* __restrict__ part) {
+  __shared__ double red[32];
+  for (int v = 0; v < nv; ++v) {
+    const double* a = V + (long long)v * n;
+    double s = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+      s += a[i] * w[i];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+      for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+      if (threadIdx.x == 0) part[(long long)v * gridDim.x + blockIdx.x] = s;
+    }
+    __syncthreads();
+  }
+}
+__global__ void k_dots_final(const double* __restrict__ part, int nv, int nblk, double* __restrict__ out) {
+  const int v = blockIdx.x;
+  if (v >= nv) return;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[(long long)v * nblk + b];
+  __shared__ double red[32];
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (threadIdx.x == 0) out[v] = s;
+  }
+}
+stm_status batched_dots(const double* V, int nv, const double* w, long long n, double* out, double* part,
+                        int nblk, cudaStream_t s) {
+  k_dots_partial<<<nblk, 256, 0, s>>>(V, nv, w, n, part); note_launch();
+  k_dots_final<<<nv, 256, 0, s>>>(part, nv, nblk, out); note_launch();
+  STM_CUDA(cudaGetLastError());
+  return STM_OK;
+}
+stm_status vec_norm_sq(const double* x, long long n, double* out, double* part, int nblk, cudaStream_t s) {
+  return batched_dots(x, 1, x, n, out, part, nblk, s);
+}
+// w -= sum_v h[v] V[v]
+__global__ void k_batched_update(const double* __restrict__ V, int nv, const double* __restrict__ h,
+                                 double* __restrict__ w, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double s = w[i];
+    for (int v = 0; v < nv; ++v) s -= h[v] * V[(long long)v * n + i];
+    w[i] = s;
+  }
+}
+stm_status batched_update(const double* V, int nv, const double* h, double* w, long long n, cudaStream_t s) {
+  k_batched_update<<<(int)std::min<long long>((n + 255) / 256, sms() * 8LL), 256, 0, s>>>(V, nv, h, w, n); note_launch();
+  STM_CUDA(cudaGetLastError());
+  return STM_OK;
+}
+// x += sum_v y[v] Z[v]
+__global__ void k_gemv_acc(const double* __restrict__ Z, int nz, const double* __restrict__ y, double* __restrict__ x,
+                           long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double s = x[i];
+    for (int v = 0; v < nz; ++v) s += y[v] * Z[(long long)v * n + i];
+    x[i] = s;
+  }
+}
+stm_status gemv_accumulate(const double* Z, int nz, const double* y, double* x, long long n, cudaStream_t s) {
+  k_gemv_acc<<<(int)std::min<long long>((n + 255) / 256, sms() * 8LL), 256, 0, s>>>(Z, nz, y, x, n); note_launch();
+  STM_CUDA(cudaGetLastError());
+  return STM_OK;
+}
+__global__ void k_axpy_small(double* a, const double* b, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a[i] += b[i];
+}
+stm_status vec_axpby_dev(double* hacc, const double* h2, int n, cudaStream_t s) {
+  k_axpy_small<<<1, 256, 0, s>>>(hacc, h2, n); note_launch();
+  STM_CUDA(cudaGetLastError());
+  return STM_OK;
+}
+
+}  // namespace stm

@@ -1,0 +1,214 @@
+"""Python binding of libstm: the C-ABI calls with torch tensors as device buffers.
+
+Every method forwards to the entry point of the same name in include/stm.h; the binding only
+checks shapes/dtypes/devices and converts pointers. All arithmetic runs in libstm's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+
+
+def make_params(dim, k, n_levels, coarse_cells, length, obstacle_lo=(0, 0, 0), obstacle_hi=(0, 0, 0),
+                tau=0.01, nu=1e-3, gamma1=35.0, gamma2=35.0, inv_precision="f64", smoother="additive",
+                omega=0.7, nu1=2, nu2=2):
+    p = _lib.StmParams()
+    p.dim, p.k, p.n_levels = dim, k, n_levels
+    pad = lambda t, v: list(t) + [v] * (3 - len(t))
+    p.coarse_cells[:] = pad(coarse_cells, 1)
+    p.length[:] = pad(length, 1.0)
+    p.obstacle_lo[:] = pad(obstacle_lo, 0)
+    p.obstacle_hi[:] = pad(obstacle_hi, 0)
+    p.tau, p.nu, p.gamma1, p.gamma2 = tau, nu, gamma1, gamma2
+    p.inv_precision = _lib.PRECISION[inv_precision] if isinstance(inv_precision, str) else inv_precision
+    p.smoother = _lib.SMOOTHER[smoother] if isinstance(smoother, str) else smoother
+    p.omega, p.nu1, p.nu2 = omega, nu1, nu2
+    return p
+
+
+def _ptr(t, n=None, name="tensor"):
+    import torch
+
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA float64 tensor")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{name} has {t.numel()} entries, expected {n}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+class Hierarchy:
+    """Owner of one libstm hierarchy (all levels' matrices, inverses and work vectors)."""
+
+    def __init__(self, params: _lib.StmParams):
+        self.lib = _lib.load()
+        self.params = params
+        h = C.c_void_p()
+        _lib.check(self.lib.stm_build_hierarchy(C.byref(params), C.byref(h)), "stm_build_hierarchy")
+        self.h = h
+        self.n_levels = params.n_levels
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            self.lib.stm_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def finest(self):
+        return self.n_levels - 1
+
+    def sizes(self, level):
+        n, c, nl, nnz = C.c_longlong(), C.c_longlong(), C.c_int(), C.c_longlong()
+        _lib.check(self.lib.stm_sizes(self.h, level, C.byref(n), C.byref(c), C.byref(nl), C.byref(nnz)), "stm_sizes")
+        return dict(n_dofs=n.value, n_cells=c.value, n_local=nl.value, nnz=nnz.value)
+
+    def n_dofs(self, level=None):
+        return self.sizes(self.finest if level is None else level)["n_dofs"]
+
+    def dof_lattice_index(self, level=None):
+        level = self.finest if level is None else level
+        out = np.zeros(self.n_dofs(level), dtype=np.int64)
+        _lib.check(self.lib.stm_dof_lattice_index(self.h, level, out.ctypes.data_as(_lib._LP)), "stm_dof_lattice_index")
+        return out
+
+    def assemble_jacobian(self, X, nu=None, stream=None):
+        nu = self.params.nu if nu is None else nu
+        _lib.check(self.lib.stm_assemble_jacobian(self.h, _ptr(X, self.n_dofs(), "X"), nu, _stream(stream)),
+                   "stm_assemble_jacobian")
+
+    def factor_cells(self, stream=None):
+        bl, bc = C.c_int(), C.c_longlong()
+        st = self.lib.stm_factor_cells(self.h, _stream(stream), C.byref(bl), C.byref(bc))
+        if st != _lib.STM_OK:
+            err = _lib.StmError(st, "stm_factor_cells", (self.lib.stm_last_error() or b"").decode())
+            err.bad_level, err.bad_cell = bl.value, bc.value
+            raise err
+
+    def spmv(self, level, x, y, transpose=False, stream=None):
+        n = self.n_dofs(level)
+        _lib.check(self.lib.stm_spmv(self.h, level, _ptr(x, n, "x"), _ptr(y, n, "y"), int(transpose), _stream(stream)),
+                   "stm_spmv")
+
+    def vanka_sweep(self, level, r, d, transpose=False, stream=None):
+        n = self.n_dofs(level)
+        _lib.check(self.lib.stm_vanka_sweep(self.h, level, _ptr(r, n, "r"), _ptr(d, n, "d"), int(transpose),
+                                            _stream(stream)), "stm_vanka_sweep")
+
+    def restrict(self, level, fine, coarse, stream=None):
+        _lib.check(self.lib.stm_restrict(self.h, level, _ptr(fine, self.n_dofs(level), "fine"),
+                                         _ptr(coarse, self.n_dofs(level - 1), "coarse"), _stream(stream)), "stm_restrict")
+
+    def prolongate_add(self, level, coarse, fine, stream=None):
+        _lib.check(self.lib.stm_prolongate_add(self.h, level, _ptr(coarse, self.n_dofs(level - 1), "coarse"),
+                                               _ptr(fine, self.n_dofs(level), "fine"), _stream(stream)),
+                   "stm_prolongate_add")
+
+    def coarse_solve(self, r, d, transpose=False, stream=None):
+        n = self.n_dofs(0)
+        _lib.check(self.lib.stm_coarse_solve(self.h, _ptr(r, n, "r"), _ptr(d, n, "d"), int(transpose), _stream(stream)),
+                   "stm_coarse_solve")
+
+    def vcycle(self, r, d, transpose=False, stream=None):
+        n = self.n_dofs()
+        _lib.check(self.lib.stm_vcycle(self.h, _ptr(r, n, "r"), _ptr(d, n, "d"), int(transpose), _stream(stream)),
+                   "stm_vcycle")
+
+    @staticmethod
+    def _opts(restart, max_iter, rtol, transpose, use_x0):
+        o = _lib.GmresOpts()
+        o.restart, o.max_iter, o.transpose, o.use_x0, o.rtol = restart, max_iter, int(transpose), int(use_x0), rtol
+        return o
+
+    @staticmethod
+    def _info(inf):
+        return dict(iters=inf.iters, restarts=inf.restarts, converged=bool(inf.converged),
+                    rel_res_true=inf.rel_res_true, rel_res_est=inf.rel_res_est)
+
+    def gmres_solve(self, b, x, rtol=1e-10, restart=30, max_iter=1000, transpose=False, use_x0=False,
+                    stream=None, raise_on_fail=True):
+        n = self.n_dofs()
+        o = self._opts(restart, max_iter, rtol, transpose, use_x0)
+        inf = _lib.SolveInfo()
+        st = self.lib.stm_gmres_solve(self.h, _ptr(b, n, "b"), _ptr(x, n, "x"), C.byref(o), C.byref(inf),
+                                      _stream(stream))
+        info = self._info(inf)
+        info["status"] = _lib.STATUS_NAMES.get(st, st)
+        if st != _lib.STM_OK and raise_on_fail:
+            _lib.check(st, "stm_gmres_solve")
+        return info
+
+    def gmres_solve_host(self, b, x, rtol=1e-10, restart=30, max_iter=1000, transpose=False, use_x0=False,
+                         stream=None, raise_on_fail=True):
+        """b, x: host float64 arrays (numpy or CPU torch, ideally pinned) of n_dofs entries."""
+        n = self.n_dofs()
+        bp, xp = _host_ptr(b, n, "b"), _host_ptr(x, n, "x")
+        o = self._opts(restart, max_iter, rtol, transpose, use_x0)
+        inf = _lib.SolveInfo()
+        st = self.lib.stm_gmres_solve_host(self.h, bp, xp, C.byref(o), C.byref(inf), _stream(stream))
+        info = self._info(inf)
+        info["status"] = _lib.STATUS_NAMES.get(st, st)
+        if st != _lib.STM_OK and raise_on_fail:
+            _lib.check(st, "stm_gmres_solve_host")
+        return info
+
+    def profile_enable(self, enable=True):
+        _lib.check(self.lib.stm_profile_enable(self.h, int(enable)), "stm_profile_enable")
+
+    def profile_read(self, kernel_class):
+        """(total event ms, launches, algorithmic bytes) of one kernel class since profile_enable."""
+        ms, n, by = C.c_double(), C.c_longlong(), C.c_double()
+        cls = _lib.KCLASS[kernel_class] if isinstance(kernel_class, str) else kernel_class
+        _lib.check(self.lib.stm_profile_read(self.h, cls, C.byref(ms), C.byref(n), C.byref(by)), "stm_profile_read")
+        return dict(ms=ms.value, launches=n.value, bytes=by.value)
+
+    @staticmethod
+    def kernel_launches():
+        return int(_lib.load().stm_kernel_launches())
+
+    def copy_jacobian(self, level):
+        import scipy.sparse as sp
+
+        s = self.sizes(level)
+        rowptr = np.zeros(s["n_dofs"] + 1, dtype=np.int64)
+        col = np.zeros(s["nnz"], dtype=np.int32)
+        val = np.zeros(s["nnz"], dtype=np.float64)
+        _lib.check(self.lib.stm_copy_jacobian(self.h, level, rowptr.ctypes.data_as(_lib._LP),
+                                              col.ctypes.data_as(_lib._IP), val.ctypes.data_as(_lib._DP)),
+                   "stm_copy_jacobian")
+        return sp.csr_matrix((val, col, rowptr), shape=(s["n_dofs"], s["n_dofs"]))
+
+    def copy_cell_inverses(self, level):
+        s = self.sizes(level)
+        out = np.zeros((s["n_cells"], s["n_local"], s["n_local"]))
+        _lib.check(self.lib.stm_copy_cell_inverses(self.h, level, out.ctypes.data_as(_lib._DP)), "stm_copy_cell_inverses")
+        return out
+
+
+def _host_ptr(a, n, name):
+    import torch
+
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda or a.dtype != torch.float64 or not a.is_contiguous() or a.numel() != n:
+            raise ValueError(f"{name}: host contiguous float64 tensor of {n} entries expected")
+        return C.cast(C.c_void_p(a.data_ptr()), _lib._DP)
+    a = np.ascontiguousarray(a)
+    if a.dtype != np.float64 or a.size != n:
+        raise ValueError(f"{name}: float64 array of {n} entries expected")
+    return a.ctypes.data_as(_lib._DP)

@@ -1,0 +1,53 @@
+"""Shared builders for the parity tests: the same seeded workload on the oracle and on libstm."""
+import numpy as np
+
+import synth
+
+
+def oracle_hierarchy(wl, variant="additive", nu=None):
+    from oracle import solvers
+    return solvers.Hierarchy(wl, synth.linearisation_point(wl), nu=nu, variant=variant)
+
+
+def oracle_lattice_index(lev):
+    """Lattice-state index of every oracle DoF of `lev` (the documented numbering)."""
+    d, K = lev.dim, lev.k + 1
+    P = lev.P
+    W = d * P + lev.np_ * int(np.prod(lev.cells))
+    out = []
+    for l in range(K):
+        for i in range(d):
+            out.append(l * W + i * P + lev.lat_of_node)
+        out.append(l * W + d * P + (lev.active_full[:, None] * lev.np_ + np.arange(lev.np_)).ravel())
+    return np.concatenate(out)
+
+
+def gpu_params(wl, prec="f64", smoother="additive", **kw):
+    from paper_2107_10561_gb300 import make_params
+    args = dict(tau=wl.tau, nu=wl.nu, gamma1=wl.gamma1, gamma2=wl.gamma2, inv_precision=prec,
+                smoother=smoother, omega=wl.omega, nu1=wl.nu1, nu2=wl.nu2)
+    args.update(kw)
+    return make_params(wl.dim, wl.k, wl.n_levels, wl.coarse_cells, wl.length, wl.obstacle_lo, wl.obstacle_hi, **args)
+
+
+def gpu_hierarchy(wl, prec="f64", smoother="additive", factor=True, **kw):
+    import torch
+    from paper_2107_10561_gb300 import Hierarchy
+    h = Hierarchy(gpu_params(wl, prec, smoother, **kw))
+    X = lattice_to_gpu(h, synth.linearisation_point(wl))
+    h.assemble_jacobian(X)
+    if factor:
+        h.factor_cells()
+    torch.cuda.synchronize()
+    return h
+
+
+def lattice_to_gpu(h, state, level=None):
+    import torch
+    idx = h.dof_lattice_index(level)
+    return torch.from_numpy(np.ascontiguousarray(state.reshape(-1)[idx])).cuda()
+
+
+def rel_max(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
