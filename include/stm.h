@@ -164,6 +164,32 @@ stm_status stm_copy_jacobian(const stm_hierarchy* h, int level, long long* rowpt
                              int* colidx_host, double* val_host);
 stm_status stm_copy_cell_inverses(const stm_hierarchy* h, int level, double* inv_host);
 
+/* Additive Vanka correction that allocates nothing (the paper has no counterpart; this entry point
+ * exists for integration only).
+ *
+ * For callers that must not allocate device memory once they are running -- for example code
+ * whose device memory is owned by another component's pool allocator, or latency-critical loops
+ * that cannot afford the implicit device synchronisation of cudaMalloc/cudaFree. It needs no
+ * hierarchy: the caller passes every input and output, and the library allocates nothing.
+ *
+ * Computes, for all cells T at once (Eq. LocVanka, damped, combined additively):
+ *   d_i += omega * (1/m_i) * sum over the cells T containing i of (J_T^{-1} t_T)_i,
+ * with m_i the number of cells whose DoF list contains i (DoFs in no cell are left unchanged).
+ *   inv_dev : n_cells cell inverses, FP64, each n_local x n_local COLUMN-major, back to back
+ *   idx_dev : int32 [n_cells][n_local] global DoF of each local DoF (entries outside
+ *             [0, n_dofs) are ignored)
+ *   t_dev   : FP64 [n_dofs] residual r - J d;  d_dev: FP64 [n_dofs], updated in place
+ * Limits: n_dofs <= 1048576 (else STM_ERR_INVALID_ARG, nothing launched), 1 <= n_local <= 1024.
+ * Scratch: a fixed 16 MiB file-scope device array, present on every device that loads the library
+ * until the process exits. The first call on a device looks up that array's device address (with
+ * the device current); make that first call before any stream capture. Every call reuses the same
+ * array and clears the part it needs, so calls that overlap on the GPU (other streams, other host
+ * threads) race with each other and must be serialised by the caller. The shared-DoF sum uses
+ * FP64 atomics, so the result matches stm_vanka_sweep(additive) up to summation order. */
+stm_status stm_vanka_apply_noalloc(long long n_cells, int n_local, long long n_dofs, const double* inv_dev,
+                                   const int* idx_dev, const double* t_dev, double* d_dev, double omega,
+                                   void* stream);
+
 /* Measurement support (not part of the method). Kernel classes whose launches can be timed with
  * CUDA events recorded on the launching stream, and the algorithmic bytes each launch moves:
  *   VANKA_LOCAL   y_T = J_T^{-1} t_T over the cells of one launch: C (n^2 s + 20 n) bytes

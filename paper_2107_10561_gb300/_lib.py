@@ -55,6 +55,7 @@ SIGNATURES = {
     "stm_gmres_solve_host": ([_P, _DP, _DP, C.POINTER(GmresOpts), C.POINTER(SolveInfo), _P], _I),
     "stm_copy_jacobian": ([_P, _I, _LP, _IP, _DP], _I),
     "stm_copy_cell_inverses": ([_P, _I, _DP], _I),
+    "stm_vanka_apply_noalloc": ([_L, _I, _L, _P, _P, _P, _P, _D, _P], _I),
     "stm_profile_enable": ([_P, _I], _I),
     "stm_profile_read": ([_P, _I, _DP, _LP, _DP], _I),
     "stm_kernel_launches": ([], C.c_longlong),

@@ -201,6 +201,24 @@ class Hierarchy:
         return out
 
 
+def vanka_apply_noalloc(inv_colmajor, idx, t, d, omega, stream=None):
+    """Allocation-free additive Vanka correction (stm_vanka_apply_noalloc): d += omega W sum_T R_T^T J_T^{-1} t_T.
+
+    inv_colmajor: CUDA float64 [C, n, n] with inv_colmajor[c, j, i] = (J_T^{-1})_{ij};
+    idx: CUDA int32 [C, n]; t, d: CUDA float64 [N]. No device memory is allocated by the library.
+    """
+    import torch
+
+    lib = _lib.load()
+    C_, n, n2 = inv_colmajor.shape
+    if n != n2 or tuple(idx.shape) != (C_, n) or idx.dtype != torch.int32 or not idx.is_cuda or not idx.is_contiguous():
+        raise ValueError("inv must be [C, n, n] and idx a contiguous CUDA int32 [C, n]")
+    N = t.numel()
+    _lib.check(lib.stm_vanka_apply_noalloc(C_, n, N, _ptr(inv_colmajor, C_ * n * n, "inv"), C.c_void_p(idx.data_ptr()),
+                                           _ptr(t, N, "t"), _ptr(d, N, "d"), float(omega), _stream(stream)),
+               "stm_vanka_apply_noalloc")
+
+
 def _host_ptr(a, n, name):
     import torch
 
