@@ -177,14 +177,14 @@ stm_status stm_restrict(stm_hierarchy* h, int level, const double* fine, double*
   if (!h || !fine || !coarse) return bad_arg("NULL argument");
   STM_TRY(need_level(h->H, level, 1));
   Level& L = h->H.L[level];
-  return csr_apply(L.Rt_rowptr, L.Rt_col, L.Rt_val, h->H.L[level - 1].N, fine, nullptr, coarse, 0, S(stream));
+  return csr_apply(L.Rt_rowptr, L.Rt_col, L.Rt_val, h->H.L[level - 1].N, L.P_nnz, fine, nullptr, coarse, 0, S(stream));
 }
 
 stm_status stm_prolongate_add(stm_hierarchy* h, int level, const double* coarse, double* fine, void* stream) {
   if (!h || !fine || !coarse) return bad_arg("NULL argument");
   STM_TRY(need_level(h->H, level, 1));
   Level& L = h->H.L[level];
-  return csr_apply(L.P_rowptr, L.P_col, L.P_val, L.N, coarse, nullptr, fine, 2, S(stream));
+  return csr_apply(L.P_rowptr, L.P_col, L.P_val, L.N, L.P_nnz, coarse, nullptr, fine, 2, S(stream));
 }
 
 stm_status stm_coarse_solve(stm_hierarchy* h, const double* r, double* d, int transpose, void* stream) {
@@ -412,7 +412,8 @@ stm_status stm_copy_cell_inverses(const stm_hierarchy* h, int level, double* out
     return STM_ERR_STATE;
   }
   const Level& L = H.L[level];
-  const size_t nn2 = (size_t)L.n * L.n, tot = nn2 * L.C;
+  const InvLayout lay = inv_layout(L.n, H.p.inv_precision);
+  const size_t nn2 = (size_t)L.n * L.n, cs = (size_t)L.n * lay.ld, tot = cs * L.C;
   const int prec = H.p.inv_precision;
   const size_t es = prec == STM_F64 ? 8 : prec == STM_F32 ? 4 : 2;
   std::vector<unsigned char> raw(tot * es);
@@ -421,7 +422,7 @@ stm_status stm_copy_cell_inverses(const stm_hierarchy* h, int level, double* out
   for (size_t c = 0; c < (size_t)L.C; ++c)
     for (int j = 0; j < L.n; ++j)
       for (int i = 0; i < L.n; ++i) {
-        const size_t e = c * nn2 + (size_t)j * L.n + i;  // stored column-major
+        const size_t e = c * cs + (size_t)j * lay.ld + i;  // stored column-major, leading dimension ld
         double v;
         if (prec == STM_F64) {
           std::memcpy(&v, &raw[e * 8], 8);

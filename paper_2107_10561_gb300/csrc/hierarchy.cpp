@@ -600,6 +600,7 @@ static stm_status build_transfer(const Level& Cl, Level& F) {
         tval[dst] = pval[e];
       }
   }
+  F.P_nnz = (long long)pcol.size();
   STM_TRY(upload(&F.P_rowptr, prow));
   STM_TRY(upload(&F.P_col, pcol));
   STM_TRY(upload(&F.P_val, pval));

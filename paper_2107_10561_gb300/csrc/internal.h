@@ -106,6 +106,7 @@ struct Level {
 
   // transfer from level g-1 (coarse) to this level: P [N x N_c], P^T [N_c x N]
   long long* P_rowptr = nullptr; int* P_col = nullptr; double* P_val = nullptr;
+  long long P_nnz = 0;
   long long* Rt_rowptr = nullptr; int* Rt_col = nullptr; double* Rt_val = nullptr;
 
   // work vectors of the V-cycle
@@ -147,6 +148,14 @@ struct ProfScope {
   ~ProfScope();
 };
 
+// Storage of the cell inverses: column-major per cell with leading dimension ld >= n, ld a
+// multiple of the vector width used by the smoother (rows n..ld-1 are zero padding).
+struct InvLayout {
+  int ld;   // padded rows per column
+  int vb;   // bytes per vector load (16, 8 or 4)
+};
+InvLayout inv_layout(int n, int prec);
+
 // Host set-up (hierarchy.cpp)
 stm_status build_levels(Hierarchy& H);
 void free_hierarchy(Hierarchy& H);
@@ -162,7 +171,7 @@ stm_status factor_coarse(Hierarchy& H, cudaStream_t s);
 stm_status ensure_transpose(Hierarchy& H, int g, cudaStream_t s);
 
 // y = alpha*A x + beta_y*y (+ b): mode 0: y = A x; 1: y = b - A x; 2: y += A x
-stm_status csr_apply(const long long* rowptr, const int* col, const double* val, long long nrows,
+stm_status csr_apply(const long long* rowptr, const int* col, const double* val, long long nrows, long long nnz,
                      const double* x, const double* b, double* y, int mode, cudaStream_t s);
 stm_status jacobian_apply(Hierarchy& H, int g, const double* x, const double* b, double* y,
                           int mode, int transpose, cudaStream_t s);

@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(512) k_cell_inverse(
     const int* __restrict__ idx, const int* __restrict__ cell_nodes, const unsigned char* __restrict__ rank,
     const unsigned char* __restrict__ cellrank, const int* __restrict__ nn, const int* __restrict__ ncell,
     const long long* __restrict__ rowptr, const double* __restrict__ val, S* __restrict__ inv, int C, int d,
-    int nv, int np, int nt, int n, int* flag, long long* bad) {
+    int nv, int np, int nt, int n, int ld, int* flag, long long* bad) {
   extern __shared__ double sm[];
   double* A = sm;
   short* perm = reinterpret_cast<short*>(A + (size_t)n * n);
@@ -131,10 +131,10 @@ __global__ void __launch_bounds__(512) k_cell_inverse(
       __syncthreads();
       continue;
     }
-    S* out = inv + (size_t)c * n * n;
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-      const int j = e / n, i = e - j * n;  // column-major store: element (i, j) at j * n + i
-      out[e] = to_store<S>(A[i * n + j]);
+    S* out = inv + (size_t)c * n * ld;
+    for (int e = threadIdx.x; e < n * ld; e += blockDim.x) {
+      const int j = e / ld, i = e - j * ld;  // column-major store: element (i, j) at j * ld + i
+      out[e] = to_store<S>(i < n ? A[i * n + j] : 0.0);
     }
     __syncthreads();
   }
@@ -145,7 +145,8 @@ static size_t storage_bytes(int prec) { return prec == STM_F64 ? 8 : prec == STM
 stm_status factor_level(Hierarchy& H, int g, cudaStream_t s) {
   Level& L = H.L[g];
   const size_t nn2 = (size_t)L.n * L.n;
-  if (!L.inv) STM_CUDA(cudaMalloc(&L.inv, storage_bytes(H.p.inv_precision) * nn2 * L.C));
+  const InvLayout lay = inv_layout(L.n, H.p.inv_precision);
+  if (!L.inv) STM_CUDA(cudaMalloc(&L.inv, storage_bytes(H.p.inv_precision) * (size_t)L.n * lay.ld * L.C));
   const size_t smem = sizeof(double) * nn2 + sizeof(short) * L.n + 16;
   int dev = 0, maxsm = 0;
   STM_CUDA(cudaGetDevice(&dev));
@@ -163,7 +164,7 @@ stm_status factor_level(Hierarchy& H, int g, cudaStream_t s) {
     STM_CUDA(cudaFuncSetAttribute(k_cell_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
     k_cell_inverse<T><<<blocks, threads, smem, s>>>(L.idx, L.cell_nodes, L.rank, L.cellrank, L.nn, L.ncell,  \
                                                     L.rowptr, L.val, (T*)L.inv, L.C, L.dim, L.nv, L.np,     \
-                                                    L.nt, L.n, H.dflag, H.dbad); note_launch();                            \
+                                                    L.nt, L.n, lay.ld, H.dflag, H.dbad); note_launch();                            \
   } while (0)
   if (H.p.inv_precision == STM_F64) LAUNCH_INV(double);
   else if (H.p.inv_precision == STM_F32) LAUNCH_INV(float);

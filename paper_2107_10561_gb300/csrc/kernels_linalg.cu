@@ -18,19 +18,38 @@ static int sms() {
   return n;
 }
 
-// One warp per row. mode 0: y = A x; 1: y = b - A x; 2: y += A x.
+// VL lanes per row (VL = 1, 2, 4, 8, 16 or 32, chosen from the mean row length); values and column
+// indices are streamed once (cache-streaming loads), x stays cached. mode 0: y = A x;
+// 1: y = b - A x; 2: y += A x.
+template <int VL>
 __global__ void __launch_bounds__(256) k_csr(const long long* __restrict__ rowptr, const int* __restrict__ col,
                                              const double* __restrict__ val, long long nrows,
                                              const double* __restrict__ x, const double* __restrict__ b,
                                              double* __restrict__ y, int mode) {
-  const int lane = threadIdx.x & 31;
-  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
-  for (long long row = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < nrows; row += warps) {
-    const long long e0 = rowptr[row], e1 = rowptr[row + 1];
-    double s = 0.0;
-    for (long long e = e0 + lane; e < e1; e += 32) s += __ldg(val + e) * __ldg(x + __ldg(col + e));
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-    if (lane == 0) {
+  // The row loop is uniform across each warp (a warp owns 32/VL consecutive rows per step), so the
+  // full-mask shuffles below always see all 32 lanes.
+  constexpr int GPW = 32 / VL;
+  const int lane = threadIdx.x & (VL - 1);
+  const int gw = (threadIdx.x & 31) / VL;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long wb = warp * GPW; wb < nrows; wb += nwarps * GPW) {
+    const long long row = wb + gw;
+    const bool ok = row < nrows;
+    const long long e0 = ok ? rowptr[row] : 0, e1 = ok ? rowptr[row + 1] : 0;
+    double s0 = 0.0, s1 = 0.0;
+    long long e = e0 + lane;
+    for (; e + VL < e1; e += 2 * VL) {
+      const double v0 = __ldcs(val + e), v1 = __ldcs(val + e + VL);
+      const int c0 = __ldcs(col + e), c1 = __ldcs(col + e + VL);
+      s0 += v0 * __ldg(x + c0);
+      s1 += v1 * __ldg(x + c1);
+    }
+    if (e < e1) s0 += __ldcs(val + e) * __ldg(x + __ldcs(col + e));
+    double s = s0 + s1;
+#pragma unroll
+    for (int off = VL / 2; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off, VL);
+    if (ok && lane == 0) {
       if (mode == 0) y[row] = s;
       else if (mode == 1) y[row] = b[row] - s;
       else y[row] += s;
@@ -38,10 +57,23 @@ __global__ void __launch_bounds__(256) k_csr(const long long* __restrict__ rowpt
   }
 }
 
-stm_status csr_apply(const long long* rowptr, const int* col, const double* val, long long nrows,
+stm_status csr_apply(const long long* rowptr, const int* col, const double* val, long long nrows, long long nnz,
                      const double* x, const double* b, double* y, int mode, cudaStream_t s) {
-  const int blocks = (int)std::min<long long>((nrows + 7) / 8, (long long)sms() * 16);
-  k_csr<<<blocks, 256, 0, s>>>(rowptr, col, val, nrows, x, b, y, mode); note_launch();
+  if (nrows <= 0) return STM_OK;
+  const double mean = (double)nnz / (double)nrows;
+  int VL = 1;
+  while (VL < 32 && VL < mean * 0.75) VL *= 2;
+  const long long threads_needed = nrows * VL;
+  const int blocks = (int)std::min<long long>((threads_needed + 255) / 256, (long long)sms() * 8);
+  switch (VL) {
+    case 1: k_csr<1><<<blocks, 256, 0, s>>>(rowptr, col, val, nrows, x, b, y, mode); break;
+    case 2: k_csr<2><<<blocks, 256, 0, s>>>(rowptr, col, val, nrows, x, b, y, mode); break;
+    case 4: k_csr<4><<<blocks, 256, 0, s>>>(rowptr, col, val, nrows, x, b, y, mode); break;
+    case 8: k_csr<8><<<blocks, 256, 0, s>>>(rowptr, col, val, nrows, x, b, y, mode); break;
+    case 16: k_csr<16><<<blocks, 256, 0, s>>>(rowptr, col, val, nrows, x, b, y, mode); break;
+    default: k_csr<32><<<blocks, 256, 0, s>>>(rowptr, col, val, nrows, x, b, y, mode); break;
+  }
+  note_launch();
   STM_CUDA(cudaGetLastError());
   return STM_OK;
 }
@@ -98,7 +130,7 @@ stm_status jacobian_apply(Hierarchy& H, int g, const double* x, const double* b,
     v = L.valT;
   }
   ProfScope ps(&H, STM_KCLASS_JACOBIAN_SPMV, s, 8.0 * (double)L.nnz + 24.0 * (double)L.N);
-  return csr_apply(L.rowptr, L.colidx, v, L.N, x, b, y, mode, s);
+  return csr_apply(L.rowptr, L.colidx, v, L.N, L.nnz, x, b, y, mode, s);
 }
 
 // Dense coarse solve: d = Cinv r (row-major) or d = Cinv^T r.
@@ -157,7 +189,7 @@ stm_status vcycle(Hierarchy& H, const double* r_fine, double* d_fine, int transp
     Level& Lc = H.L[g - 1];
     {
       ProfScope ps(&H, STM_KCLASS_TRANSFER, s, 0.0);
-      st = csr_apply(L.Rt_rowptr, L.Rt_col, L.Rt_val, Lc.N, L.t, nullptr, Lc.r, 0, s);
+      st = csr_apply(L.Rt_rowptr, L.Rt_col, L.Rt_val, Lc.N, L.P_nnz, L.t, nullptr, Lc.r, 0, s);
     }
     if (st != STM_OK) return st;
     r = Lc.r;
@@ -177,7 +209,7 @@ stm_status vcycle(Hierarchy& H, const double* r_fine, double* d_fine, int transp
     stm_status st;
     {
       ProfScope ps(&H, STM_KCLASS_TRANSFER, s, 0.0);
-      st = csr_apply(L.P_rowptr, L.P_col, L.P_val, L.N, H.L[g - 1].d, nullptr, d, 2, s);
+      st = csr_apply(L.P_rowptr, L.P_col, L.P_val, L.N, L.P_nnz, H.L[g - 1].d, nullptr, d, 2, s);
     }
     if (st != STM_OK) return st;
     for (int it = 0; it < nu2; ++it) {

@@ -1,8 +1,11 @@
 // Cell-based space-time Vanka smoother (Sec. 4.2, Eq. LocVanka, damping of Sec. 5.3).
 //
 // Local step for cell T: y_T = J_T^{-1} t_T with t = r - J d gathered over all (k+1) time nodes
-// of the cell's DoFs. The inverse is streamed once per sweep (the dominant HBM traffic), stored
-// column-major per cell so that consecutive threads read consecutive rows of one column.
+// of the cell's DoFs. The inverses are the dominant HBM stream of the whole solve. Each cell's
+// inverse is stored column-major with its rows padded to a multiple of the vector width, so a
+// thread owns a fixed chunk of V consecutive rows and walks the columns with aligned 16/8/4-byte
+// vector loads: consecutive threads read consecutive memory, every load is fully used, no
+// per-element reductions. Small cells are packed several per CTA to keep enough loads in flight.
 // Shared DoFs are combined in a second, deterministic pass:
 //   additive : d_i += omega / m_i * sum over the owners of i of y_T[alpha]
 //   overwrite: d_i += omega * y_Tlast[alpha] (highest-index owning cell, "last update wins")
@@ -14,68 +17,181 @@ namespace stm {
 template <typename S> struct Acc { using T = float; };
 template <> struct Acc<double> { using T = double; };
 
-template <typename S> __device__ __forceinline__ float ld_f(const S* p);
-template <> __device__ __forceinline__ float ld_f<float>(const float* p) { return __ldg(p); }
-template <> __device__ __forceinline__ float ld_f<__nv_bfloat16>(const __nv_bfloat16* p) {
-  return __bfloat162float(*p);
-}
-__device__ __forceinline__ double ld_d(const double* p) { return __ldg(p); }
+static int storage_size(int prec) { return prec == STM_F64 ? 8 : prec == STM_F32 ? 4 : 2; }
 
-// One CTA per cell (grid-stride). Threads are split into G column groups of n rows: thread
-// (g, i) accumulates sum_{j = g (mod G)} Inv[j][i] t_j (forward) and the G partial sums are added
-// in shared memory. transpose = 1 computes y = Inv^T t: each warp owns whole columns.
+InvLayout inv_layout(int n, int prec) {
+  const int s = storage_size(prec);
+  for (int vb = 16; vb >= 4; vb /= 2) {
+    const int V = vb / s;
+    if (V < 1) break;
+    const int ld = (n + V - 1) / V * V;
+    if (vb == 4 || ld * 100 <= n * 106) return InvLayout{ld, vb};
+  }
+  return InvLayout{n, s};
+}
+
+// Thread geometry of the forward kernel for one level.
+struct VGeom {
+  int n, ld, LDV, Q, T, P;
+};
+
+static VGeom vanka_geometry(int n, InvLayout lay, int prec) {
+  VGeom g;
+  g.n = n;
+  g.ld = lay.ld;
+  g.LDV = lay.ld / (lay.vb / storage_size(prec));
+  if (g.LDV >= 64) {
+    g.Q = std::max(1, 256 / g.LDV);
+  } else {
+    g.Q = std::max(1, 32 / g.LDV);
+  }
+  g.T = g.LDV * g.Q;
+  g.P = std::max(1, 256 / g.T);
+  return g;
+}
+
+// Loads VB bytes (VB / sizeof(S) elements) and converts them to the accumulation type.
+template <typename S, int VB> struct VecLoad;
+template <> struct VecLoad<double, 16> {
+  static constexpr int V = 2;
+  __device__ static void load(const double* p, double* o) {
+    const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+    o[0] = v.x;
+    o[1] = v.y;
+  }
+};
+template <> struct VecLoad<double, 8> {
+  static constexpr int V = 1;
+  __device__ static void load(const double* p, double* o) { o[0] = __ldg(p); }
+};
+template <> struct VecLoad<float, 16> {
+  static constexpr int V = 4;
+  __device__ static void load(const float* p, float* o) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  }
+};
+template <> struct VecLoad<float, 8> {
+  static constexpr int V = 2;
+  __device__ static void load(const float* p, float* o) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    o[0] = v.x; o[1] = v.y;
+  }
+};
+template <> struct VecLoad<float, 4> {
+  static constexpr int V = 1;
+  __device__ static void load(const float* p, float* o) { o[0] = __ldg(p); }
+};
+__device__ __forceinline__ void bf16x2_to_f32(unsigned u, float* o) {
+  o[0] = __uint_as_float(u << 16);
+  o[1] = __uint_as_float(u & 0xffff0000u);
+}
+template <> struct VecLoad<__nv_bfloat16, 16> {
+  static constexpr int V = 8;
+  __device__ static void load(const __nv_bfloat16* p, float* o) {
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
+    bf16x2_to_f32(v.x, o); bf16x2_to_f32(v.y, o + 2); bf16x2_to_f32(v.z, o + 4); bf16x2_to_f32(v.w, o + 6);
+  }
+};
+template <> struct VecLoad<__nv_bfloat16, 8> {
+  static constexpr int V = 4;
+  __device__ static void load(const __nv_bfloat16* p, float* o) {
+    const uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
+    bf16x2_to_f32(v.x, o); bf16x2_to_f32(v.y, o + 2);
+  }
+};
+template <> struct VecLoad<__nv_bfloat16, 4> {
+  static constexpr int V = 2;
+  __device__ static void load(const __nv_bfloat16* p, float* o) {
+    bf16x2_to_f32(__ldg(reinterpret_cast<const unsigned*>(p)), o);
+  }
+};
+
+// Forward local solves y_T = Inv_T t_T for the cells of `cell_list` (all cells if NULL).
+// CTA = P cell slots of T threads; thread (rc, cg) of a slot accumulates rows rc*V..rc*V+V-1 over
+// the columns j = cg (mod Q); the Q partial sums of a row are added through shared memory.
+template <typename S, int VB>
+__global__ void __launch_bounds__(256) k_vanka_local(const S* __restrict__ inv, const int* __restrict__ idx,
+                                                     const double* __restrict__ t, double* __restrict__ Y,
+                                                     const int* __restrict__ cell_list, int ncells, VGeom g,
+                                                     double* __restrict__ d_scatter, double omega) {
+  using A = typename Acc<S>::T;
+  using L = VecLoad<S, VB>;
+  constexpr int V = L::V;
+  extern __shared__ double smd[];
+  A* tl = reinterpret_cast<A*>(smd);      // [P][n]
+  A* part = tl + g.P * g.n;               // [P][Q][ld]
+  const int slot = threadIdx.x / g.T;
+  const int lt = threadIdx.x - slot * g.T;
+  const int rc = lt % g.LDV, cg = lt / g.LDV;
+  for (int base = blockIdx.x * g.P; base < ncells; base += gridDim.x * g.P) {
+    const int ci = base + slot;
+    const bool has = slot < g.P && ci < ncells;
+    const int c = has ? (cell_list ? cell_list[ci] : ci) : 0;
+    const int* ic = idx + (long long)c * g.n;
+    __syncthreads();
+    if (has)
+      for (int i = lt; i < g.n; i += g.T) tl[slot * g.n + i] = (A)t[ic[i]];
+    __syncthreads();
+    if (has) {
+      A acc[V];
+#pragma unroll
+      for (int v = 0; v < V; ++v) acc[v] = 0;
+      const S* M = inv + (size_t)c * g.n * g.ld + rc * V;
+      const A* tc = tl + slot * g.n;
+#pragma unroll 4
+      for (int j = cg; j < g.n; j += g.Q) {
+        A e[V];
+        L::load(M + (size_t)j * g.ld, e);
+        const A tj = tc[j];
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] += e[v] * tj;
+      }
+      A* pp = part + (slot * g.Q + cg) * g.ld + rc * V;
+#pragma unroll
+      for (int v = 0; v < V; ++v) pp[v] = acc[v];
+    }
+    __syncthreads();
+    if (has)
+      for (int i = lt; i < g.n; i += g.T) {
+        A y = 0;
+        for (int q = 0; q < g.Q; ++q) y += part[(slot * g.Q + q) * g.ld + i];
+        if (d_scatter) d_scatter[ic[i]] += omega * (double)y;
+        else Y[(long long)c * g.n + i] = (double)y;
+      }
+  }
+}
+
+// Transposed local solves y_T = Inv_T^T t_T (adjoint smoother): one warp per column, a dot product
+// of the column with t_T.
 template <typename S>
-__global__ void __launch_bounds__(256) k_vanka_local(
-    const S* __restrict__ inv, const int* __restrict__ idx, const double* __restrict__ t,
-    double* __restrict__ Y, const int* __restrict__ cell_list, int ncells, int n, int G,
-    int transpose, double* __restrict__ d_scatter, double omega) {
+__global__ void __launch_bounds__(256) k_vanka_local_t(const S* __restrict__ inv, const int* __restrict__ idx,
+                                                       const double* __restrict__ t, double* __restrict__ Y,
+                                                       const int* __restrict__ cell_list, int ncells, int n, int ld,
+                                                       double* __restrict__ d_scatter, double omega) {
   using A = typename Acc<S>::T;
   extern __shared__ double smd[];
-  double* tl = smd;                                 // [n]
-  A* part = reinterpret_cast<A*>(smd + n);          // [G][n]
-  const int tid = threadIdx.x;
+  double* tl = smd;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int ci = blockIdx.x; ci < ncells; ci += gridDim.x) {
     const int c = cell_list ? cell_list[ci] : ci;
     const int* ic = idx + (long long)c * n;
     __syncthreads();
-    for (int i = tid; i < n; i += blockDim.x) tl[i] = t[ic[i]];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) tl[i] = t[ic[i]];
     __syncthreads();
-    const S* M = inv + (size_t)c * n * n;
-    if (!transpose) {
-      if (tid < G * n) {
-        const int g = tid / n, i = tid - g * n;
-        A acc = 0;
-        const S* col = M + (size_t)g * n + i;
-        const size_t stride = (size_t)G * n;
-        int j = g;
-#pragma unroll 4
-        for (; j < n; j += G, col += stride) {
-          if constexpr (sizeof(S) == 8) acc += ld_d((const double*)col) * tl[j];
-          else acc += ld_f<S>(col) * (A)tl[j];
-        }
-        part[g * n + i] = acc;
+    const S* M = inv + (size_t)c * n * ld;
+    for (int j = wid; j < n; j += nw) {
+      const S* col = M + (size_t)j * ld;
+      A acc = 0;
+      for (int i = lane; i < n; i += 32) {
+        if constexpr (sizeof(S) == 8) acc += __ldg((const double*)(col + i)) * tl[i];
+        else if constexpr (sizeof(S) == 4) acc += __ldg((const float*)(col + i)) * (A)tl[i];
+        else acc += __bfloat162float(col[i]) * (A)tl[i];
       }
-      __syncthreads();
-      for (int i = tid; i < n; i += blockDim.x) {
-        A y = 0;
-        for (int g = 0; g < G; ++g) y += part[g * n + i];
-        if (d_scatter) d_scatter[ic[i]] += omega * (double)y;
-        else Y[(long long)c * n + i] = (double)y;
-      }
-    } else {
-      const int lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-      for (int j = wid; j < n; j += nw) {
-        const S* col = M + (size_t)j * n;
-        A acc = 0;
-        for (int i = lane; i < n; i += 32) {
-          if constexpr (sizeof(S) == 8) acc += ld_d((const double*)(col + i)) * tl[i];
-          else acc += ld_f<S>(col + i) * (A)tl[i];
-        }
-        for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-        if (lane == 0) {
-          if (d_scatter) d_scatter[ic[j]] += omega * (double)acc;
-          else Y[(long long)c * n + j] = (double)acc;
-        }
+      for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+      if (lane == 0) {
+        if (d_scatter) d_scatter[ic[j]] += omega * (double)acc;
+        else Y[(long long)c * n + j] = (double)acc;
       }
     }
   }
@@ -108,25 +224,47 @@ static int sm_count() {
   return n;
 }
 
+template <typename S>
+static void launch_fwd(const Level& L, const void* inv, int vb, const VGeom& g, const double* t, const int* cells,
+                       int nc, double* scatter, double omega, cudaStream_t s) {
+  using A = typename Acc<S>::T;
+  const size_t smem = sizeof(A) * ((size_t)g.P * g.n + (size_t)g.P * g.Q * g.ld) + 16;
+  const int groups = (nc + g.P - 1) / g.P;
+  const int blocks = std::min(groups, sm_count() * 8);
+  const int threads = g.T * g.P;
+  if (vb == 16) {
+    k_vanka_local<S, 16><<<blocks, threads, smem, s>>>((const S*)inv, L.idx, t, L.Y, cells, nc, g, scatter, omega);
+  } else if (vb == 8 || sizeof(S) == 8) {
+    k_vanka_local<S, 8><<<blocks, threads, smem, s>>>((const S*)inv, L.idx, t, L.Y, cells, nc, g, scatter, omega);
+  } else if constexpr (sizeof(S) < 8) {
+    k_vanka_local<S, 4><<<blocks, threads, smem, s>>>((const S*)inv, L.idx, t, L.Y, cells, nc, g, scatter, omega);
+  }
+}
+
 static stm_status launch_local(Hierarchy& H, Level& L, const double* t, const int* cells, int nc,
                                int transpose, double* scatter, cudaStream_t s) {
   if (nc <= 0) return STM_OK;
-  const int threads = 256;
-  const int G = std::max(1, threads / L.n);
   const int prec = H.p.inv_precision;
-  const size_t smem = sizeof(double) * L.n + (prec == STM_F64 ? 8 : 4) * (size_t)G * L.n + 16;
-  const int blocks = std::min(nc, sm_count() * 8);
-  ProfScope ps(&H, STM_KCLASS_VANKA_LOCAL, s,
-               (double)nc * ((double)L.n * L.n * (prec == STM_F64 ? 8 : prec == STM_F32 ? 4 : 2) + 20.0 * L.n));
-  if (prec == STM_F64) {
-    k_vanka_local<double><<<blocks, threads, smem, s>>>((const double*)L.inv, L.idx, t, L.Y, cells, nc, L.n, G,
-                                                        transpose, scatter, H.p.omega);
-  } else if (prec == STM_F32) {
-    k_vanka_local<float><<<blocks, threads, smem, s>>>((const float*)L.inv, L.idx, t, L.Y, cells, nc, L.n, G,
-                                                       transpose, scatter, H.p.omega);
+  const InvLayout lay = inv_layout(L.n, prec);
+  ProfScope ps(&H, STM_KCLASS_VANKA_LOCAL, s, (double)nc * ((double)L.n * L.n * storage_size(prec) + 20.0 * L.n));
+  const double omega = H.p.omega;
+  if (!transpose) {
+    const VGeom g = vanka_geometry(L.n, lay, prec);
+    if (prec == STM_F64) launch_fwd<double>(L, L.inv, lay.vb, g, t, cells, nc, scatter, omega, s);
+    else if (prec == STM_F32) launch_fwd<float>(L, L.inv, lay.vb, g, t, cells, nc, scatter, omega, s);
+    else launch_fwd<__nv_bfloat16>(L, L.inv, lay.vb, g, t, cells, nc, scatter, omega, s);
   } else {
-    k_vanka_local<__nv_bfloat16><<<blocks, threads, smem, s>>>((const __nv_bfloat16*)L.inv, L.idx, t, L.Y, cells,
-                                                               nc, L.n, G, transpose, scatter, H.p.omega);
+    const int blocks = std::min(nc, sm_count() * 8);
+    const size_t smem = sizeof(double) * L.n + 16;
+    if (prec == STM_F64)
+      k_vanka_local_t<double><<<blocks, 256, smem, s>>>((const double*)L.inv, L.idx, t, L.Y, cells, nc, L.n, lay.ld,
+                                                        scatter, omega);
+    else if (prec == STM_F32)
+      k_vanka_local_t<float><<<blocks, 256, smem, s>>>((const float*)L.inv, L.idx, t, L.Y, cells, nc, L.n, lay.ld,
+                                                       scatter, omega);
+    else
+      k_vanka_local_t<__nv_bfloat16><<<blocks, 256, smem, s>>>((const __nv_bfloat16*)L.inv, L.idx, t, L.Y, cells, nc,
+                                                               L.n, lay.ld, scatter, omega);
   }
   note_launch();
   STM_CUDA(cudaGetLastError());
@@ -162,7 +300,8 @@ stm_status vanka_step(Hierarchy& H, int g, const double* r, double* d, int trans
   const int blocks = (int)std::min<long long>((L.N + 255) / 256, sm_count() * 16LL);
   ProfScope ps(&H, STM_KCLASS_VANKA_COMBINE, s, 0.0);
   k_vanka_gather<<<blocks, 256, 0, s>>>(d, L.Y, L.own_ptr, L.own_pos, L.last_owner, L.wmult, L.N, omega,
-                                        H.p.smoother == STM_VANKA_PAPER_OVERWRITE); note_launch();
+                                        H.p.smoother == STM_VANKA_PAPER_OVERWRITE);
+  note_launch();
   STM_CUDA(cudaGetLastError());
   return STM_OK;
 }
