@@ -458,6 +458,12 @@ static stm_status build_level(const stm_params& p, int g, Level& L, std::vector<
   }
   for (int col = (1 << d); col < 9; ++col) L.colour_off[col] = (int)colour_cells.size();
 
+  std::vector<int> job_nodes(R);
+  std::iota(job_nodes.begin(), job_nodes.end(), 0);
+  std::stable_sort(job_nodes.begin(), job_nodes.end(), [&](int a, int b) {
+    return nn[a] != nn[b] ? nn[a] < nn[b] : ncell[a] < ncell[b];
+  });
+  STM_TRY(upload(&L.job_nodes, job_nodes));
   STM_TRY(upload(&L.idx, idx));
   STM_TRY(upload(&L.cell_nodes, L.h_cell_nodes));
   STM_TRY(upload(&L.bmask, bmask));
@@ -618,15 +624,12 @@ stm_status build_levels(Hierarchy& H) {
   for (int g = 0; g < G; ++g) {
     std::vector<int> nbr_ptr, nbr, node_cells;
     STM_TRY(build_level(p, g, H.L[g], &nbr_ptr, &nbr, &node_cells));
-    int *d_ptr = nullptr, *d_nbr = nullptr, *d_nc = nullptr;
-    STM_TRY(upload(&d_ptr, nbr_ptr));
-    STM_TRY(upload(&d_nbr, nbr));
-    STM_TRY(upload(&d_nc, node_cells));
-    stm_status st = launch_fill_colidx(H.L[g], d_ptr, d_nbr, d_nc, 0);
-    cudaDeviceSynchronize();
-    cudaFree(d_ptr);
-    cudaFree(d_nbr);
-    cudaFree(d_nc);
+    Level& L = H.L[g];
+    STM_TRY(upload(&L.nbr_ptr, nbr_ptr));
+    STM_TRY(upload(&L.nbr, nbr));
+    STM_TRY(upload(&L.node_cells, node_cells));
+    stm_status st = launch_fill_colidx(L, L.nbr_ptr, L.nbr, L.node_cells, 0);
+    STM_CUDA(cudaDeviceSynchronize());
     if (st != STM_OK) return st;
     if (g > 0) STM_TRY(build_transfer(H.L[g - 1], H.L[g]));
   }
@@ -655,7 +658,8 @@ stm_status build_levels(Hierarchy& H) {
 
 void free_hierarchy(Hierarchy& H) {
   for (Level& L : H.L) {
-    void* ptrs[] = {L.idx, L.cell_nodes, L.bmask, L.rank, L.cellrank, L.nn, L.ncell, L.rowptr,
+    void* ptrs[] = {L.idx, L.cell_nodes, L.bmask, L.rank, L.cellrank, L.nn, L.ncell, L.rowptr, L.nbr_ptr, L.nbr,
+                    L.node_cells, L.job_nodes,
                     L.colidx, L.val, L.valT, L.ref, L.inj, L.wnod, L.inv, L.wmult, L.own_ptr,
                     L.own_pos, L.last_owner, L.colour_cells, L.Y, L.P_rowptr, L.P_col, L.P_val,
                     L.Rt_rowptr, L.Rt_col, L.Rt_val, L.d, L.r, L.t};

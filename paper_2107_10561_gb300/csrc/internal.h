@@ -83,6 +83,10 @@ struct Level {
   unsigned char* rank = nullptr;  // [C][nv][nv] rank of node j in the neighbour list of node i
   unsigned char* cellrank = nullptr; // [C][nv] rank of the cell among the cells of node i
   int* nn = nullptr;              // [R] number of neighbour nodes
+  int* nbr_ptr = nullptr;         // [R+1] neighbour lists (sorted node ids)
+  int* nbr = nullptr;
+  int* node_cells = nullptr;      // [R][2^d] cells containing each node, sorted, -1 padded
+  int* job_nodes = nullptr;       // [R] node ids ordered by (neighbour count, cell count, id)
   int* ncell = nullptr;           // [R] number of cells containing the node
   long long* rowptr = nullptr;    // [N+1]
   int* colidx = nullptr;          // [nnz]
@@ -173,6 +177,8 @@ stm_status ensure_transpose(Hierarchy& H, int g, cudaStream_t s);
 // y = alpha*A x + beta_y*y (+ b): mode 0: y = A x; 1: y = b - A x; 2: y += A x
 stm_status csr_apply(const long long* rowptr, const int* col, const double* val, long long nrows, long long nnz,
                      const double* x, const double* b, double* y, int mode, cudaStream_t s);
+stm_status spmv_structured(const Level& L, const double* v, const double* x, const double* b, double* y, int mode,
+                           cudaStream_t s);
 stm_status jacobian_apply(Hierarchy& H, int g, const double* x, const double* b, double* y,
                           int mode, int transpose, cudaStream_t s);
 stm_status vanka_step(Hierarchy& H, int g, const double* r, double* d, int transpose,

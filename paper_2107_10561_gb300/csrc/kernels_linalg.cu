@@ -130,7 +130,7 @@ stm_status jacobian_apply(Hierarchy& H, int g, const double* x, const double* b,
     v = L.valT;
   }
   ProfScope ps(&H, STM_KCLASS_JACOBIAN_SPMV, s, 8.0 * (double)L.nnz + 24.0 * (double)L.N);
-  return csr_apply(L.rowptr, L.colidx, v, L.N, L.nnz, x, b, y, mode, s);
+  return spmv_structured(L, v, x, b, y, mode, s);
 }
 
 // Dense coarse solve: d = Cinv r (row-major) or d = Cinv^T r.

@@ -1,0 +1,217 @@
+// Structured product with the slab Jacobian J_g (FP64): y = J x, y = b - J x or y += J x.
+//
+// Every velocity row (a, l, i) of J couples node i with the same neighbour list nbr(i) in every
+// (time b, component m) block, plus the pressures of the cells around i at time a (Problem 3.1,
+// Eq. newton_system_matrix_dG_1 with a diagonal time mass). A VL-lane group therefore takes one
+// node and computes all K*d of its velocity rows together: each neighbour's K*d entries of x are
+// loaded once and reused by all K*d rows, and the column indices are never read (the values are
+// addressed through the row pointers and the neighbour list). Pressure rows (a, cell, q) are
+// taken one cell per group, all K*n_p rows at once. Values are streamed (cache-streaming loads).
+// FP64 issue slots are the limit on this part (one FP64 warp instruction every ~17 cycles per SM).
+// A group (16 lanes in 2D, 32 in 3D) walks the flattened positions of its rows, so each step reads
+// whole 128-byte lines of every row and few lanes idle; the rows' partial sums are combined by a
+// reduce-scatter butterfly (few FP64 adds); node jobs are ordered by neighbour count (job_nodes) so
+// that the groups of one warp run equal trip counts.
+// Results equal the plain CSR product up to FP64 summation order.
+#include "internal.h"
+
+namespace stm {
+
+__host__ __device__ constexpr int pow2ceil(int v) { return v <= 1 ? 1 : 2 * pow2ceil((v + 1) / 2); }
+
+// Reduce-scatter over the VL lanes of a group: on entry every lane holds NA partial sums; on exit
+// acc[0] of lane L holds the full group sum of accumulator scatter_index(L). Each halving step
+// trades half of the accumulators with the partner lane, so the FP64 adds total NA - 1 + the
+// remaining log2(VL/NA) steps instead of NA * log2(VL).
+template <int VL, int NA>
+__device__ __forceinline__ void reduce_scatter(double* acc, int lane) {
+  static_assert(NA <= VL, "one accumulator per lane at most");
+  int cnt = NA;
+#pragma unroll
+  for (int off = VL / 2; off >= 1; off >>= 1) {
+    if (cnt > 1) {
+      const int half = cnt / 2;
+      const bool upper = (lane & off) != 0;
+#pragma unroll
+      for (int k = 0; k < NA / 2; ++k) {
+        if (k < half) {
+          const double send = upper ? acc[k] : acc[k + half];
+          const double keep = upper ? acc[k + half] : acc[k];
+          acc[k] = keep + __shfl_xor_sync(0xffffffffu, send, off, VL);
+        }
+      }
+      cnt = half;
+    } else {
+      acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], off, VL);
+    }
+  }
+}
+template <int VL, int NA>
+__device__ __forceinline__ int scatter_index(int lane, int* writer_mask) {
+  int cnt = NA, k = 0, wm = 0;
+#pragma unroll
+  for (int off = VL / 2; off >= 1; off >>= 1) {
+    if (cnt > 1) {
+      const int half = cnt / 2;
+      if (lane & off) k += half;
+      cnt = half;
+    } else {
+      wm |= off;
+    }
+  }
+  *writer_mask = wm;
+  return k;
+}
+
+template <int VL, int K, int D>
+__global__ void __launch_bounds__(256) k_spmv_struct(
+    const long long* __restrict__ rowptr, const double* __restrict__ val, const int* __restrict__ nbr_ptr,
+    const int* __restrict__ nbr, const int* __restrict__ ncell, const int* __restrict__ node_cells,
+    const int* __restrict__ cell_nodes, const int* __restrict__ job_nodes, long long block, int R, int C, int nv,
+    const double* __restrict__ x, const double* __restrict__ b, double* __restrict__ y, int mode) {
+  constexpr int GPW = 32 / VL;
+  constexpr int KD = K * D;
+  constexpr int NP = D + 1;  // P1 pressure modes per cell
+  constexpr int KP = K * NP;
+  constexpr int MAXC = 1 << D;
+  constexpr int NAV = pow2ceil(KD);
+  constexpr int NAP = pow2ceil(KP);
+  const int lane = threadIdx.x & (VL - 1);
+  const int gw = (threadIdx.x & 31) / VL;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  int wmask_v, wmask_p;
+  const int kv = scatter_index<VL, NAV>(lane, &wmask_v);
+  const int kp = scatter_index<VL, NAP>(lane, &wmask_p);
+
+  // phase 1: the K*D velocity rows of one node per group (warp-uniform loop)
+  for (long long wb = warp * GPW; wb < R; wb += nwarps * GPW) {
+    const long long job = wb + gw;
+    const bool ok = job < R;
+    const int i = ok ? job_nodes[job] : 0;
+    double acc[NAV];
+#pragma unroll
+    for (int r = 0; r < NAV; ++r) acc[r] = 0.0;
+    if (ok) {
+      const int p0 = nbr_ptr[i], nn = nbr_ptr[i + 1] - p0, nc = ncell[i];
+      long long rp[KD];
+#pragma unroll
+      for (int a = 0; a < K; ++a)
+#pragma unroll
+        for (int l = 0; l < D; ++l) rp[a * D + l] = rowptr[a * block + (long long)l * R + i];
+      // flattened velocity positions p = (b*D + m)*nn + j of the row, VL consecutive per step
+      const int npos = KD * nn;
+      int j = lane, bm = 0;
+      while (j >= nn) { j -= nn; ++bm; }
+      for (int p = lane; p < npos; p += VL) {
+        const int bb = bm / D, m = bm - bb * D;
+        const double xv = __ldg(x + bb * block + (long long)m * R + nbr[p0 + j]);
+#pragma unroll
+        for (int a = 0; a < K; ++a) {
+          const int off = p + (bb > a ? NP * nc : 0);
+#pragma unroll
+          for (int l = 0; l < D; ++l) acc[a * D + l] += __ldcs(val + rp[a * D + l] + off) * xv;
+        }
+        j += VL;
+        while (j >= nn) { j -= nn; ++bm; }
+      }
+      // pressure columns of time a: n_p entries per cell of node i, after the time-a velocity block
+      for (int t = lane; t < NP * nc; t += VL) {
+        const int ci = t / NP, q = t - ci * NP;
+        const long long pc = (long long)D * R + (long long)node_cells[(long long)i * MAXC + ci] * NP + q;
+#pragma unroll
+        for (int a = 0; a < K; ++a) {
+          const double xp = __ldg(x + a * block + pc);
+          const int off = (a + 1) * D * nn + t;
+#pragma unroll
+          for (int l = 0; l < D; ++l) acc[a * D + l] += __ldcs(val + rp[a * D + l] + off) * xp;
+        }
+      }
+    }
+    reduce_scatter<VL, NAV>(acc, lane);
+    if (ok && kv < KD && (lane & wmask_v) == 0) {
+      const int a = kv / D, l = kv - a * D;
+      const long long row = a * block + (long long)l * R + i;
+      const double v = acc[0];
+      if (mode == 0) y[row] = v;
+      else if (mode == 1) y[row] = b[row] - v;
+      else y[row] += v;
+    }
+  }
+
+  // phase 2: the K*n_p pressure rows of one cell per group; entries ordered m * nv + j
+  for (long long wb = warp * GPW; wb < C; wb += nwarps * GPW) {
+    const long long c = wb + gw;
+    const bool ok = c < C;
+    double acc[NAP];
+#pragma unroll
+    for (int r = 0; r < NAP; ++r) acc[r] = 0.0;
+    if (ok) {
+      long long rp[KP];
+#pragma unroll
+      for (int a = 0; a < K; ++a)
+#pragma unroll
+        for (int q = 0; q < NP; ++q) rp[a * NP + q] = rowptr[a * block + (long long)D * R + c * NP + q];
+      for (int t = lane; t < D * nv; t += VL) {
+        const int m = t / nv, jj = t - m * nv;
+        const int node = cell_nodes[c * nv + jj];
+#pragma unroll
+        for (int a = 0; a < K; ++a) {
+          const double xa = __ldg(x + a * block + (long long)m * R + node);
+#pragma unroll
+          for (int q = 0; q < NP; ++q) acc[a * NP + q] += __ldcs(val + rp[a * NP + q] + t) * xa;
+        }
+      }
+    }
+    reduce_scatter<VL, NAP>(acc, lane);
+    if (ok && kp < KP && (lane & wmask_p) == 0) {
+      const int a = kp / NP, q = kp - a * NP;
+      const long long row = a * block + (long long)D * R + c * NP + q;
+      const double v = acc[0];
+      if (mode == 0) y[row] = v;
+      else if (mode == 1) y[row] = b[row] - v;
+      else y[row] += v;
+    }
+  }
+}
+
+static int sms_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 152;
+  }
+  return n;
+}
+
+template <int VL, int K, int D>
+static void launch_struct(const Level& L, const double* v, const double* x, const double* b, double* y, int mode,
+                          cudaStream_t s) {
+  const long long threads_needed = (long long)std::max(L.R, L.C) * VL;
+  const int blocks = (int)std::min<long long>((threads_needed + 255) / 256, (long long)sms_count() * 8);
+  k_spmv_struct<VL, K, D><<<blocks, 256, 0, s>>>(L.rowptr, v, L.nbr_ptr, L.nbr, L.ncell, L.node_cells, L.cell_nodes,
+                                                 L.job_nodes, L.block, L.R, L.C, L.nv, x, b, y, mode);
+}
+
+stm_status spmv_structured(const Level& L, const double* v, const double* x, const double* b, double* y, int mode,
+                           cudaStream_t s) {
+  const int key = L.dim * 10 + L.K;
+  switch (key) {
+    case 21: launch_struct<16, 1, 2>(L, v, x, b, y, mode, s); break;
+    case 22: launch_struct<16, 2, 2>(L, v, x, b, y, mode, s); break;
+    case 23: launch_struct<16, 3, 2>(L, v, x, b, y, mode, s); break;
+    case 31: launch_struct<32, 1, 3>(L, v, x, b, y, mode, s); break;
+    case 32: launch_struct<32, 2, 3>(L, v, x, b, y, mode, s); break;
+    case 33: launch_struct<32, 3, 3>(L, v, x, b, y, mode, s); break;
+    default:
+      set_error("structured SpMV: unsupported (dim, k)");
+      return STM_ERR_INVALID_ARG;
+  }
+  note_launch();
+  STM_CUDA(cudaGetLastError());
+  return STM_OK;
+}
+
+}  // namespace stm

@@ -50,60 +50,43 @@ static VGeom vanka_geometry(int n, InvLayout lay, int prec) {
   return g;
 }
 
-// Loads VB bytes (VB / sizeof(S) elements) and converts them to the accumulation type.
-template <typename S, int VB> struct VecLoad;
-template <> struct VecLoad<double, 16> {
-  static constexpr int V = 2;
-  __device__ static void load(const double* p, double* o) {
-    const double2 v = __ldg(reinterpret_cast<const double2*>(p));
-    o[0] = v.x;
-    o[1] = v.y;
-  }
-};
-template <> struct VecLoad<double, 8> {
-  static constexpr int V = 1;
-  __device__ static void load(const double* p, double* o) { o[0] = __ldg(p); }
-};
-template <> struct VecLoad<float, 16> {
-  static constexpr int V = 4;
-  __device__ static void load(const float* p, float* o) {
-    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
-    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
-  }
-};
-template <> struct VecLoad<float, 8> {
-  static constexpr int V = 2;
-  __device__ static void load(const float* p, float* o) {
-    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
-    o[0] = v.x; o[1] = v.y;
-  }
-};
-template <> struct VecLoad<float, 4> {
-  static constexpr int V = 1;
-  __device__ static void load(const float* p, float* o) { o[0] = __ldg(p); }
-};
-__device__ __forceinline__ void bf16x2_to_f32(unsigned u, float* o) {
-  o[0] = __uint_as_float(u << 16);
-  o[1] = __uint_as_float(u & 0xffff0000u);
+// Raw vector loads (VB bytes as 32-bit words) and their conversion to the accumulation type.
+template <int VB> struct Raw { unsigned w[VB / 4]; };
+template <int VB> __device__ __forceinline__ Raw<VB> ld_raw(const void* p);
+template <> __device__ __forceinline__ Raw<16> ld_raw<16>(const void* p) {
+  const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
+  return Raw<16>{{v.x, v.y, v.z, v.w}};
 }
-template <> struct VecLoad<__nv_bfloat16, 16> {
-  static constexpr int V = 8;
-  __device__ static void load(const __nv_bfloat16* p, float* o) {
-    const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
-    bf16x2_to_f32(v.x, o); bf16x2_to_f32(v.y, o + 2); bf16x2_to_f32(v.z, o + 4); bf16x2_to_f32(v.w, o + 6);
+template <> __device__ __forceinline__ Raw<8> ld_raw<8>(const void* p) {
+  const uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
+  return Raw<8>{{v.x, v.y}};
+}
+template <> __device__ __forceinline__ Raw<4> ld_raw<4>(const void* p) {
+  return Raw<4>{{__ldg(reinterpret_cast<const unsigned*>(p))}};
+}
+template <typename S, int VB> struct Conv;
+template <int VB> struct Conv<double, VB> {
+  static constexpr int V = VB / 8;
+  __device__ static void run(const Raw<VB>& r, double* o) {
+#pragma unroll
+    for (int v = 0; v < V; ++v) o[v] = __hiloint2double((int)r.w[2 * v + 1], (int)r.w[2 * v]);
   }
 };
-template <> struct VecLoad<__nv_bfloat16, 8> {
-  static constexpr int V = 4;
-  __device__ static void load(const __nv_bfloat16* p, float* o) {
-    const uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
-    bf16x2_to_f32(v.x, o); bf16x2_to_f32(v.y, o + 2);
+template <int VB> struct Conv<float, VB> {
+  static constexpr int V = VB / 4;
+  __device__ static void run(const Raw<VB>& r, float* o) {
+#pragma unroll
+    for (int v = 0; v < V; ++v) o[v] = __uint_as_float(r.w[v]);
   }
 };
-template <> struct VecLoad<__nv_bfloat16, 4> {
-  static constexpr int V = 2;
-  __device__ static void load(const __nv_bfloat16* p, float* o) {
-    bf16x2_to_f32(__ldg(reinterpret_cast<const unsigned*>(p)), o);
+template <int VB> struct Conv<__nv_bfloat16, VB> {
+  static constexpr int V = VB / 2;
+  __device__ static void run(const Raw<VB>& r, float* o) {
+#pragma unroll
+    for (int v = 0; v < VB / 4; ++v) {
+      o[2 * v] = __uint_as_float(r.w[v] << 16);
+      o[2 * v + 1] = __uint_as_float(r.w[v] & 0xffff0000u);
+    }
   }
 };
 
@@ -116,8 +99,9 @@ __global__ void __launch_bounds__(256) k_vanka_local(const S* __restrict__ inv, 
                                                      const int* __restrict__ cell_list, int ncells, VGeom g,
                                                      double* __restrict__ d_scatter, double omega) {
   using A = typename Acc<S>::T;
-  using L = VecLoad<S, VB>;
-  constexpr int V = L::V;
+  using CV = Conv<S, VB>;
+  constexpr int V = CV::V;
+  constexpr int UB = VB == 16 ? 4 : 8;  // column loads issued before their FMAs
   extern __shared__ double smd[];
   A* tl = reinterpret_cast<A*>(smd);      // [P][n]
   A* part = tl + g.P * g.n;               // [P][Q][ld]
@@ -139,13 +123,24 @@ __global__ void __launch_bounds__(256) k_vanka_local(const S* __restrict__ inv, 
       for (int v = 0; v < V; ++v) acc[v] = 0;
       const S* M = inv + (size_t)c * g.n * g.ld + rc * V;
       const A* tc = tl + slot * g.n;
-#pragma unroll 4
-      for (int j = cg; j < g.n; j += g.Q) {
-        A e[V];
-        L::load(M + (size_t)j * g.ld, e);
-        const A tj = tc[j];
+      for (int j0 = cg; j0 < g.n; j0 += UB * g.Q) {
+        Raw<VB> raw[UB];
 #pragma unroll
-        for (int v = 0; v < V; ++v) acc[v] += e[v] * tj;
+        for (int u = 0; u < UB; ++u) {
+          const int j = j0 + u * g.Q;
+          if (j < g.n) raw[u] = ld_raw<VB>(M + (size_t)j * g.ld);
+        }
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+          const int j = j0 + u * g.Q;
+          if (j < g.n) {
+            A e[V];
+            CV::run(raw[u], e);
+            const A tj = tc[j];
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] += e[v] * tj;
+          }
+        }
       }
       A* pp = part + (slot * g.Q + cg) * g.ld + rc * V;
 #pragma unroll
