@@ -157,6 +157,31 @@ stm_status stm_gmres_solve(stm_hierarchy* h, const double* b_dev, double* x_dev,
 stm_status stm_gmres_solve_host(stm_hierarchy* h, const double* b_host, double* x_host,
                                 const stm_gmres_opts* opts, stm_solve_info* info, void* stream);
 
+/* Right-hand side of one Newton step from the linearisation point w of the last
+ * stm_assemble_jacobian, on the finest level (Problem 3.1 with f = 0, Eqs. Def:Lh, Def:B_GamD):
+ *   which = 0: b(U, nu) + c(w, w), where b(U, nu) = int_{I_n} B_GamD(g, (psi, xi)) dt
+ *              + <v(t_{n-1}^-), psi(t_{n-1}^+)> with inflow data g = U g_1 on x = 0 (g = 0 on walls and
+ *              obstacle), previous-slab state U g_1 e_x, g_1 the Poiseuille profile 4y(H-y)/H^2
+ *              (3D: 16 y(H-y) z(L-z)/(H^2 L^2)), and c(w, w) = sum_bc T_abc <(w^c . grad) w^b, psi>;
+ *              then J(w) X = b + c is exactly one Newton step from w;
+ *   which = 1: db/dU (b is linear in U);   which = 2: db/dnu (b is affine in nu).
+ * b_dev: FP64 [n_dofs of the finest level], overwritten. */
+stm_status stm_assemble_rhs(stm_hierarchy* h, double U, double nu, int which, double* b_dev, void* stream);
+
+/* Weights j of the drag-like functional J(X) = int_{I_n} int_wake v_1 dx dt = j . X, where the wake
+ * is the union of finest cells inside the level-1 cell box [wake_lo, wake_hi) (all z in 3D).
+ * j_dev: FP64 [n_dofs of the finest level], overwritten. */
+stm_status stm_functional_weights(stm_hierarchy* h, const int* wake_lo, const int* wake_hi, double* j_dev,
+                                  void* stream);
+
+/* y = (dJ/dnu) x on the finest level. J is affine in nu; its nu-part is the diffusion and the
+ * gamma1 / symmetric Nitsche terms of Eqs. Def:Ah and Def:B_GamD, diagonal in time (Mt). */
+stm_status stm_jacobian_dnu_apply(stm_hierarchy* h, const double* x_dev, double* y_dev, void* stream);
+
+/* *out = x . y over n entries (FP64, deterministic reduction). Synchronous. */
+stm_status stm_dot(stm_hierarchy* h, const double* x_dev, const double* y_dev, long long n, double* out,
+                   void* stream);
+
 /* Copies of internal data for verification (synchronous, caller-owned host buffers):
  * the CSR of J_g (rowptr: n_dofs+1, colidx/val: nnz) and the cell inverses of level g >= 1 as
  * FP64, row-major per cell ([n_cells][n][n], converted from the stored precision). */

@@ -392,6 +392,42 @@ stm_status stm_gmres_solve_host(stm_hierarchy* h, const double* b_host, double* 
   return st;
 }
 
+stm_status stm_assemble_rhs(stm_hierarchy* h, double U, double nu, int which, double* b_dev, void* stream) {
+  if (!h || !b_dev) return bad_arg("NULL argument");
+  if (which < 0 || which > 2) return bad_arg("which must be 0 (b + c), 1 (db/dU) or 2 (db/dnu)");
+  if (which == 0 && !h->H.assembled) {
+    set_error("assemble_rhs(which=0) needs the linearisation point of assemble_jacobian");
+    return STM_ERR_STATE;
+  }
+  return assemble_cellvec(h->H, which, U, nu, nullptr, nullptr, b_dev, S(stream));
+}
+
+stm_status stm_functional_weights(stm_hierarchy* h, const int* wake_lo, const int* wake_hi, double* j_dev,
+                                  void* stream) {
+  if (!h || !wake_lo || !wake_hi || !j_dev) return bad_arg("NULL argument");
+  for (int m = 0; m < h->H.p.dim; ++m)
+    if (wake_lo[m] < 0 || wake_hi[m] > h->H.p.coarse_cells[m] || wake_lo[m] > wake_hi[m])
+      return bad_arg("wake box outside the level-1 grid");
+  return assemble_cellvec(h->H, 3, 0.0, h->H.p.nu, wake_lo, wake_hi, j_dev, S(stream));
+}
+
+stm_status stm_jacobian_dnu_apply(stm_hierarchy* h, const double* x_dev, double* y_dev, void* stream) {
+  if (!h || !x_dev || !y_dev) return bad_arg("NULL argument");
+  return dnu_apply(h->H, x_dev, y_dev, S(stream));
+}
+
+stm_status stm_dot(stm_hierarchy* h, const double* x_dev, const double* y_dev, long long n, double* out,
+                   void* stream) {
+  if (!h || !x_dev || !y_dev || !out || n < 0) return bad_arg("NULL argument or negative size");
+  Hierarchy& H = h->H;
+  STM_TRY(ensure_krylov(H, std::max(H.restart_cap, 30)));
+  cudaStream_t s = S(stream);
+  STM_TRY(batched_dots(x_dev, 1, y_dev, n, H.hcol, H.part, H.nblk_dot, s));
+  STM_CUDA(cudaMemcpyAsync(out, H.hcol, sizeof(double), cudaMemcpyDeviceToHost, s));
+  STM_CUDA(cudaStreamSynchronize(s));
+  return STM_OK;
+}
+
 stm_status stm_copy_jacobian(const stm_hierarchy* h, int level, long long* rowptr, int* colidx, double* val) {
   if (!h || !rowptr || !colidx || !val) return bad_arg("NULL argument");
   STM_TRY(need_level(h->H, level, 0));

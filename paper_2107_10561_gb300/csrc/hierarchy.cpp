@@ -162,6 +162,15 @@ static stm_status build_reference(Level& L) {
   o.fPf = 2 * nv * nv;
   o.face_stride = 2 * nv * nv + np * nv;
   off += 2 * d * o.face_stride;
+  int nqf0 = 1;
+  for (int m = 0; m < d - 1; ++m) nqf0 *= kQ1;
+  o.Xq = off; off += nq * d;
+  o.nqf = nqf0;
+  o.XF = off; off += nqf0 * d;
+  o.WF = off; off += nqf0;
+  o.phiF = off; off += nqf0 * nv;
+  o.gnF = off; off += nqf0 * nv;
+  o.xiF = off; off += nqf0 * np;
   o.total = off;
   std::vector<double> ref(off, 0.0);
   double gx[kQ1], gw[kQ1];
@@ -259,6 +268,31 @@ static stm_status build_reference(Level& L) {
         }
       for (int a = 0; a < np; ++a)
         for (int i = 0; i < nv; ++i) Pf[a * nv + i] += w * area * pbasis(x, a) * pv[i];
+    }
+  }
+  for (int q = 0; q < nq; ++q)
+    for (int m = 0; m < d; ++m) ref[o.Xq + q * d + m] = X[q * 3 + m];
+  {
+    double area = 1.0;
+    for (int m = 1; m < d; ++m) area *= L.h[m];
+    for (int qf = 0; qf < o.nqf; ++qf) {
+      double x[3] = {0.0, 0.0, 0.0};
+      double w = 1.0;
+      int t = qf;
+      for (int m = 1; m < d; ++m) {
+        x[m] = gx[t % kQ1];
+        w *= gw[t % kQ1];
+        t /= kQ1;
+      }
+      for (int m = 0; m < d; ++m) ref[o.XF + qf * d + m] = x[m];
+      ref[o.WF + qf] = w * area;
+      for (int i = 0; i < nv; ++i) {
+        double v, g[3];
+        basis(x, i, &v, g);
+        ref[o.phiF + qf * nv + i] = v;
+        ref[o.gnF + qf * nv + i] = -g[0];
+      }
+      for (int a = 0; a < np; ++a) ref[o.xiF + qf * np + a] = pbasis(x, a);
     }
   }
   L.ro = o;
@@ -466,6 +500,7 @@ static stm_status build_level(const stm_params& p, int g, Level& L, std::vector<
   STM_TRY(upload(&L.job_nodes, job_nodes));
   STM_TRY(upload(&L.idx, idx));
   STM_TRY(upload(&L.cell_nodes, L.h_cell_nodes));
+  STM_TRY(upload(&L.cell_xyz, L.h_cell_xyz));
   STM_TRY(upload(&L.bmask, bmask));
   STM_TRY(upload(&L.rank, rank));
   STM_TRY(upload(&L.cellrank, cellrank));
@@ -658,7 +693,7 @@ stm_status build_levels(Hierarchy& H) {
 
 void free_hierarchy(Hierarchy& H) {
   for (Level& L : H.L) {
-    void* ptrs[] = {L.idx, L.cell_nodes, L.bmask, L.rank, L.cellrank, L.nn, L.ncell, L.rowptr, L.nbr_ptr, L.nbr,
+    void* ptrs[] = {L.idx, L.cell_nodes, L.cell_xyz, L.bmask, L.rank, L.cellrank, L.nn, L.ncell, L.rowptr, L.nbr_ptr, L.nbr,
                     L.node_cells, L.job_nodes,
                     L.colidx, L.val, L.valT, L.ref, L.inj, L.wnod, L.inv, L.wmult, L.own_ptr,
                     L.own_pos, L.last_owner, L.colour_cells, L.Y, L.P_rowptr, L.P_col, L.P_val,

@@ -52,9 +52,13 @@ struct Profiler {
 //   M[nv][nv], Kst[nv][nv]      mass, stiffness
 //   Div[d][np][nv]              (d_m phi_j, xi_q)
 //   per face f in 0..2d-1:  S[nv][nv], G[nv][nv] (<grad phi_j . n, phi_i>), Pf[np][nv]
+//   Xq[nq][d]                   reference coordinates of the volume points
+//   inflow face x = 0 (face 0): nqf points XF[nqf][d], WF[nqf] (weight x |F|), phiF[nqf][nv],
+//   gnF[nqf][nv] (grad phi . n with n = -e_x), xiF[nqf][np]
 struct RefOffsets {
   int nq, nv, np;
   int W, phi, gphi, M, Kst, Div, face0, face_stride, fS, fG, fPf;
+  int Xq, nqf, XF, WF, phiF, gnF, xiF;
   int total;
 };
 
@@ -79,6 +83,7 @@ struct Level {
   // device data -----------------------------------------------------------------------------
   int* idx = nullptr;             // [C][n] global DoF of each local DoF
   int* cell_nodes = nullptr;      // [C][nv]
+  int* cell_xyz = nullptr;        // [C][3] integer cell coordinates
   unsigned char* bmask = nullptr; // [C] bit f set: face f on Gamma_D
   unsigned char* rank = nullptr;  // [C][nv][nv] rank of node j in the neighbour list of node i
   unsigned char* cellrank = nullptr; // [C][nv] rank of the cell among the cells of node i
@@ -184,6 +189,9 @@ stm_status jacobian_apply(Hierarchy& H, int g, const double* x, const double* b,
 stm_status vanka_step(Hierarchy& H, int g, const double* r, double* d, int transpose,
                       bool d_is_zero, cudaStream_t s);
 stm_status coarse_apply(Hierarchy& H, const double* r, double* d, int transpose, cudaStream_t s);
+stm_status assemble_cellvec(Hierarchy& H, int mode, double U, double nu, const int* wake_lo, const int* wake_hi,
+                            double* out, cudaStream_t s);
+stm_status dnu_apply(Hierarchy& H, const double* x, double* y, cudaStream_t s);
 stm_status vcycle(Hierarchy& H, const double* r, double* d, int transpose, cudaStream_t s);
 
 // BLAS-1 style helpers on device vectors (kernels_krylov.cu)

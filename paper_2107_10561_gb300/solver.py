@@ -168,6 +168,29 @@ class Hierarchy:
             _lib.check(st, "stm_gmres_solve_host")
         return info
 
+    def assemble_rhs(self, U, nu, b, which=0, stream=None):
+        """b = b(U, nu) + c(w, w) (which=0), db/dU (1) or db/dnu (2) on the finest level."""
+        _lib.check(self.lib.stm_assemble_rhs(self.h, float(U), float(nu), int(which), _ptr(b, self.n_dofs(), "b"),
+                                             _stream(stream)), "stm_assemble_rhs")
+
+    def functional_weights(self, wake_lo, wake_hi, j, stream=None):
+        lo = (C.c_int * 3)(*(list(wake_lo) + [0] * (3 - len(wake_lo))))
+        hi = (C.c_int * 3)(*(list(wake_hi) + [1] * (3 - len(wake_hi))))
+        _lib.check(self.lib.stm_functional_weights(self.h, lo, hi, _ptr(j, self.n_dofs(), "j"), _stream(stream)),
+                   "stm_functional_weights")
+
+    def jacobian_dnu_apply(self, x, y, stream=None):
+        n = self.n_dofs()
+        _lib.check(self.lib.stm_jacobian_dnu_apply(self.h, _ptr(x, n, "x"), _ptr(y, n, "y"), _stream(stream)),
+                   "stm_jacobian_dnu_apply")
+
+    def dot(self, x, y, stream=None):
+        out = C.c_double()
+        n = x.numel()
+        _lib.check(self.lib.stm_dot(self.h, _ptr(x, n, "x"), _ptr(y, n, "y"), n, C.byref(out), _stream(stream)),
+                   "stm_dot")
+        return out.value
+
     def profile_enable(self, enable=True):
         _lib.check(self.lib.stm_profile_enable(self.h, int(enable)), "stm_profile_enable")
 
