@@ -234,9 +234,10 @@ typedef enum {
 
 /* Turn event timing of kernel launches on (1) or off (0); turning it on clears the records. */
 stm_status stm_profile_enable(stm_hierarchy* h, int enable);
-/* Synchronises the device and returns, for one kernel class, the summed event time (ms), the
- * number of timed launches and the summed algorithmic bytes since profiling was enabled. */
-stm_status stm_profile_read(stm_hierarchy* h, int kernel_class, double* total_ms, long long* launches,
+/* Synchronises the device and returns, for one kernel class on one level (-1: all levels), the
+ * summed event time (ms), the number of timed launches and the summed algorithmic bytes since
+ * profiling was enabled. Per-level figures exist for VANKA_LOCAL, VANKA_COMBINE, JACOBIAN_SPMV. */
+stm_status stm_profile_read(stm_hierarchy* h, int kernel_class, int level, double* total_ms, long long* launches,
                             double* bytes);
 /* Number of kernel launches issued by this library in this process so far. */
 long long stm_kernel_launches(void);

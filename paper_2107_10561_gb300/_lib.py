@@ -61,7 +61,7 @@ SIGNATURES = {
     "stm_copy_cell_inverses": ([_P, _I, _DP], _I),
     "stm_vanka_apply_noalloc": ([_L, _I, _L, _P, _P, _P, _P, _D, _P], _I),
     "stm_profile_enable": ([_P, _I], _I),
-    "stm_profile_read": ([_P, _I, _DP, _LP, _DP], _I),
+    "stm_profile_read": ([_P, _I, _I, _DP, _LP, _DP], _I),
     "stm_kernel_launches": ([], C.c_longlong),
     "stm_destroy": ([_P], None),
     "stm_last_error": ([], C.c_char_p),

@@ -498,7 +498,8 @@ static cudaEvent_t pool_get(Profiler& P) {
   return e;
 }
 
-ProfScope::ProfScope(Hierarchy* H_, int cls_, cudaStream_t s_, double bytes_) : H(H_), cls(cls_), s(s_), bytes(bytes_) {
+ProfScope::ProfScope(Hierarchy* H_, int cls_, cudaStream_t s_, double bytes_, int level_)
+    : H(H_), cls(cls_), level(level_), s(s_), bytes(bytes_) {
   if (H && H->prof.on) {
     a = pool_get(H->prof);
     cudaEventRecord(a, s);
@@ -509,7 +510,7 @@ ProfScope::~ProfScope() {
   if (a) {
     cudaEvent_t b = pool_get(H->prof);
     cudaEventRecord(b, s);
-    H->prof.recs.push_back(ProfRec{a, b, cls, bytes});
+    H->prof.recs.push_back(ProfRec{a, b, cls, level, bytes});
   }
 }
 
@@ -517,9 +518,13 @@ static void profile_drain(Profiler& P) {
   for (ProfRec& r : P.recs) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
-      P.total_ms[r.cls] += ms;
-      P.count[r.cls] += 1;
-      P.bytes[r.cls] += r.bytes;
+      const int slots[2] = {0, (r.level >= 0 && r.level + 1 < kProfLevels) ? r.level + 1 : -1};
+      for (int k = 0; k < 2; ++k) {
+        if (slots[k] < 0) continue;
+        P.total_ms[r.cls][slots[k]] += ms;
+        P.count[r.cls][slots[k]] += 1;
+        P.bytes[r.cls][slots[k]] += r.bytes;
+      }
     }
     P.pool.push_back(r.a);
     P.pool.push_back(r.b);
@@ -536,21 +541,25 @@ stm_status stm_profile_enable(stm_hierarchy* h, int enable) {
   STM_CUDA(cudaDeviceSynchronize());
   profile_drain(P);
   if (enable) {
-    for (int c = 0; c < STM_KCLASS_COUNT; ++c) P.total_ms[c] = 0.0, P.count[c] = 0, P.bytes[c] = 0.0;
+    for (int c = 0; c < STM_KCLASS_COUNT; ++c)
+      for (int l = 0; l < kProfLevels; ++l) P.total_ms[c][l] = 0.0, P.count[c][l] = 0, P.bytes[c][l] = 0.0;
   }
   P.on = enable != 0;
   return STM_OK;
 }
 
-stm_status stm_profile_read(stm_hierarchy* h, int kernel_class, double* total_ms, long long* launches, double* bytes) {
+stm_status stm_profile_read(stm_hierarchy* h, int kernel_class, int level, double* total_ms, long long* launches,
+                            double* bytes) {
   if (!h) return bad_arg("NULL hierarchy");
   if (kernel_class < 0 || kernel_class >= STM_KCLASS_COUNT) return bad_arg("kernel_class out of range");
+  if (level < -1 || level + 1 >= kProfLevels) return bad_arg("level out of range");
   Profiler& P = h->H.prof;
   STM_CUDA(cudaDeviceSynchronize());
   profile_drain(P);
-  if (total_ms) *total_ms = P.total_ms[kernel_class];
-  if (launches) *launches = P.count[kernel_class];
-  if (bytes) *bytes = P.bytes[kernel_class];
+  const int slot = level + 1;
+  if (total_ms) *total_ms = P.total_ms[kernel_class][slot];
+  if (launches) *launches = P.count[kernel_class][slot];
+  if (bytes) *bytes = P.bytes[kernel_class][slot];
   return STM_OK;
 }
 

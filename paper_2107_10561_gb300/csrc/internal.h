@@ -30,18 +30,19 @@ stm_status cuda_fail(cudaError_t e, const char* what);
 extern std::atomic<long long> g_launches;
 inline void note_launch(long long n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+constexpr int kProfLevels = 17;  // slot 0: all levels, slot 1 + g: level g
 struct ProfRec {
   cudaEvent_t a, b;
-  int cls;
+  int cls, level;
   double bytes;
 };
 struct Profiler {
   bool on = false;
   std::vector<ProfRec> recs;
   std::vector<cudaEvent_t> pool;
-  double total_ms[STM_KCLASS_COUNT] = {};
-  long long count[STM_KCLASS_COUNT] = {};
-  double bytes[STM_KCLASS_COUNT] = {};
+  double total_ms[STM_KCLASS_COUNT][kProfLevels] = {};
+  long long count[STM_KCLASS_COUNT][kProfLevels] = {};
+  double bytes[STM_KCLASS_COUNT][kProfLevels] = {};
 };
 
 // Reference tables of a uniform level (all cells congruent): computed on the host --------------
@@ -149,11 +150,11 @@ struct Hierarchy {
 // Records CUDA events around the launches made in its lifetime when profiling is on.
 struct ProfScope {
   Hierarchy* H;
-  int cls;
+  int cls, level;
   cudaStream_t s;
   double bytes;
   cudaEvent_t a = nullptr;
-  ProfScope(Hierarchy* H_, int cls_, cudaStream_t s_, double bytes_);
+  ProfScope(Hierarchy* H_, int cls_, cudaStream_t s_, double bytes_, int level_ = -1);
   ~ProfScope();
 };
 

@@ -129,7 +129,7 @@ stm_status jacobian_apply(Hierarchy& H, int g, const double* x, const double* b,
     if (st != STM_OK) return st;
     v = L.valT;
   }
-  ProfScope ps(&H, STM_KCLASS_JACOBIAN_SPMV, s, 8.0 * (double)L.nnz + 24.0 * (double)L.N);
+  ProfScope ps(&H, STM_KCLASS_JACOBIAN_SPMV, s, 8.0 * (double)L.nnz + 24.0 * (double)L.N, g);
   return spmv_structured(L, v, x, b, y, mode, s);
 }
 

@@ -236,12 +236,13 @@ static void launch_fwd(const Level& L, const void* inv, int vb, const VGeom& g, 
   }
 }
 
-static stm_status launch_local(Hierarchy& H, Level& L, const double* t, const int* cells, int nc,
+static stm_status launch_local(Hierarchy& H, Level& L, int level, const double* t, const int* cells, int nc,
                                int transpose, double* scatter, cudaStream_t s) {
   if (nc <= 0) return STM_OK;
   const int prec = H.p.inv_precision;
   const InvLayout lay = inv_layout(L.n, prec);
-  ProfScope ps(&H, STM_KCLASS_VANKA_LOCAL, s, (double)nc * ((double)L.n * L.n * storage_size(prec) + 20.0 * L.n));
+  ProfScope ps(&H, STM_KCLASS_VANKA_LOCAL, s, (double)nc * ((double)L.n * L.n * storage_size(prec) + 20.0 * L.n),
+               level);
   const double omega = H.p.omega;
   if (!transpose) {
     const VGeom g = vanka_geometry(L.n, lay, prec);
@@ -279,7 +280,7 @@ stm_status vanka_step(Hierarchy& H, int g, const double* r, double* d, int trans
         if (st != STM_OK) return st;
         t = L.t;
       }
-      stm_status st = launch_local(H, L, t, L.colour_cells + L.colour_off[col], nc, transpose, d, s);
+      stm_status st = launch_local(H, L, g, t, L.colour_cells + L.colour_off[col], nc, transpose, d, s);
       if (st != STM_OK) return st;
     }
     return STM_OK;
@@ -290,10 +291,10 @@ stm_status vanka_step(Hierarchy& H, int g, const double* r, double* d, int trans
     if (st != STM_OK) return st;
     t = L.t;
   }
-  stm_status st = launch_local(H, L, t, nullptr, L.C, transpose, nullptr, s);
+  stm_status st = launch_local(H, L, g, t, nullptr, L.C, transpose, nullptr, s);
   if (st != STM_OK) return st;
   const int blocks = (int)std::min<long long>((L.N + 255) / 256, sm_count() * 16LL);
-  ProfScope ps(&H, STM_KCLASS_VANKA_COMBINE, s, 0.0);
+  ProfScope ps(&H, STM_KCLASS_VANKA_COMBINE, s, 0.0, g);
   k_vanka_gather<<<blocks, 256, 0, s>>>(d, L.Y, L.own_ptr, L.own_pos, L.last_owner, L.wmult, L.N, omega,
                                         H.p.smoother == STM_VANKA_PAPER_OVERWRITE);
   note_launch();

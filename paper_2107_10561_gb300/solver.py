@@ -194,11 +194,12 @@ class Hierarchy:
     def profile_enable(self, enable=True):
         _lib.check(self.lib.stm_profile_enable(self.h, int(enable)), "stm_profile_enable")
 
-    def profile_read(self, kernel_class):
-        """(total event ms, launches, algorithmic bytes) of one kernel class since profile_enable."""
+    def profile_read(self, kernel_class, level=-1):
+        """(total event ms, launches, algorithmic bytes) of one kernel class (one level, -1: all)."""
         ms, n, by = C.c_double(), C.c_longlong(), C.c_double()
         cls = _lib.KCLASS[kernel_class] if isinstance(kernel_class, str) else kernel_class
-        _lib.check(self.lib.stm_profile_read(self.h, cls, C.byref(ms), C.byref(n), C.byref(by)), "stm_profile_read")
+        _lib.check(self.lib.stm_profile_read(self.h, cls, int(level), C.byref(ms), C.byref(n), C.byref(by)),
+                   "stm_profile_read")
         return dict(ms=ms.value, launches=n.value, bytes=by.value)
 
     @staticmethod
