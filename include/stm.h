@@ -182,6 +182,22 @@ stm_status stm_jacobian_dnu_apply(stm_hierarchy* h, const double* x_dev, double*
 stm_status stm_dot(stm_hierarchy* h, const double* x_dev, const double* y_dev, long long n, double* out,
                    void* stream);
 
+/* Multi-right-hand-side path: nrhs <= 32 columns share the hierarchy (one J, one set of cell
+ * inverses). Vectors are column-major [nrhs][n_dofs] (leading dimension n_dofs), FP64, on the device.
+ *  - stm_vanka_sweep_multi: one additive smoothing step D <- S(D, R) on level g >= 1 for every column
+ *    (Eq. LocVanka with damping). The local products Y_T = J_T^{-1} T_T run on the 32-column blocks:
+ *    with BF16 inverses on the tensor cores (FP32 accumulation; T split into two BF16 parts so that the
+ *    only rounding is the stored inverse's), with FP32 / FP64 inverses on CUDA cores.
+ *  - stm_gmres_solve_multi: right-preconditioned FGMRES per column, lock-stepped so that every
+ *    iteration applies one 32-column V-cycle (Algorithm 1) and one 32-column product with J; each
+ *    column keeps its own Arnoldi basis, Hessenberg matrix and stopping test. infos: nrhs entries.
+ *    Additive smoother and J x = b only (transpose must be 0); restart <= 60. Synchronises once per
+ *    iteration. Returns STM_ERR_NOT_CONVERGED if some column hits max_iter. */
+stm_status stm_vanka_sweep_multi(stm_hierarchy* h, int level, int nrhs, const double* R_dev, double* D_dev,
+                                 void* stream);
+stm_status stm_gmres_solve_multi(stm_hierarchy* h, int nrhs, const double* B_dev, double* X_dev,
+                                 const stm_gmres_opts* opts, stm_solve_info* infos, void* stream);
+
 /* Copies of internal data for verification (synchronous, caller-owned host buffers):
  * the CSR of J_g (rowptr: n_dofs+1, colidx/val: nnz) and the cell inverses of level g >= 1 as
  * FP64, row-major per cell ([n_cells][n][n], converted from the stored precision). */

@@ -16,11 +16,6 @@ const char* last_error_cstr();
 
 using namespace stm;
 
-#define STM_TRY(x)               \
-  do {                           \
-    stm_status s_ = (x);         \
-    if (s_ != STM_OK) return s_; \
-  } while (0)
 
 static stm_status bad_arg(const char* msg) {
   set_error(msg);
@@ -425,6 +420,226 @@ stm_status stm_dot(stm_hierarchy* h, const double* x_dev, const double* y_dev, l
   STM_TRY(batched_dots(x_dev, 1, y_dev, n, H.hcol, H.part, H.nblk_dot, s));
   STM_CUDA(cudaMemcpyAsync(out, H.hcol, sizeof(double), cudaMemcpyDeviceToHost, s));
   STM_CUDA(cudaStreamSynchronize(s));
+  return STM_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Multi-right-hand-side smoothing step and FGMRES (up to 32 columns sharing one hierarchy)
+// ---------------------------------------------------------------------------------------------
+stm_status stm_vanka_sweep_multi(stm_hierarchy* h, int level, int nrhs, const double* R_dev, double* D_dev,
+                                 void* stream) {
+  if (!h || !R_dev || !D_dev) return bad_arg("NULL argument");
+  if (nrhs < 1 || nrhs > 32) return bad_arg("nrhs must be in [1, 32]");
+  STM_TRY(need_level(h->H, level, 1));
+  if (!h->H.factored) {
+    set_error("vanka_sweep_multi before factor_cells");
+    return STM_ERR_STATE;
+  }
+  Hierarchy& H = h->H;
+  if (H.p.smoother != STM_VANKA_ADDITIVE) return bad_arg("multi-RHS smoothing implements the additive smoother");
+  STM_TRY(ensure_multi(H));
+  Level& L = H.L[level];
+  cudaStream_t s = S(stream);
+  STM_TRY(multi_to_interleaved(R_dev, L.mr, L.N, nrhs, s));
+  STM_TRY(multi_to_interleaved(D_dev, L.md, L.N, nrhs, s));
+  STM_TRY(vanka_step_multi(H, level, L.mr, L.md, false, s));
+  return multi_from_interleaved(L.md, D_dev, L.N, nrhs, s);
+}
+
+static stm_status ensure_krylov_multi(Hierarchy& H, int m) {
+  const size_t N = (size_t)H.L.back().N, NRs = 32;
+  if (H.mrestart_cap >= m && H.mV) return STM_OK;
+  void* ptrs[] = {H.mV, H.mZ, H.mW, H.mB, H.mX, H.mh, H.mpart, H.mf, H.my};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  STM_CUDA(cudaMalloc(&H.mV, sizeof(double) * (m + 1) * N * NRs));
+  STM_CUDA(cudaMalloc(&H.mZ, sizeof(double) * m * N * NRs));
+  STM_CUDA(cudaMalloc(&H.mW, sizeof(double) * N * NRs));
+  STM_CUDA(cudaMalloc(&H.mB, sizeof(double) * N * NRs));
+  STM_CUDA(cudaMalloc(&H.mX, sizeof(double) * N * NRs));
+  STM_CUDA(cudaMalloc(&H.mh, sizeof(double) * (2 * m + 8) * NRs));
+  STM_CUDA(cudaMalloc(&H.mpart, sizeof(double) * (m + 2) * 304 * NRs));
+  STM_CUDA(cudaMalloc(&H.mf, sizeof(double) * NRs));
+  STM_CUDA(cudaMalloc(&H.my, sizeof(double) * (m + 1) * NRs));
+  H.mrestart_cap = m;
+  return STM_OK;
+}
+
+stm_status stm_gmres_solve_multi(stm_hierarchy* h, int nrhs, const double* B_dev, double* X_dev,
+                                 const stm_gmres_opts* opts, stm_solve_info* infos, void* stream) {
+  if (!h || !B_dev || !X_dev || !opts) return bad_arg("NULL argument");
+  if (nrhs < 1 || nrhs > 32) return bad_arg("nrhs must be in [1, 32]");
+  if (opts->restart < 1 || opts->restart > 60 || opts->max_iter < 0 || !(opts->rtol >= 0.0))
+    return bad_arg("restart in [1,60], max_iter >= 0, rtol >= 0");
+  if (opts->transpose) return bad_arg("the multi-RHS solve implements J x = b only");
+  Hierarchy& H = h->H;
+  if (!H.factored) {
+    set_error("gmres_solve_multi before factor_cells");
+    return STM_ERR_STATE;
+  }
+  if (H.p.smoother != STM_VANKA_ADDITIVE) return bad_arg("multi-RHS solve implements the additive smoother");
+  const int m = opts->restart;
+  const int nb = 304;
+  Level& F = H.L.back();
+  const long long N = F.N;
+  cudaStream_t s = S(stream);
+  STM_TRY(ensure_multi(H));
+  STM_TRY(ensure_krylov_multi(H, m));
+  const size_t VS = (size_t)N * 32;  // doubles per multi-vector
+  STM_TRY(multi_to_interleaved(B_dev, H.mB, N, nrhs, s));
+  if (opts->use_x0) {
+    STM_TRY(multi_to_interleaved(X_dev, H.mX, N, nrhs, s));
+  } else {
+    STM_CUDA(cudaMemsetAsync(H.mX, 0, sizeof(double) * VS, s));
+  }
+  std::vector<double> hbuf((2 * m + 8) * 32), fvec(32), yv((m + 1) * 32, 0.0);
+  auto col_norms = [&](const double* V, double* out) -> stm_status {
+    STM_TRY(mdots(V, 1, V, N, H.mh, H.mpart, nb, s));
+    STM_CUDA(cudaMemcpyAsync(hbuf.data(), H.mh, sizeof(double) * 32, cudaMemcpyDeviceToHost, s));
+    STM_CUDA(cudaStreamSynchronize(s));
+    for (int c = 0; c < 32; ++c) out[c] = std::sqrt(hbuf[c]);
+    return STM_OK;
+  };
+  double bnorm[32], beta[32];
+  STM_TRY(col_norms(H.mB, bnorm));
+  for (int c = 0; c < nrhs; ++c)
+    if (!std::isfinite(bnorm[c])) {
+      set_error("non-finite right-hand side");
+      return STM_ERR_NONFINITE;
+    }
+  std::vector<int> iters(32, 0), conv(32, 0), restarts(32, 0);
+  std::vector<double> est(32, 1.0), relres(32, 0.0);
+  for (int c = 0; c < 32; ++c)
+    if (c >= nrhs || bnorm[c] == 0.0) conv[c] = 1;
+  std::vector<double> Hm((size_t)(m + 1) * m * 32), cs(m * 32), sn(m * 32), g((m + 1) * 32);
+  int it = 0;
+  for (;;) {
+    STM_TRY(spmm_structured(F, H.mX, H.mB, H.mV, 1, s));
+    STM_TRY(col_norms(H.mV, beta));
+    bool any = false;
+    std::vector<int> active(32, 0), jd(32, 0);
+    for (int c = 0; c < 32; ++c) {
+      if (c < nrhs && bnorm[c] > 0.0) {
+        if (!std::isfinite(beta[c])) {
+          set_error("non-finite residual norm");
+          return STM_ERR_NONFINITE;
+        }
+        est[c] = beta[c] / bnorm[c];
+        if (beta[c] <= opts->rtol * bnorm[c]) conv[c] = 1;
+      }
+      active[c] = !conv[c] && it < opts->max_iter;
+      any = any || active[c];
+      fvec[c] = active[c] ? 1.0 / beta[c] : 0.0;
+    }
+    if (!any) break;
+    STM_CUDA(cudaMemcpyAsync(H.mf, fvec.data(), sizeof(double) * 32, cudaMemcpyHostToDevice, s));
+    STM_TRY(mscale(H.mV, H.mV, H.mf, N, s));
+    std::fill(Hm.begin(), Hm.end(), 0.0);
+    std::fill(g.begin(), g.end(), 0.0);
+    for (int c = 0; c < 32; ++c) g[c] = active[c] ? beta[c] : 0.0;  // g[j][c] at j * 32 + c
+    int jmax = 0;
+    for (int j = 0; j < m; ++j) {
+      double* vj = H.mV + j * VS;
+      double* zj = H.mZ + j * VS;
+      STM_TRY(vcycle_multi(H, vj, zj, s));
+      STM_TRY(spmm_structured(F, zj, nullptr, H.mW, 0, s));
+      {
+        ProfScope ps(&H, STM_KCLASS_KRYLOV, s, 8.0 * VS * (4.0 * (j + 1) + 4.0));
+        STM_TRY(mdots(H.mV, j + 1, H.mW, N, H.mh, H.mpart, nb, s));
+        STM_TRY(mupdate(H.mV, j + 1, H.mh, H.mW, N, -1.0, s));
+        STM_TRY(mdots(H.mV, j + 1, H.mW, N, H.mh + (m + 2) * 32, H.mpart, nb, s));
+        STM_TRY(mupdate(H.mV, j + 1, H.mh + (m + 2) * 32, H.mW, N, -1.0, s));
+        STM_TRY(madd_small(H.mh, H.mh + (m + 2) * 32, (j + 1) * 32, s));
+        STM_TRY(mdots(H.mW, 1, H.mW, N, H.mh + (j + 1) * 32, H.mpart, nb, s));
+      }
+      STM_CUDA(cudaMemcpyAsync(hbuf.data(), H.mh, sizeof(double) * (j + 2) * 32, cudaMemcpyDeviceToHost, s));
+      STM_CUDA(cudaStreamSynchronize(s));
+      ++it;
+      jmax = j + 1;
+      bool still = false;
+      for (int c = 0; c < 32; ++c) {
+        fvec[c] = 0.0;
+        if (!active[c]) continue;
+        auto Hc = [&](int r, int k) -> double& { return Hm[((size_t)r * m + k) * 32 + c]; };
+        const double hn = std::sqrt(hbuf[(j + 1) * 32 + c]);
+        if (!std::isfinite(hn)) {
+          set_error("non-finite Arnoldi norm");
+          return STM_ERR_NONFINITE;
+        }
+        for (int i = 0; i <= j; ++i) Hc(i, j) = hbuf[i * 32 + c];
+        Hc(j + 1, j) = hn;
+        for (int i = 0; i < j; ++i) {
+          const double a = Hc(i, j), b = Hc(i + 1, j);
+          Hc(i, j) = cs[i * 32 + c] * a + sn[i * 32 + c] * b;
+          Hc(i + 1, j) = -sn[i * 32 + c] * a + cs[i * 32 + c] * b;
+        }
+        const double a = Hc(j, j), b = Hc(j + 1, j);
+        const double rho = std::hypot(a, b);
+        cs[j * 32 + c] = a / rho;
+        sn[j * 32 + c] = b / rho;
+        Hc(j, j) = rho;
+        Hc(j + 1, j) = 0.0;
+        g[(j + 1) * 32 + c] = -sn[j * 32 + c] * g[j * 32 + c];
+        g[j * 32 + c] = cs[j * 32 + c] * g[j * 32 + c];
+        iters[c] += 1;
+        jd[c] = j + 1;
+        est[c] = std::fabs(g[(j + 1) * 32 + c]) / bnorm[c];
+        if (std::fabs(g[(j + 1) * 32 + c]) <= opts->rtol * bnorm[c] || hn == 0.0) {
+          conv[c] = 1;
+          active[c] = 0;
+        } else if (it >= opts->max_iter) {
+          active[c] = 0;
+        } else {
+          fvec[c] = 1.0 / hn;
+          still = true;
+        }
+      }
+      // next basis vector (columns that stopped get zeros)
+      STM_CUDA(cudaMemcpyAsync(H.mf, fvec.data(), sizeof(double) * 32, cudaMemcpyHostToDevice, s));
+      STM_TRY(mscale(H.mV + (j + 1) * VS, H.mW, H.mf, N, s));
+      if (!still) break;
+    }
+    // per column: y = H^{-1} g over its own jd columns, x += Z y
+    std::fill(yv.begin(), yv.end(), 0.0);
+    for (int c = 0; c < 32; ++c) {
+      for (int i = jd[c] - 1; i >= 0; --i) {
+        double t = g[i * 32 + c];
+        for (int k2 = i + 1; k2 < jd[c]; ++k2) t -= Hm[((size_t)i * m + k2) * 32 + c] * yv[k2 * 32 + c];
+        yv[i * 32 + c] = t / Hm[((size_t)i * m + i) * 32 + c];
+      }
+    }
+    STM_CUDA(cudaMemcpyAsync(H.my, yv.data(), sizeof(double) * jmax * 32, cudaMemcpyHostToDevice, s));
+    STM_TRY(mupdate(H.mZ, jmax, H.my, H.mX, N, 1.0, s));
+    for (int c = 0; c < 32; ++c)
+      if (!conv[c]) restarts[c] += 1;
+    if (it >= opts->max_iter) {
+      bool all = true;
+      for (int c = 0; c < nrhs; ++c) all = all && conv[c];
+      if (!all) break;
+    }
+  }
+  // true residuals
+  STM_TRY(spmm_structured(F, H.mX, H.mB, H.mW, 1, s));
+  double rn[32];
+  STM_TRY(col_norms(H.mW, rn));
+  STM_TRY(multi_from_interleaved(H.mX, X_dev, N, nrhs, s));
+  STM_CUDA(cudaStreamSynchronize(s));
+  bool all = true;
+  for (int c = 0; c < nrhs; ++c) {
+    relres[c] = bnorm[c] > 0.0 ? rn[c] / bnorm[c] : 0.0;
+    all = all && conv[c];
+    if (infos) {
+      infos[c].iters = iters[c];
+      infos[c].restarts = restarts[c];
+      infos[c].converged = conv[c];
+      infos[c].rel_res_true = relres[c];
+      infos[c].rel_res_est = est[c];
+    }
+  }
+  if (!all) {
+    set_error("multi-RHS FGMRES reached max_iter for some columns");
+    return STM_ERR_NOT_CONVERGED;
+  }
   return STM_OK;
 }
 

@@ -126,11 +126,6 @@ static stm_status upload(T** dst, const std::vector<T>& src) {
   STM_CUDA(cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice));
   return STM_OK;
 }
-#define STM_TRY(x)                       \
-  do {                                   \
-    stm_status s_ = (x);                 \
-    if (s_ != STM_OK) return s_;         \
-  } while (0)
 
 // ---------------------------------------------------------------------------------------------
 // Reference tables of a uniform level
@@ -697,11 +692,12 @@ void free_hierarchy(Hierarchy& H) {
                     L.node_cells, L.job_nodes,
                     L.colidx, L.val, L.valT, L.ref, L.inj, L.wnod, L.inv, L.wmult, L.own_ptr,
                     L.own_pos, L.last_owner, L.colour_cells, L.Y, L.P_rowptr, L.P_col, L.P_val,
-                    L.Rt_rowptr, L.Rt_col, L.Rt_val, L.d, L.r, L.t};
+                    L.Rt_rowptr, L.Rt_col, L.Rt_val, L.d, L.r, L.t, L.md, L.mr, L.mt, L.mY};
     for (void* q : ptrs)
       if (q) cudaFree(q);
   }
-  void* hp[] = {H.cinv, H.dflag, H.dbad, H.V, H.Z, H.w, H.hcol, H.part, H.yvec, H.bbuf, H.xbuf};
+  void* hp[] = {H.cinv, H.dflag, H.dbad, H.V, H.Z, H.w, H.hcol, H.part, H.yvec, H.bbuf, H.xbuf,
+                H.mV, H.mZ, H.mW, H.mB, H.mX, H.mh, H.mpart, H.mf, H.my};
   for (void* q : hp)
     if (q) cudaFree(q);
   for (ProfRec& r : H.prof.recs) {

@@ -26,6 +26,14 @@ stm_status cuda_fail(cudaError_t e, const char* what);
     if (e_ != cudaSuccess) return ::stm::cuda_fail(e_, #call);  \
   } while (0)
 
+#ifndef STM_TRY
+#define STM_TRY(x)               \
+  do {                           \
+    stm_status s_ = (x);         \
+    if (s_ != STM_OK) return s_; \
+  } while (0)
+#endif
+
 // Launch accounting and optional per-class CUDA-event timing --------------------------------
 extern std::atomic<long long> g_launches;
 inline void note_launch(long long n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
@@ -121,6 +129,8 @@ struct Level {
 
   // work vectors of the V-cycle
   double *d = nullptr, *r = nullptr, *t = nullptr;
+  // multi-right-hand-side work space ([N][32] interleaved; mY: [C*n][32]), allocated on first use
+  double *md = nullptr, *mr = nullptr, *mt = nullptr, *mY = nullptr;
 };
 
 struct Hierarchy {
@@ -144,6 +154,10 @@ struct Hierarchy {
   double* bbuf = nullptr;         // host-API staging for b and x
   double* xbuf = nullptr;
   int nblk_dot = 0;
+  // multi-right-hand-side FGMRES work space ([.][N][32])
+  int mrestart_cap = 0;
+  double *mV = nullptr, *mZ = nullptr, *mW = nullptr, *mB = nullptr, *mX = nullptr, *mh = nullptr, *mpart = nullptr,
+         *mf = nullptr, *my = nullptr;
   Profiler prof;
 };
 
@@ -193,6 +207,18 @@ stm_status coarse_apply(Hierarchy& H, const double* r, double* d, int transpose,
 stm_status assemble_cellvec(Hierarchy& H, int mode, double U, double nu, const int* wake_lo, const int* wake_hi,
                             double* out, cudaStream_t s);
 stm_status dnu_apply(Hierarchy& H, const double* x, double* y, cudaStream_t s);
+// multi-right-hand-side path (kernels_multi.cu), multi-vectors interleaved [N][32]
+stm_status multi_to_interleaved(const double* src, double* dst, long long N, int nrhs, cudaStream_t s);
+stm_status multi_from_interleaved(const double* src, double* dst, long long N, int nrhs, cudaStream_t s);
+stm_status spmm_structured(const Level& L, const double* X, const double* B, double* Y, int mode, cudaStream_t s);
+stm_status ensure_multi(Hierarchy& H);
+stm_status vanka_step_multi(Hierarchy& H, int g, const double* R, double* Dm, bool d_is_zero, cudaStream_t s);
+stm_status vcycle_multi(Hierarchy& H, const double* R_fine, double* D_fine, cudaStream_t s);
+stm_status mdots(const double* V, int nv, const double* w, long long n, double* out, double* part, int nblk,
+                 cudaStream_t s);
+stm_status mupdate(const double* V, int nv, const double* h, double* w, long long n, double sign, cudaStream_t s);
+stm_status mscale(double* y, const double* x, const double* f, long long n, cudaStream_t s);
+stm_status madd_small(double* a, const double* b, int n, cudaStream_t s);
 stm_status vcycle(Hierarchy& H, const double* r, double* d, int transpose, cudaStream_t s);
 
 // BLAS-1 style helpers on device vectors (kernels_krylov.cu)

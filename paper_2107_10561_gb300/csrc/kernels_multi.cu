@@ -1,0 +1,560 @@
+// Multi-right-hand-side path: up to 32 right-hand sides share one hierarchy (one J, one set of
+// cell inverses). Multi-vectors are stored interleaved, [N][32] FP64 (column c of DoF i at
+// i * 32 + c), so every gather of a DoF fetches its 32 values in one 256-byte line.
+//  * SpMM with J_g: the structured pattern of k_spmv_struct, one warp per node (cell) with the
+//    32 lanes on the 32 right-hand sides: each value of J is read once for all columns (broadcast).
+//  * Vanka local solves Y_T = J_T^{-1} T_T for a 32-column block (a6'' of the hot path): with BF16
+//    inverses on the tensor cores (mma.sync m16n8k16, FP32 accumulation); the gathered block T is
+//    split into T_hi + T_lo BF16 parts so that the only rounding is that of the stored inverse.
+//    FP32 / FP64 inverses use CUDA cores.
+//  * additive combine, transfers, coarse solve and the V-cycle (Algorithm 1) on 32 columns.
+#include <cstdint>
+#include <type_traits>
+
+#include "internal.h"
+
+namespace stm {
+
+constexpr int NR = 32;  // columns of a multi-vector
+
+static int msms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 152;
+  }
+  return n;
+}
+
+// ---------------------------------------------------------------------------------------------
+// layout conversion: column-major [nrhs][N] (ld N) <-> interleaved [N][32]
+// ---------------------------------------------------------------------------------------------
+__global__ void k_to_interleaved(const double* __restrict__ src, double* __restrict__ dst, long long N, int nrhs) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N * NR; e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / NR;
+    const int c = (int)(e - i * NR);
+    dst[e] = c < nrhs ? src[(long long)c * N + i] : 0.0;
+  }
+}
+__global__ void k_from_interleaved(const double* __restrict__ src, double* __restrict__ dst, long long N, int nrhs) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N * nrhs; e += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(e / N);
+    const long long i = e - (long long)c * N;
+    dst[e] = src[i * NR + c];
+  }
+}
+stm_status multi_to_interleaved(const double* src, double* dst, long long N, int nrhs, cudaStream_t s) {
+  k_to_interleaved<<<(int)std::min<long long>((N * NR + 255) / 256, msms() * 16LL), 256, 0, s>>>(src, dst, N, nrhs);
+  note_launch();
+  STM_CUDA(cudaGetLastError());
+  return STM_OK;
+}
+stm_status multi_from_interleaved(const double* src, double* dst, long long N, int nrhs, cudaStream_t s) {
+  k_from_interleaved<<<(int)std::min<long long>((N * nrhs + 255) / 256, msms() * 16LL), 256, 0, s>>>(src, dst, N, nrhs);
+  note_launch();
+  STM_CUDA(cudaGetLastError());
+  return STM_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// SpMM with J_g (FP64): mode 0: Y = J X; 1: Y = B - J X
+// ---------------------------------------------------------------------------------------------
+template <int K, int D>
+__global__ void __launch_bounds__(256) k_spmm_struct(
+    const long long* __restrict__ rowptr, const double* __restrict__ val, const int* __restrict__ nbr_ptr,
+    const int* __restrict__ nbr, const int* __restrict__ ncell, const int* __restrict__ node_cells,
+    const int* __restrict__ cell_nodes, long long block, int R, int C, int nv, const double* __restrict__ X,
+    const double* __restrict__ B, double* __restrict__ Y, int mode) {
+  constexpr int KD = K * D;
+  constexpr int NP = D + 1;
+  constexpr int MAXC = 1 << D;
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long job = warp; job < (long long)R + C; job += nwarps) {
+    if (job < R) {
+      const int i = (int)job;
+      const int p0 = nbr_ptr[i], nn = nbr_ptr[i + 1] - p0, nc = ncell[i];
+      long long rp[KD];
+      double acc[KD];
+#pragma unroll
+      for (int a = 0; a < K; ++a)
+#pragma unroll
+        for (int l = 0; l < D; ++l) {
+          rp[a * D + l] = rowptr[a * block + (long long)l * R + i];
+          acc[a * D + l] = 0.0;
+        }
+      for (int j = 0; j < nn; ++j) {
+        const long long nj = nbr[p0 + j];
+#pragma unroll
+        for (int bb = 0; bb < K; ++bb)
+#pragma unroll
+          for (int m = 0; m < D; ++m) {
+            const double xv = X[(bb * block + (long long)m * R + nj) * NR + lane];
+#pragma unroll
+            for (int a = 0; a < K; ++a) {
+              const long long off = (long long)bb * D * nn + (bb > a ? NP * nc : 0) + (long long)m * nn + j;
+#pragma unroll
+              for (int l = 0; l < D; ++l) acc[a * D + l] += __ldg(val + rp[a * D + l] + off) * xv;
+            }
+          }
+      }
+      for (int t = 0; t < NP * nc; ++t) {
+        const int ci = t / NP, q = t - ci * NP;
+        const long long pc = (long long)D * R + (long long)node_cells[(long long)i * MAXC + ci] * NP + q;
+#pragma unroll
+        for (int a = 0; a < K; ++a) {
+          const double xp = X[(a * block + pc) * NR + lane];
+#pragma unroll
+          for (int l = 0; l < D; ++l) acc[a * D + l] += __ldg(val + rp[a * D + l] + (long long)(a + 1) * D * nn + t) * xp;
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < K; ++a)
+#pragma unroll
+        for (int l = 0; l < D; ++l) {
+          const long long o = (a * block + (long long)l * R + i) * NR + lane;
+          Y[o] = mode == 1 ? B[o] - acc[a * D + l] : acc[a * D + l];
+        }
+    } else {
+      const long long c = job - R;
+      long long rp[K * NP];
+      double acc[K * NP];
+#pragma unroll
+      for (int a = 0; a < K; ++a)
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+          rp[a * NP + q] = rowptr[a * block + (long long)D * R + c * NP + q];
+          acc[a * NP + q] = 0.0;
+        }
+      for (int t = 0; t < D * nv; ++t) {
+        const int m = t / nv, jj = t - m * nv;
+        const long long node = cell_nodes[c * nv + jj];
+#pragma unroll
+        for (int a = 0; a < K; ++a) {
+          const double xa = X[(a * block + (long long)m * R + node) * NR + lane];
+#pragma unroll
+          for (int q = 0; q < NP; ++q) acc[a * NP + q] += __ldg(val + rp[a * NP + q] + t) * xa;
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < K; ++a)
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+          const long long o = (a * block + (long long)D * R + c * NP + q) * NR + lane;
+          Y[o] = mode == 1 ? B[o] - acc[a * NP + q] : acc[a * NP + q];
+        }
+    }
+  }
+}
+
+stm_status spmm_structured(const Level& L, const double* X, const double* B, double* Y, int mode, cudaStream_t s) {
+  const long long jobs = (long long)L.R + L.C;
+  const int blocks = (int)std::min<long long>((jobs * 32 + 255) / 256, (long long)msms() * 8);
+  const int key = L.dim * 10 + L.K;
+#define SPMM(K, D) \
+  k_spmm_struct<K, D><<<blocks, 256, 0, s>>>(L.rowptr, L.val, L.nbr_ptr, L.nbr, L.ncell, L.node_cells, L.cell_nodes, \
+                                             L.block, L.R, L.C, L.nv, X, B, Y, mode)
+  switch (key) {
+    case 21: SPMM(1, 2); break;
+    case 22: SPMM(2, 2); break;
+    case 23: SPMM(3, 2); break;
+    case 31: SPMM(1, 3); break;
+    case 32: SPMM(2, 3); break;
+    case 33: SPMM(3, 3); break;
+    default:
+      set_error("multi-RHS SpMM: unsupported (dim, k)");
+      return STM_ERR_INVALID_ARG;
+  }
+#undef SPMM
+  note_launch();
+  STM_CUDA(cudaGetLastError());
+  return STM_OK;
+}
+
+// CSR (transfers) on 32 columns: warp per row, lane = column. mode 0: Y = A X; 2: Y += A X.
+__global__ void __launch_bounds__(256) k_csr_multi(const long long* __restrict__ rowptr, const int* __restrict__ col,
+                                                   const double* __restrict__ val, long long nrows,
+                                                   const double* __restrict__ X, double* __restrict__ Y, int mode) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long row = warp; row < nrows; row += nwarps) {
+    double s = 0.0;
+    for (long long e = rowptr[row]; e < rowptr[row + 1]; ++e) s += __ldg(val + e) * X[(long long)__ldg(col + e) * NR + lane];
+    if (mode == 2) Y[row * NR + lane] += s;
+    else Y[row * NR + lane] = s;
+  }
+}
+stm_status csr_multi(const long long* rowptr, const int* col, const double* val, long long nrows, const double* X,
+                     double* Y, int mode, cudaStream_t s) {
+  const int blocks = (int)std::min<long long>((nrows * 32 + 255) / 256, (long long)msms() * 8);
+  k_csr_multi<<<blocks, 256, 0, s>>>(rowptr, col, val, nrows, X, Y, mode);
+  note_launch();
+  STM_CUDA(cudaGetLastError());
+  return STM_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Vanka local solves on 32 columns
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(smem)), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(smem)), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::); }
+__device__ __forceinline__ void ldmatrix_x4_trans(unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3,
+                                                  const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(smem_addr(p)));
+}
+__device__ __forceinline__ void mma_bf16(float* c, unsigned a0, unsigned a1, unsigned a2, unsigned a3, unsigned b0,
+                                         unsigned b1) {
+  asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+               : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+               : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// Tensor-core geometry of one level (BF16 inverses).
+struct TCGeom {
+  int n, ld;      // local size and stored leading dimension (rows, multiple of 8)
+  int MT, KT;     // 16-row tiles of the output / 16-wide steps of the contraction
+  int lds;        // shared-memory row length (elements) of the A tile, conflict-free for ldmatrix
+  int ldt;        // shared-memory row length of the T tiles
+};
+
+// Y_T[n][32] = Inv_T[n][n] (BF16, column-major with leading dimension ld) * T_T[n][32].
+// Shared memory: A tile stored as in global (one "row" per column j, i contiguous), padded with
+// zeros to KT*16 columns and MT*16 rows; T_hi / T_lo as [32][ldt] (k contiguous per column).
+// Warp w computes output row tiles w, w + nwarps, ... over all 4 column tiles of 8.
+__global__ void __launch_bounds__(256) k_vanka_mrhs_tc(const __nv_bfloat16* __restrict__ inv,
+                                                       const int* __restrict__ idx, const double* __restrict__ T,
+                                                       double* __restrict__ Yout, int ncells, TCGeom g) {
+  extern __shared__ __align__(16) unsigned char smb[];
+  __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(smb);                 // [KT*16][lds]
+  __nv_bfloat16* Th = As + (size_t)g.KT * 16 * g.lds;                         // [32][ldt]
+  __nv_bfloat16* Tl = Th + (size_t)NR * g.ldt;                                // [32][ldt]
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarps = nth >> 5;
+  // zero the padding once: columns j >= n of A, rows i >= ld of A, k >= n of T
+  for (int e = tid; e < g.KT * 16 * g.lds; e += nth) {
+    const int j = e / g.lds, i = e - j * g.lds;
+    if (j >= g.n || i >= g.ld) As[e] = __float2bfloat16(0.0f);
+  }
+  for (int e = tid; e < NR * g.ldt; e += nth) {
+    const int k = e % g.ldt;
+    if (k >= g.n) {
+      Th[e] = __float2bfloat16(0.0f);
+      Tl[e] = __float2bfloat16(0.0f);
+    }
+  }
+  // 16-byte copies when the stored columns are 16-byte aligned (ld % 8 == 0), 4-byte copies otherwise
+  const int ch_el = (g.ld % 8 == 0) ? 8 : 2;
+  const int chunks_per_col = g.ld / ch_el;
+  for (int c = blockIdx.x; c < ncells; c += gridDim.x) {
+    __syncthreads();
+    // A: asynchronous 16-byte copies of the stored columns
+    const __nv_bfloat16* M = inv + (size_t)c * g.n * g.ld;
+    for (int e = tid; e < g.n * chunks_per_col; e += nth) {
+      const int j = e / chunks_per_col, ch = e - j * chunks_per_col;
+      if (ch_el == 8) cp_async16(As + (size_t)j * g.lds + ch * 8, M + (size_t)j * g.ld + ch * 8);
+      else cp_async4(As + (size_t)j * g.lds + ch * 2, M + (size_t)j * g.ld + ch * 2);
+    }
+    // T: gather 32 columns of every local DoF, split into BF16 hi + lo
+    const int* ic = idx + (long long)c * g.n;
+    for (int e = tid; e < g.n * NR; e += nth) {
+      const int k = e / NR, col = e - k * NR;
+      const double v = T[(long long)ic[k] * NR + col];
+      const __nv_bfloat16 hi = __double2bfloat16(v);
+      const __nv_bfloat16 lo = __double2bfloat16(v - (double)__bfloat162float(hi));
+      Th[col * g.ldt + k] = hi;
+      Tl[col * g.ldt + k] = lo;
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    const int gq = lane >> 2, tq = lane & 3;
+    for (int mt = warp; mt < g.MT; mt += nwarps) {
+      float acc[4][4];
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[nt][r] = 0.0f;
+      for (int kt = 0; kt < g.KT; ++kt) {
+        // A fragments (row-major 16x16 tile of Inv) from the column-major tile by a transposed ldmatrix:
+        // sub-matrices (rows +0/+8, k +0/+8) for lanes 0-7, 8-15, 16-23, 24-31
+        const int sub = lane >> 3, r8 = lane & 7;
+        const int io = (sub & 1) * 8, ko = (sub >> 1) * 8;
+        unsigned a0, a1, a2, a3;
+        ldmatrix_x4_trans(a0, a1, a2, a3, As + (size_t)(kt * 16 + ko + r8) * g.lds + mt * 16 + io);
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+          const int ncol = nt * 8 + gq;
+          const unsigned* th = reinterpret_cast<const unsigned*>(Th + ncol * g.ldt + kt * 16);
+          const unsigned* tl = reinterpret_cast<const unsigned*>(Tl + ncol * g.ldt + kt * 16);
+          mma_bf16(acc[nt], a0, a1, a2, a3, th[tq], th[tq + 4]);
+          mma_bf16(acc[nt], a0, a1, a2, a3, tl[tq], tl[tq + 4]);
+        }
+      }
+      // C fragment: rows gq / gq + 8, columns 2 tq, 2 tq + 1 of each 8-column tile
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        const int r0 = mt * 16 + gq, r1 = r0 + 8, cc = nt * 8 + 2 * tq;
+        if (r0 < g.n) {
+          Yout[((long long)c * g.n + r0) * NR + cc] = acc[nt][0];
+          Yout[((long long)c * g.n + r0) * NR + cc + 1] = acc[nt][1];
+        }
+        if (r1 < g.n) {
+          Yout[((long long)c * g.n + r1) * NR + cc] = acc[nt][2];
+          Yout[((long long)c * g.n + r1) * NR + cc + 1] = acc[nt][3];
+        }
+      }
+    }
+  }
+}
+
+// CUDA-core variant for FP32 / FP64 inverses: lane = column, warps over rows, Inv read by broadcast.
+template <typename S>
+__global__ void __launch_bounds__(256) k_vanka_mrhs_cc(const S* __restrict__ inv, const int* __restrict__ idx,
+                                                       const double* __restrict__ T, double* __restrict__ Yout,
+                                                       int ncells, int n, int ld) {
+  using A = typename std::conditional<sizeof(S) == 8, double, float>::type;
+  extern __shared__ __align__(16) unsigned char smc[];
+  A* Ts = reinterpret_cast<A*>(smc);  // [n][32]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int c = blockIdx.x; c < ncells; c += gridDim.x) {
+    __syncthreads();
+    const int* ic = idx + (long long)c * n;
+    for (int e = threadIdx.x; e < n * NR; e += blockDim.x) {
+      const int k = e / NR, col = e - k * NR;
+      Ts[e] = (A)T[(long long)ic[k] * NR + col];
+    }
+    __syncthreads();
+    const S* M = inv + (size_t)c * n * ld;
+    for (int i = warp; i < n; i += nwarps) {
+      A s = 0;
+      for (int j = 0; j < n; ++j) s += (A)M[(size_t)j * ld + i] * Ts[j * NR + lane];
+      Yout[((long long)c * n + i) * NR + lane] = (double)s;
+    }
+  }
+}
+
+// d[i][c] += omega / m_i * sum over the owners of i of Y[pos][c]
+__global__ void k_vanka_gather_multi(double* __restrict__ d, const double* __restrict__ Y, const int* __restrict__ own_ptr,
+                                     const int* __restrict__ own_pos, const double* __restrict__ wmult, long long N,
+                                     double omega) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N * NR; e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / NR;
+    const int col = (int)(e - i * NR);
+    double s = 0.0;
+    for (int p = own_ptr[i]; p < own_ptr[i + 1]; ++p) s += Y[(long long)own_pos[p] * NR + col];
+    d[e] += omega * wmult[i] * s;
+  }
+}
+
+static TCGeom tc_geometry(const Level& L, int ld) {
+  TCGeom g;
+  g.n = L.n;
+  g.ld = ld;
+  g.MT = (ld + 15) / 16;
+  g.KT = (L.n + 15) / 16;
+  g.lds = g.MT * 16 + 8;
+  g.ldt = g.KT * 16 + 8;
+  return g;
+}
+
+stm_status ensure_multi(Hierarchy& H) {
+  for (Level& L : H.L) {
+    if (L.mY && L.md) continue;
+    if (!L.md) {
+      STM_CUDA(cudaMalloc(&L.md, sizeof(double) * (size_t)L.N * NR));
+      STM_CUDA(cudaMalloc(&L.mr, sizeof(double) * (size_t)L.N * NR));
+      STM_CUDA(cudaMalloc(&L.mt, sizeof(double) * (size_t)L.N * NR));
+    }
+    if (!L.mY) STM_CUDA(cudaMalloc(&L.mY, sizeof(double) * (size_t)L.C * L.n * NR));
+  }
+  return STM_OK;
+}
+
+stm_status vanka_step_multi(Hierarchy& H, int g, const double* R, double* Dm, bool d_is_zero, cudaStream_t s) {
+  Level& L = H.L[g];
+  const double* T = R;
+  if (!d_is_zero) {
+    ProfScope ps(&H, STM_KCLASS_JACOBIAN_SPMV, s, 8.0 * (double)L.nnz + 24.0 * NR * (double)L.N, g);
+    STM_TRY(spmm_structured(L, Dm, R, L.mt, 1, s));
+    T = L.mt;
+  }
+  const int prec = H.p.inv_precision;
+  const InvLayout lay = inv_layout(L.n, prec);
+  {
+    ProfScope ps(&H, STM_KCLASS_VANKA_LOCAL, s,
+                 (double)L.C * ((double)L.n * L.n * (prec == STM_F64 ? 8 : prec == STM_F32 ? 4 : 2) + 4.0 * L.n +
+                                16.0 * NR * L.n),
+                 g);
+    if (prec == STM_BF16) {
+      const TCGeom tg = tc_geometry(L, lay.ld);
+      const size_t smem = sizeof(__nv_bfloat16) * ((size_t)tg.KT * 16 * tg.lds + 2 * (size_t)NR * tg.ldt);
+      STM_CUDA(cudaFuncSetAttribute(k_vanka_mrhs_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      const int threads = std::min(256, std::max(64, tg.MT * 32));
+      const int blocks = std::min(L.C, msms() * 4);
+      k_vanka_mrhs_tc<<<blocks, threads, smem, s>>>((const __nv_bfloat16*)L.inv, L.idx, T, L.mY, L.C, tg);
+    } else {
+      const size_t smem = (prec == STM_F64 ? 8 : 4) * (size_t)L.n * NR;
+      const int blocks = std::min(L.C, msms() * 8);
+      if (prec == STM_F64) {
+        STM_CUDA(cudaFuncSetAttribute(k_vanka_mrhs_cc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_vanka_mrhs_cc<double><<<blocks, 256, smem, s>>>((const double*)L.inv, L.idx, T, L.mY, L.C, L.n, lay.ld);
+      } else {
+        STM_CUDA(cudaFuncSetAttribute(k_vanka_mrhs_cc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_vanka_mrhs_cc<float><<<blocks, 256, smem, s>>>((const float*)L.inv, L.idx, T, L.mY, L.C, L.n, lay.ld);
+      }
+    }
+    note_launch();
+    STM_CUDA(cudaGetLastError());
+  }
+  ProfScope ps(&H, STM_KCLASS_VANKA_COMBINE, s, 0.0, g);
+  const int blocks = (int)std::min<long long>((L.N * NR + 255) / 256, msms() * 16LL);
+  k_vanka_gather_multi<<<blocks, 256, 0, s>>>(Dm, L.mY, L.own_ptr, L.own_pos, L.wmult, L.N, H.p.omega);
+  note_launch();
+  STM_CUDA(cudaGetLastError());
+  return STM_OK;
+}
+
+// Coarse solve on 32 columns: D = Cinv R (FP64), warp per row of Cinv, lane = column.
+__global__ void __launch_bounds__(256) k_dense_gemm_multi(const double* __restrict__ A, long long n,
+                                                          const double* __restrict__ R, double* __restrict__ Dm) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long row = warp; row < n; row += nwarps) {
+    const double* a = A + row * n;
+    double s = 0.0;
+    for (long long k = 0; k < n; ++k) s += __ldg(a + k) * R[k * NR + lane];
+    Dm[row * NR + lane] = s;
+  }
+}
+
+stm_status vcycle_multi(Hierarchy& H, const double* R_fine, double* D_fine, cudaStream_t s) {
+  const int G = (int)H.L.size();
+  const double* r = R_fine;
+  for (int g = G - 1; g >= 1; --g) {
+    Level& L = H.L[g];
+    double* d = (g == G - 1) ? D_fine : L.md;
+    STM_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * (size_t)L.N * NR, s));
+    for (int it = 0; it < H.p.nu1; ++it) STM_TRY(vanka_step_multi(H, g, r, d, it == 0, s));
+    if (H.p.nu1 > 0) {
+      STM_TRY(spmm_structured(L, d, r, L.mt, 1, s));
+    } else {
+      STM_CUDA(cudaMemcpyAsync(L.mt, r, sizeof(double) * (size_t)L.N * NR, cudaMemcpyDeviceToDevice, s));
+    }
+    Level& Lc = H.L[g - 1];
+    {
+      ProfScope ps(&H, STM_KCLASS_TRANSFER, s, 0.0);
+      STM_TRY(csr_multi(L.Rt_rowptr, L.Rt_col, L.Rt_val, Lc.N, L.mt, Lc.mr, 0, s));
+    }
+    r = Lc.mr;
+  }
+  {
+    ProfScope ps(&H, STM_KCLASS_COARSE, s, 8.0 * (double)H.N0 * H.N0);
+    const int blocks = (int)std::min<long long>((H.N0 * 32 + 255) / 256, (long long)msms() * 8);
+    k_dense_gemm_multi<<<blocks, 256, 0, s>>>(H.cinv, H.N0, r, H.L[0].md);
+    note_launch();
+    STM_CUDA(cudaGetLastError());
+  }
+  for (int g = 1; g < G; ++g) {
+    Level& L = H.L[g];
+    double* d = (g == G - 1) ? D_fine : L.md;
+    const double* rg = (g == G - 1) ? R_fine : L.mr;
+    {
+      ProfScope ps(&H, STM_KCLASS_TRANSFER, s, 0.0);
+      STM_TRY(csr_multi(L.P_rowptr, L.P_col, L.P_val, L.N, H.L[g - 1].md, d, 2, s));
+    }
+    for (int it = 0; it < H.p.nu2; ++it) STM_TRY(vanka_step_multi(H, g, rg, d, false, s));
+  }
+  return STM_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Krylov building blocks on 32 columns (column-wise dot products, updates, scaling)
+// ---------------------------------------------------------------------------------------------
+// part[v][blk][c] = partial of sum_i V_v[i][c] w[i][c]; threads: lane = column, warps stride rows
+__global__ void __launch_bounds__(256) k_mdots_partial(const double* __restrict__ V, int nv, const double* __restrict__ w,
+                                                       long long n, double* __restrict__ part) {
+  __shared__ double red[8][NR];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int v = 0; v < nv; ++v) {
+    const double* a = V + (size_t)v * n * NR;
+    double s = 0.0;
+    for (long long i = (long long)blockIdx.x * nw + wid; i < n; i += (long long)gridDim.x * nw)
+      s += a[i * NR + lane] * w[i * NR + lane];
+    red[wid][lane] = s;
+    __syncthreads();
+    if (wid == 0) {
+      double t = 0.0;
+      for (int k = 0; k < nw; ++k) t += red[k][lane];
+      part[((size_t)v * gridDim.x + blockIdx.x) * NR + lane] = t;
+    }
+    __syncthreads();
+  }
+}
+__global__ void k_mdots_final(const double* __restrict__ part, int nv, int nblk, double* __restrict__ out) {
+  const int v = blockIdx.x, lane = threadIdx.x;
+  if (v >= nv || lane >= NR) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += part[((size_t)v * nblk + b) * NR + lane];
+  out[v * NR + lane] = s;
+}
+stm_status mdots(const double* V, int nv, const double* w, long long n, double* out, double* part, int nblk,
+                 cudaStream_t s) {
+  k_mdots_partial<<<nblk, 256, 0, s>>>(V, nv, w, n, part);
+  note_launch();
+  k_mdots_final<<<nv, 32, 0, s>>>(part, nv, nblk, out);
+  note_launch();
+  STM_CUDA(cudaGetLastError());
+  return STM_OK;
+}
+// w[i][c] -= sum_v h[v][c] V_v[i][c]   (sign = -1)   or   x[i][c] += sum_v h[v][c] Z_v[i][c] (sign = +1)
+__global__ void k_mupdate(const double* __restrict__ V, int nv, const double* __restrict__ h, double* __restrict__ w,
+                          long long n, double sign) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n * NR; e += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(e % NR);
+    double s = w[e];
+    for (int v = 0; v < nv; ++v) s += sign * h[v * NR + c] * V[(size_t)v * n * NR + e];
+    w[e] = s;
+  }
+}
+stm_status mupdate(const double* V, int nv, const double* h, double* w, long long n, double sign, cudaStream_t s) {
+  k_mupdate<<<(int)std::min<long long>((n * NR + 255) / 256, msms() * 16LL), 256, 0, s>>>(V, nv, h, w, n, sign);
+  note_launch();
+  STM_CUDA(cudaGetLastError());
+  return STM_OK;
+}
+// y[i][c] = x[i][c] * f[c]
+__global__ void k_mscale(double* __restrict__ y, const double* __restrict__ x, const double* __restrict__ f, long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n * NR; e += (long long)gridDim.x * blockDim.x)
+    y[e] = x[e] * f[e % NR];
+}
+stm_status mscale(double* y, const double* x, const double* f, long long n, cudaStream_t s) {
+  k_mscale<<<(int)std::min<long long>((n * NR + 255) / 256, msms() * 16LL), 256, 0, s>>>(y, x, f, n);
+  note_launch();
+  STM_CUDA(cudaGetLastError());
+  return STM_OK;
+}
+__global__ void k_madd_small(double* a, const double* b, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a[i] += b[i];
+}
+stm_status madd_small(double* a, const double* b, int n, cudaStream_t s) {
+  k_madd_small<<<1, 256, 0, s>>>(a, b, n);
+  note_launch();
+  STM_CUDA(cudaGetLastError());
+  return STM_OK;
+}
+
+}  // namespace stm

@@ -191,6 +191,29 @@ class Hierarchy:
                    "stm_dot")
         return out.value
 
+    def vanka_sweep_multi(self, level, R, D, stream=None):
+        """One additive smoothing step for every column of R, D: CUDA float64 [nrhs, n_dofs]."""
+        nrhs, n = R.shape
+        if tuple(D.shape) != (nrhs, n) or n != self.n_dofs(level):
+            raise ValueError("R and D must be [nrhs, n_dofs(level)]")
+        _lib.check(self.lib.stm_vanka_sweep_multi(self.h, level, nrhs, _ptr(R, nrhs * n, "R"), _ptr(D, nrhs * n, "D"),
+                                                  _stream(stream)), "stm_vanka_sweep_multi")
+
+    def gmres_solve_multi(self, B, X, rtol=1e-8, restart=30, max_iter=1000, use_x0=False, stream=None,
+                          raise_on_fail=True):
+        """Lock-stepped FGMRES for every column of B: CUDA float64 [nrhs <= 32, n_dofs]; returns per-column infos."""
+        nrhs, n = B.shape
+        if tuple(X.shape) != (nrhs, n) or n != self.n_dofs():
+            raise ValueError("B and X must be [nrhs, n_dofs]")
+        o = self._opts(restart, max_iter, rtol, False, use_x0)
+        infos = (_lib.SolveInfo * nrhs)()
+        st = self.lib.stm_gmres_solve_multi(self.h, nrhs, _ptr(B, nrhs * n, "B"), _ptr(X, nrhs * n, "X"), C.byref(o),
+                                            infos, _stream(stream))
+        out = [self._info(i) for i in infos]
+        if st != _lib.STM_OK and raise_on_fail:
+            _lib.check(st, "stm_gmres_solve_multi")
+        return out
+
     def profile_enable(self, enable=True):
         _lib.check(self.lib.stm_profile_enable(self.h, int(enable)), "stm_profile_enable")
 
