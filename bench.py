@@ -37,6 +37,7 @@ def parse():
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--precisions", default="f64,f32,bf16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--multi-restart", type=int, default=20)
     ap.add_argument("--oracle-child", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -275,6 +276,85 @@ def gpu_leg(args, rank, world, local_rank):
     return wl, sizes, results, head, clocks, e2e_s, dist
 
 
+def gpu_leg_multi(args, local_rank):
+    """Multi-RHS workload: 32 right-hand sides b(U_j, nu) + c(w, w) sharing one hierarchy."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2107_10561_gb300 import Hierarchy, make_params
+    from paper_2107_10561_gb300 import build as _build
+
+    torch.cuda.set_device(local_rank)
+    _build.build()
+    wl = workload(args.workload)
+    nrhs = wl.extra["nrhs"]
+    prec = args.precisions.split(",")[-1]
+    p = make_params(wl.dim, wl.k, wl.n_levels, wl.coarse_cells, wl.length, wl.obstacle_lo, wl.obstacle_hi,
+                    wl.tau, wl.nu, wl.gamma1, wl.gamma2, prec, "additive", wl.omega, wl.nu1, wl.nu2)
+    t0 = time.perf_counter()
+    h = Hierarchy(p)
+    build_s = time.perf_counter() - t0
+    idx = h.dof_lattice_index()
+    X = torch.from_numpy(np.ascontiguousarray(synth.linearisation_point(wl).reshape(-1)[idx])).cuda()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    torch.cuda.synchronize()
+    e0.record()
+    h.assemble_jacobian(X)
+    e1.record()
+    h.factor_cells()
+    e2.record()
+    torch.cuda.synchronize()
+    n = h.n_dofs()
+    B = torch.empty((nrhs, n), dtype=torch.float64, device="cuda")
+    for c, U in enumerate(synth.inflow_sweep(nrhs)):
+        h.assemble_rhs(float(U), wl.nu, B[c], which=0)
+    Xs = torch.zeros_like(B)
+    for _ in range(args.warmup):
+        Xs.zero_()
+        infos = h.gmres_solve_multi(B, Xs, rtol=args.rtol, restart=args.multi_restart)
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    h.profile_enable(True)
+    launches0 = Hierarchy.kernel_launches()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        Xs.zero_()
+        infos = h.gmres_solve_multi(B, Xs, rtol=args.rtol, restart=args.multi_restart)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    clocks = sampler.stop()
+    kern = {k: h.profile_read(k) for k in ("vanka_local", "jacobian_spmv", "vanka_combine", "transfer", "coarse",
+                                           "krylov")}
+    fin = h.profile_read("vanka_local", wl.n_levels - 1)
+    sizes = [h.sizes(g) for g in range(wl.n_levels)]
+    pk = peaks()
+    hbm = pk["hbm_gbs"] if pk else 6800.0
+    ach = fin["bytes"] / (fin["ms"] * 1e-3) / 1e9 if fin["ms"] > 0 else None
+    cfg = describe(wl, sizes)
+    cfg.update({"rtol": args.rtol, "nrhs": nrhs, "rhs": "b(U_j, nu) + c(w, w), U_j = linspace(0.2, 0.45, 32)",
+                "restart": args.multi_restart, "parallelism": "single GPU",
+                "l2": "inputs larger than L2 (finest J %.1f GB)" % (sizes[-1]["nnz"] * 12 / 1e9)})
+    line = {"metric": "GMG-GMRES s to 1e-8 rel. res (mixed vs FP64, one GB300); Vanka sweep GB/s",
+            "value": ms / 1e3, "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": f"f64 Krylov/SpMM/coarse + {prec} cell inverses ({'tensor cores, ' if prec == 'bf16' else ''}f32 accumulate)",
+            "data": "synthetic", "config": cfg, "per_rhs_s": ms / 1e3 / nrhs,
+            "iters": [i["iters"] for i in infos], "max_rel_res_true": max(i["rel_res_true"] for i in infos),
+            "setup": {"build_hierarchy_s": build_s, "assemble_ms": e0.elapsed_time(e1), "factor_ms": e1.elapsed_time(e2)},
+            "kernel_ms_per_solve": {k: v["ms"] / args.steps for k, v in kern.items()},
+            "gpu_launches": int(Hierarchy.kernel_launches() - launches0),
+            "roofline": {"kernel": f"k_vanka_mrhs ({prec}), finest level, 32 columns", "bound": "hbm",
+                         "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm if ach else None,
+                         "traffic": None, "avg_launch_us": 1e3 * fin["ms"] / max(fin["launches"], 1)},
+            "clocks": clocks, "cpu_baseline": None,
+            "cpu_baseline_note": "the FP64 oracle of this workload needs ~70 GB of host memory and hours; not timed"}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.oracle_child:
@@ -302,6 +382,10 @@ def main():
         print(json.dumps(line))
         return
 
+    if workload(args.workload).extra.get("nrhs"):
+        if rank == 0:
+            gpu_leg_multi(args, local_rank)
+        return
     wl, sizes, results, head, clocks, e2e_s, dist = gpu_leg(args, rank, world, local_rank)
     if rank != 0:
         if dist:
