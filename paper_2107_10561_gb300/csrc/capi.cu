@@ -96,6 +96,7 @@ stm_status stm_dof_lattice_index(const stm_hierarchy* h, int level, long long* o
 stm_status stm_assemble_jacobian(stm_hierarchy* h, const double* X, double nu, void* stream) {
   if (!h || !X) return bad_arg("NULL argument");
   Hierarchy& H = h->H;
+  clear_graphs(H);
   STM_TRY(inject_linearisation(H, X, S(stream)));
   for (int g = 0; g < (int)H.L.size(); ++g) STM_TRY(assemble_level(H, g, nu, S(stream)));
   H.assembled = true;
@@ -112,6 +113,7 @@ stm_status stm_factor_cells(stm_hierarchy* h, void* stream, int* bad_level, long
   }
   if (bad_level) *bad_level = -1;
   if (bad_cell) *bad_cell = -1;
+  clear_graphs(H);
   cudaStream_t s = S(stream);
   for (int g = 1; g < (int)H.L.size(); ++g) {
     STM_CUDA(cudaMemsetAsync(H.dflag, 0, sizeof(int) * 2, s));
@@ -284,7 +286,7 @@ static stm_status gmres_core(Hierarchy& H, const double* b, double* x, const stm
     for (int j = 0; j < m; ++j) {
       double* vj = H.V + (size_t)j * N;
       double* zj = H.Z + (size_t)j * N;
-      STM_TRY(vcycle(H, vj, zj, tr, s));
+      STM_TRY(vcycle_graph(H, vj, zj, tr, s));
       STM_TRY(jacobian_apply(H, G - 1, zj, nullptr, H.w, 0, tr, s));
       // classical Gram-Schmidt, twice
       ProfScope ps(&H, STM_KCLASS_KRYLOV, s, 8.0 * N * (4.0 * (j + 1) + 4.0));

@@ -687,6 +687,9 @@ stm_status build_levels(Hierarchy& H) {
 }
 
 void free_hierarchy(Hierarchy& H) {
+  clear_graphs(H);
+  if (H.cap_stream) cudaStreamDestroy(H.cap_stream);
+  H.cap_stream = nullptr;
   for (Level& L : H.L) {
     void* ptrs[] = {L.idx, L.cell_nodes, L.cell_xyz, L.bmask, L.rank, L.cellrank, L.nn, L.ncell, L.rowptr, L.nbr_ptr, L.nbr,
                     L.node_cells, L.job_nodes,

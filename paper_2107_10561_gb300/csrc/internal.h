@@ -5,6 +5,8 @@
 #include <cuda_bf16.h>
 
 #include <atomic>
+#include <map>
+#include <tuple>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -159,6 +161,11 @@ struct Hierarchy {
   double *mV = nullptr, *mZ = nullptr, *mW = nullptr, *mB = nullptr, *mX = nullptr, *mh = nullptr, *mpart = nullptr,
          *mf = nullptr, *my = nullptr;
   Profiler prof;
+  // CUDA graphs of the V-cycle, one per (r, d, transpose) pointer triple; launched on the caller's
+  // stream, captured on a private stream (the legacy default stream cannot be captured)
+  bool use_graphs = true;
+  cudaStream_t cap_stream = nullptr;
+  std::map<std::tuple<const double*, double*, int>, std::pair<cudaGraphExec_t, long long>> vgraphs;
 };
 
 // Records CUDA events around the launches made in its lifetime when profiling is on.
@@ -220,6 +227,9 @@ stm_status mupdate(const double* V, int nv, const double* h, double* w, long lon
 stm_status mscale(double* y, const double* x, const double* f, long long n, cudaStream_t s);
 stm_status madd_small(double* a, const double* b, int n, cudaStream_t s);
 stm_status vcycle(Hierarchy& H, const double* r, double* d, int transpose, cudaStream_t s);
+// V-cycle through a cached CUDA graph (direct launches while profiling is on)
+stm_status vcycle_graph(Hierarchy& H, const double* r, double* d, int transpose, cudaStream_t s);
+void clear_graphs(Hierarchy& H);
 
 // BLAS-1 style helpers on device vectors (kernels_krylov.cu)
 stm_status vec_fill(double* x, double v, long long n, cudaStream_t s);

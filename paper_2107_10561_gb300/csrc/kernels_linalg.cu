@@ -220,6 +220,47 @@ stm_status vcycle(Hierarchy& H, const double* r_fine, double* d_fine, int transp
   return STM_OK;
 }
 
+void clear_graphs(Hierarchy& H) {
+  for (auto& kv : H.vgraphs) cudaGraphExecDestroy(kv.second.first);
+  H.vgraphs.clear();
+}
+
+stm_status vcycle_graph(Hierarchy& H, const double* r, double* d, int transpose, cudaStream_t s) {
+  if (H.prof.on || !H.use_graphs) return vcycle(H, r, d, transpose, s);
+  const auto key = std::make_tuple(r, d, transpose);
+  auto it = H.vgraphs.find(key);
+  if (it == H.vgraphs.end()) {
+    if (transpose)
+      for (int g = 0; g < (int)H.L.size(); ++g) STM_TRY(ensure_transpose(H, g, s));
+    if (!H.cap_stream) STM_CUDA(cudaStreamCreateWithFlags(&H.cap_stream, cudaStreamNonBlocking));
+    const long long before = g_launches.load();
+    STM_CUDA(cudaStreamBeginCapture(H.cap_stream, cudaStreamCaptureModeThreadLocal));
+    const stm_status st = vcycle(H, r, d, transpose, H.cap_stream);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(H.cap_stream, &graph);
+    const long long kernels = g_launches.load() - before;
+    g_launches.fetch_sub(kernels);  // counted again on every graph launch
+    if (st != STM_OK || ce != cudaSuccess || !graph) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      H.use_graphs = false;  // capture not possible here: launch directly from now on
+      return vcycle(H, r, d, transpose, s);
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+      cudaGetLastError();
+      H.use_graphs = false;
+      return vcycle(H, r, d, transpose, s);
+    }
+    it = H.vgraphs.emplace(key, std::make_pair(exec, kernels)).first;
+  }
+  STM_CUDA(cudaGraphLaunch(it->second.first, s));
+  note_launch(it->second.second);
+  return STM_OK;
+}
+
 // ---------------------------------------------------------------------------------------------
 // Krylov helpers
 // ---------------------------------------------------------------------------------------------

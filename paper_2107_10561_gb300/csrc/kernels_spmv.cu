@@ -64,7 +64,7 @@ __device__ __forceinline__ int scatter_index(int lane, int* writer_mask) {
 }
 
 template <int VL, int K, int D>
-__global__ void __launch_bounds__(256) k_spmv_struct(
+__global__ void __launch_bounds__(256, 4) k_spmv_struct(
     const long long* __restrict__ rowptr, const double* __restrict__ val, const int* __restrict__ nbr_ptr,
     const int* __restrict__ nbr, const int* __restrict__ ncell, const int* __restrict__ node_cells,
     const int* __restrict__ cell_nodes, const int* __restrict__ job_nodes, long long block, int R, int C, int nv,
