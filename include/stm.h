@@ -255,6 +255,10 @@ stm_status stm_profile_enable(stm_hierarchy* h, int enable);
  * profiling was enabled. Per-level figures exist for VANKA_LOCAL, VANKA_COMBINE, JACOBIAN_SPMV. */
 stm_status stm_profile_read(stm_hierarchy* h, int kernel_class, int level, double* total_ms, long long* launches,
                             double* bytes);
+/* Measured FP64 FMA throughput of the current device in TFLOP/s (8 independent FMA chains per thread,
+ * best of two timed runs). The FP64 products with J are bound by this rate on GB300. Synchronous. */
+stm_status stm_measure_fp64_peak(double* tflops, void* stream);
+
 /* Number of kernel launches issued by this library in this process so far. */
 long long stm_kernel_launches(void);
 

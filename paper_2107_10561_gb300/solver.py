@@ -226,6 +226,13 @@ class Hierarchy:
         return dict(ms=ms.value, launches=n.value, bytes=by.value)
 
     @staticmethod
+    def measure_fp64_peak(stream=None):
+        out = C.c_double()
+        lib = _lib.load()
+        _lib.check(lib.stm_measure_fp64_peak(C.byref(out), _stream(stream)), "stm_measure_fp64_peak")
+        return out.value
+
+    @staticmethod
     def kernel_launches():
         return int(_lib.load().stm_kernel_launches())
 
