@@ -153,25 +153,31 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
-def recorded_traffic(workload_name, prec):
-    """DRAM bytes per launch of the finest-level local-solve kernel from a committed ncu capture,
-    valid only while the kernel source is unchanged since the capture (sha256 of the file)."""
+def recorded_traffic(workload_name, kernel, prec=None):
+    """DRAM bytes per launch of a finest-level kernel from a committed ncu capture, valid only
+    while the kernel's source file is unchanged since the capture (sha256 of the file)."""
     import hashlib
 
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "roofline_traffic.json")))
     except (OSError, ValueError):
         return None
-    src = os.path.join(ROOT, "paper_2107_10561_gb300", "csrc", "kernels_vanka.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
     for e in rec.get("captures", []):
-        if e.get("workload") == workload_name and e.get("precision") == prec and e.get("kernels_vanka_cu_sha256") == sha:
+        if e.get("workload") != workload_name or e.get("kernel") != kernel:
+            continue
+        if prec is not None and e.get("precision") != prec:
+            continue
+        try:
+            sha = hashlib.sha256(open(os.path.join(ROOT, e["source"]), "rb").read()).hexdigest()
+        except (OSError, KeyError):
+            continue
+        if sha == e.get("source_sha256"):
             return {"per_launch_bytes": e["dram_bytes_read"] + e["dram_bytes_write"], "source": e["profile"]}
     return None
 
 
-def spmv_roofline(r, wl, sizes, fp64_peak):
-    """Dominant kernel of the solve: the structured FP64 product with the finest J (FP64-pipe bound).
+def spmv_roofline(r, wl, sizes, fp64_peak, workload_name):
+    """Dominant kernel of the solve: the node-block FP64 product with the finest J (FP64-pipe bound).
 
     achieved = 2 * nnz FLOP per launch (one FMA per stored value) / average event time per launch;
     peak = FP64 FMA throughput measured in the same run (stm_measure_fp64_peak)."""
@@ -181,10 +187,14 @@ def spmv_roofline(r, wl, sizes, fp64_peak):
     nnz = sizes[-1]["nnz"]
     us = 1e3 * f["ms"] / f["launches"]
     achieved = 2.0 * nnz / (us * 1e-6) / 1e12
-    return {"kernel": "k_spmv_struct (J_g x, finest level, FP64)", "bound": "alu", "achieved": achieved,
+    traffic = recorded_traffic(workload_name, "k_spmv_nodeblock")
+    return {"kernel": "k_spmv_nodeblock (J_g x, finest level, FP64)", "bound": "alu", "achieved": achieved,
             "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak if fp64_peak else None,
-            "traffic": None, "peak_source": "FP64 FMA rate measured in this run (stm_measure_fp64_peak)",
+            "traffic": traffic["per_launch_bytes"] if traffic else None,
+            "traffic_source": traffic["source"] if traffic else "no capture of the current kernel source",
+            "peak_source": "FP64 FMA rate measured in this run (stm_measure_fp64_peak)",
             "flops_per_launch": 2.0 * nnz, "avg_launch_us": us,
+            "algorithmic_bytes_per_launch": f["bytes"] / f["launches"],
             "hbm_gbs_algorithmic": f["bytes"] / (f["ms"] * 1e-3) / 1e9}
 
 
@@ -287,6 +297,8 @@ def gpu_leg(args, rank, world, local_rank):
         r["kernels"] = {k: h.profile_read(k) for k in ("vanka_local", "jacobian_spmv", "vanka_combine", "transfer",
                                                        "coarse", "krylov")}
         r["finest"] = {k: h.profile_read(k, wl.n_levels - 1) for k in ("vanka_local", "jacobian_spmv")}
+        r["per_level"] = {k: [h.profile_read(k, g) for g in range(wl.n_levels)]
+                          for k in ("vanka_local", "jacobian_spmv", "vanka_combine", "transfer")}
         h.profile_enable(False)
     clocks = sampler.stop()
     fp64_peak = Hierarchy.measure_fp64_peak()
@@ -427,7 +439,8 @@ def main():
     r = results[head]
     vl = r["finest"]["vanka_local"]
     achieved = vl["bytes"] / (vl["ms"] * 1e-3) / 1e9 if vl["ms"] > 0 else None
-    traffic = recorded_traffic(args.workload, head)
+    vk = "k_vanka_warp" if sizes[-1]["n_local"] <= 64 else "k_vanka_local"
+    traffic = recorded_traffic(args.workload, vk, head)
     cfg = describe(wl, sizes)
     cfg["rtol"] = args.rtol
     inv_bytes = {"f64": 8, "f32": 4, "bf16": 2}
@@ -456,11 +469,13 @@ def main():
                              "finest_vanka_us": 1e3 * v["finest"]["vanka_local"]["ms"] / max(v["finest"]["vanka_local"]["launches"], 1),
                              "finest_spmv_us": 1e3 * v["finest"]["jacobian_spmv"]["ms"] / max(v["finest"]["jacobian_spmv"]["launches"], 1),
                              "kernel_ms_per_solve": {k: kv["ms"] / args.steps for k, kv in v["kernels"].items()},
+                             "us_per_launch_by_level": {k: [round(1e3 * e["ms"] / e["launches"], 2) if e["launches"] else None
+                                                            for e in lv] for k, lv in v["per_level"].items()},
                              "s_per_solve_profiled_pass": v["ms_per_solve_profiled"] / 1e3}
                          for p, v in results.items()},
         "gpu_launches": int(r["launches_per_step"] * args.steps),
-        "roofline": spmv_roofline(r, wl, sizes, fp64_peak),
-        "roofline_vanka_sweep": {"kernel": f"k_vanka_local (y_T = J_T^{{-1}} t_T), finest level, {head} inverses",
+        "roofline": spmv_roofline(r, wl, sizes, fp64_peak, args.workload),
+        "roofline_vanka_sweep": {"kernel": f"{vk} (y_T = J_T^{{-1}} t_T), finest level, {head} inverses",
                                  "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                                  "frac": (achieved / hbm) if achieved else None,
                                  "traffic": traffic["per_launch_bytes"] if traffic else None,

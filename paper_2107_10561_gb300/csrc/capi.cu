@@ -174,14 +174,14 @@ stm_status stm_restrict(stm_hierarchy* h, int level, const double* fine, double*
   if (!h || !fine || !coarse) return bad_arg("NULL argument");
   STM_TRY(need_level(h->H, level, 1));
   Level& L = h->H.L[level];
-  return csr_apply(L.Rt_rowptr, L.Rt_col, L.Rt_val, h->H.L[level - 1].N, L.P_nnz, fine, nullptr, coarse, 0, S(stream));
+  return transfer_restrict(L, h->H.L[level - 1], fine, coarse, S(stream));
 }
 
 stm_status stm_prolongate_add(stm_hierarchy* h, int level, const double* coarse, double* fine, void* stream) {
   if (!h || !fine || !coarse) return bad_arg("NULL argument");
   STM_TRY(need_level(h->H, level, 1));
   Level& L = h->H.L[level];
-  return csr_apply(L.P_rowptr, L.P_col, L.P_val, L.N, L.P_nnz, coarse, nullptr, fine, 2, S(stream));
+  return transfer_prolong_add(L, h->H.L[level - 1], coarse, fine, S(stream));
 }
 
 stm_status stm_coarse_solve(stm_hierarchy* h, const double* r, double* d, int transpose, void* stream) {
@@ -344,6 +344,13 @@ static stm_status gmres_core(Hierarchy& H, const double* b, double* x, const stm
       break;
     }
     ++inf.restarts;
+  }
+  int copy_timeout = 0;
+  STM_CUDA(cudaMemcpyAsync(&copy_timeout, H.dflag + 3, sizeof(int), cudaMemcpyDeviceToHost, s));
+  STM_CUDA(cudaStreamSynchronize(s));
+  if (copy_timeout) {
+    set_error("a bulk copy of cell inverses did not complete within its wait limit");
+    return STM_ERR_CUDA;
   }
   inf.iters = it;
   inf.converged = converged ? 1 : 0;

@@ -487,6 +487,16 @@ static stm_status build_level(const stm_params& p, int g, Level& L, std::vector<
   }
   for (int col = (1 << d); col < 9; ++col) L.colour_off[col] = (int)colour_cells.size();
 
+  std::vector<long long> nbase(R + 1, 0);
+  for (int nd = 0; nd < R; ++nd)
+    nbase[nd + 1] = nbase[nd] + (long long)(L.K * d) * ((long long)L.K * d * nn[nd] + (long long)np * ncell[nd]);
+  STM_TRY(upload(&L.nbase, nbase));
+  STM_CUDA(cudaMalloc((void**)&L.nval, sizeof(double) * nbase[R]));
+  {
+    const long long prows = ((long long)L.K * C * np + 31) / 32 * 32;
+    STM_CUDA(cudaMalloc((void**)&L.pvalT, sizeof(double) * prows * d * L.nv));
+    STM_CUDA(cudaMemset(L.pvalT, 0, sizeof(double) * prows * d * L.nv));
+  }
   std::vector<int> job_nodes(R);
   std::iota(job_nodes.begin(), job_nodes.end(), 0);
   std::stable_sort(job_nodes.begin(), job_nodes.end(), [&](int a, int b) {
@@ -636,6 +646,51 @@ static stm_status build_transfer(const Level& Cl, Level& F) {
         tval[dst] = pval[e];
       }
   }
+  // node lists and cell maps of the matrix-free transfers
+  {
+    std::vector<int> cptr(Cl.R + 1, 0);
+    for (int e : vcol) cptr[e + 1]++;
+    for (int i = 0; i < Cl.R; ++i) cptr[i + 1] += cptr[i];
+    std::vector<int> cnode(vcol.size());
+    std::vector<double> cw(vcol.size());
+    std::vector<int> fill(cptr.begin(), cptr.end() - 1);
+    for (int nd = 0; nd < F.R; ++nd)
+      for (int e = vptr[nd]; e < vptr[nd + 1]; ++e) {
+        const int dst = fill[vcol[e]]++;
+        cnode[dst] = nd;
+        cw[dst] = vval[e];
+      }
+    const int nch = 1 << d;
+    std::vector<int> parent(F.C), children((size_t)Cl.C * nch, -1);
+    std::vector<unsigned char> bits(F.C);
+    for (int c = 0; c < F.C; ++c) {
+      const int* xyz = &F.h_cell_xyz[3 * c];
+      long long pf = xyz[0] / 2 + (long long)Cl.cells[0] * (xyz[1] / 2 + (long long)Cl.cells[1] * (xyz[2] / 2));
+      int b = 0;
+      for (int m = 0; m < d; ++m) b |= (xyz[m] & 1) << m;
+      parent[c] = Cl.h_full_active[pf];
+      bits[c] = (unsigned char)b;
+      if (parent[c] < 0) {
+        set_error("transfer: fine cell without an active parent");
+        return STM_ERR_INVALID_ARG;
+      }
+      children[(size_t)parent[c] * nch + b] = c;
+    }
+    for (int v : children)
+      if (v < 0) {
+        set_error("transfer: active coarse cell with a removed child");
+        return STM_ERR_INVALID_ARG;
+      }
+    STM_TRY(upload(&F.tv_ptr, vptr));
+    STM_TRY(upload(&F.tv_node, vcol));
+    STM_TRY(upload(&F.tv_w, vval));
+    STM_TRY(upload(&F.tc_ptr, cptr));
+    STM_TRY(upload(&F.tc_node, cnode));
+    STM_TRY(upload(&F.tc_w, cw));
+    STM_TRY(upload(&F.cparent, parent));
+    STM_TRY(upload(&F.cbits, bits));
+    STM_TRY(upload(&F.cchildren, children));
+  }
   F.P_nnz = (long long)pcol.size();
   STM_TRY(upload(&F.P_rowptr, prow));
   STM_TRY(upload(&F.P_col, pcol));
@@ -682,6 +737,7 @@ stm_status build_levels(Hierarchy& H) {
     STM_TRY(upload(&L.inj, inj));
   }
   STM_CUDA(cudaMalloc((void**)&H.dflag, sizeof(int) * 4));
+  STM_CUDA(cudaMemset(H.dflag, 0, sizeof(int) * 4));
   STM_CUDA(cudaMalloc((void**)&H.dbad, sizeof(long long) * 2));
   return STM_OK;
 }
@@ -692,10 +748,11 @@ void free_hierarchy(Hierarchy& H) {
   H.cap_stream = nullptr;
   for (Level& L : H.L) {
     void* ptrs[] = {L.idx, L.cell_nodes, L.cell_xyz, L.bmask, L.rank, L.cellrank, L.nn, L.ncell, L.rowptr, L.nbr_ptr, L.nbr,
-                    L.node_cells, L.job_nodes,
+                    L.node_cells, L.job_nodes, L.nbase, L.nval, L.pvalT,
                     L.colidx, L.val, L.valT, L.ref, L.inj, L.wnod, L.inv, L.wmult, L.own_ptr,
                     L.own_pos, L.last_owner, L.colour_cells, L.Y, L.P_rowptr, L.P_col, L.P_val,
-                    L.Rt_rowptr, L.Rt_col, L.Rt_val, L.d, L.r, L.t, L.md, L.mr, L.mt, L.mY};
+                    L.Rt_rowptr, L.Rt_col, L.Rt_val, L.tv_ptr, L.tv_node, L.tv_w, L.tc_ptr, L.tc_node,
+                    L.tc_w, L.cparent, L.cbits, L.cchildren, L.d, L.r, L.t, L.md, L.mr, L.mt, L.mY};
     for (void* q : ptrs)
       if (q) cudaFree(q);
   }

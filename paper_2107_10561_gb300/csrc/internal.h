@@ -103,6 +103,14 @@ struct Level {
   int* nbr = nullptr;
   int* node_cells = nullptr;      // [R][2^d] cells containing each node, sorted, -1 padded
   int* job_nodes = nullptr;       // [R] node ids ordered by (neighbour count, cell count, id)
+  // node-block copy of the velocity-row values of J (forward SpMV): for node i, positions
+  // p = (b*d + m)*nn + j (velocity) then K*d*nn + ci*n_p + q (pressure of the node's cells), each
+  // position holding the K*d row values (a*d + l) contiguously; block of node i starts at nbase[i]
+  long long* nbase = nullptr;     // [R+1]
+  double* nval = nullptr;
+  // pressure rows pr = (a*C + c)*n_p + q of J, warp-transposed for the forward SpMV: entry
+  // t = m*nv + j of row pr at pvalT[((pr/32)*d*nv + t)*32 + pr%32] (rows padded to a multiple of 32)
+  double* pvalT = nullptr;
   int* ncell = nullptr;           // [R] number of cells containing the node
   long long* rowptr = nullptr;    // [N+1]
   int* colidx = nullptr;          // [nnz]
@@ -128,6 +136,14 @@ struct Level {
   long long* P_rowptr = nullptr; int* P_col = nullptr; double* P_val = nullptr;
   long long P_nnz = 0;
   long long* Rt_rowptr = nullptr; int* Rt_col = nullptr; double* Rt_val = nullptr;
+  // the same P without assembled blocks (single-right-hand-side V-cycle): the Q2 weights of a fine
+  // node are shared by every time node and velocity component, so one list per node serves all
+  // K*d blocks; the P1disc child map follows from the child's position bits in its parent
+  int* tv_ptr = nullptr; int* tv_node = nullptr; double* tv_w = nullptr;  // [R+1] fine node -> coarse
+  int* tc_ptr = nullptr; int* tc_node = nullptr; double* tc_w = nullptr;  // [R_c+1] coarse node -> fine
+  int* cparent = nullptr;         // [C] coarse cell containing each fine cell
+  unsigned char* cbits = nullptr; // [C] child position bits (bit m: upper half along axis m)
+  int* cchildren = nullptr;       // [C_c][2^d] fine cells of each coarse cell, by position bits
 
   // work vectors of the V-cycle
   double *d = nullptr, *r = nullptr, *t = nullptr;
@@ -204,8 +220,13 @@ stm_status ensure_transpose(Hierarchy& H, int g, cudaStream_t s);
 // y = alpha*A x + beta_y*y (+ b): mode 0: y = A x; 1: y = b - A x; 2: y += A x
 stm_status csr_apply(const long long* rowptr, const int* col, const double* val, long long nrows, long long nnz,
                      const double* x, const double* b, double* y, int mode, cudaStream_t s);
+// Matrix-free transfers between level g-1 and level g (kernels_transfer.cu)
+stm_status transfer_restrict(const Level& F, const Level& Cl, const double* fine, double* coarse, cudaStream_t s);
+stm_status transfer_prolong_add(const Level& F, const Level& Cl, const double* coarse, double* fine, cudaStream_t s);
 stm_status spmv_structured(const Level& L, const double* v, const double* x, const double* b, double* y, int mode,
                            cudaStream_t s);
+stm_status spmv_nodeblock(const Level& L, const double* x, const double* b, double* y, int mode, cudaStream_t s);
+stm_status build_nodeblock(Level& L, cudaStream_t s);
 stm_status jacobian_apply(Hierarchy& H, int g, const double* x, const double* b, double* y,
                           int mode, int transpose, cudaStream_t s);
 stm_status vanka_step(Hierarchy& H, int g, const double* r, double* d, int transpose,

@@ -250,7 +250,7 @@ stm_status assemble_level(Hierarchy& H, int g, double nu, cudaStream_t s) {
     cudaFree(L.valT);
     L.valT = nullptr;
   }
-  return STM_OK;
+  return build_nodeblock(L, s);
 }
 
 }  // namespace stm

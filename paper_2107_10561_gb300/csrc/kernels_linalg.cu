@@ -130,6 +130,7 @@ stm_status jacobian_apply(Hierarchy& H, int g, const double* x, const double* b,
     v = L.valT;
   }
   ProfScope ps(&H, STM_KCLASS_JACOBIAN_SPMV, s, 8.0 * (double)L.nnz + 24.0 * (double)L.N, g);
+  if (!transpose) return spmv_nodeblock(L, x, b, y, mode, s);
   return spmv_structured(L, v, x, b, y, mode, s);
 }
 
@@ -188,8 +189,8 @@ stm_status vcycle(Hierarchy& H, const double* r_fine, double* d_fine, int transp
     if (st != STM_OK) return st;
     Level& Lc = H.L[g - 1];
     {
-      ProfScope ps(&H, STM_KCLASS_TRANSFER, s, 0.0);
-      st = csr_apply(L.Rt_rowptr, L.Rt_col, L.Rt_val, Lc.N, L.P_nnz, L.t, nullptr, Lc.r, 0, s);
+      ProfScope ps(&H, STM_KCLASS_TRANSFER, s, 0.0, g);
+      st = transfer_restrict(L, Lc, L.t, Lc.r, s);
     }
     if (st != STM_OK) return st;
     r = Lc.r;
@@ -208,8 +209,8 @@ stm_status vcycle(Hierarchy& H, const double* r_fine, double* d_fine, int transp
     const double* rg = (g == G - 1) ? r_fine : L.r;
     stm_status st;
     {
-      ProfScope ps(&H, STM_KCLASS_TRANSFER, s, 0.0);
-      st = csr_apply(L.P_rowptr, L.P_col, L.P_val, L.N, L.P_nnz, H.L[g - 1].d, nullptr, d, 2, s);
+      ProfScope ps(&H, STM_KCLASS_TRANSFER, s, 0.0, g);
+      st = transfer_prolong_add(L, H.L[g - 1], H.L[g - 1].d, d, s);
     }
     if (st != STM_OK) return st;
     for (int it = 0; it < nu2; ++it) {

@@ -175,6 +175,220 @@ __global__ void __launch_bounds__(256, 4) k_spmv_struct(
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Node-block copy of the velocity rows and the forward product that reads it
+// ---------------------------------------------------------------------------------------------
+// One warp per node: CSR position pos of velocity row (a, l) -> node-block position p:
+//   pos < (a+1) d nn                 : p = pos                        (velocity blocks b <= a)
+//   next n_p nc entries (pressure)   : p = K d nn + (pos - (a+1) d nn)
+//   beyond                           : p = pos - n_p nc               (velocity blocks b > a)
+__global__ void k_build_nodeblock(const long long* __restrict__ rowptr, const double* __restrict__ val,
+                                  const int* __restrict__ nbr_ptr, const int* __restrict__ ncell,
+                                  const long long* __restrict__ nbase, double* __restrict__ nval, long long block,
+                                  int R, int K, int D, int NP) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const int KD = K * D;
+  for (long long i = warp; i < R; i += nwarps) {
+    const int nn = nbr_ptr[i + 1] - nbr_ptr[i], nc = ncell[i];
+    const int len = KD * nn + NP * nc;
+    for (int a = 0; a < K; ++a)
+      for (int l = 0; l < D; ++l) {
+        const long long rb = rowptr[a * block + (long long)l * R + i];
+        for (int pos = lane; pos < len; pos += 32) {
+          const int lim = (a + 1) * D * nn;
+          int p;
+          if (pos < lim) p = pos;
+          else if (pos < lim + NP * nc) p = KD * nn + (pos - lim);
+          else p = pos - NP * nc;
+          nval[nbase[i] + (long long)p * KD + a * D + l] = val[rb + pos];
+        }
+      }
+  }
+}
+
+// One thread per pressure row pr = (a*C + c)*n_p + q: its d*nv CSR entries (ordered m*nv + j, the
+// cell's nodes in ascending id) go to the warp-transposed copy.
+__global__ void k_build_pval(const long long* __restrict__ rowptr, const double* __restrict__ val,
+                             double* __restrict__ pvalT, long long block, int R, int C, int K, int D, int NP, int nv) {
+  const long long npr = (long long)K * C * NP;
+  const int dnv = D * nv;
+  for (long long pr = blockIdx.x * (long long)blockDim.x + threadIdx.x; pr < npr;
+       pr += (long long)gridDim.x * blockDim.x) {
+    const long long a = pr / ((long long)C * NP);
+    const long long row = a * block + (long long)D * R + (pr - a * C * NP);
+    const double* v = val + rowptr[row];
+    double* o = pvalT + ((pr >> 5) * dnv) * 32 + (pr & 31);
+    for (int t = 0; t < dnv; ++t) o[(long long)t * 32] = v[t];
+  }
+}
+
+stm_status build_nodeblock(Level& L, cudaStream_t s) {
+  const int blocks = (int)std::min<long long>(((long long)L.R * 32 + 255) / 256, 152LL * 8);
+  k_build_nodeblock<<<blocks, 256, 0, s>>>(L.rowptr, L.val, L.nbr_ptr, L.ncell, L.nbase, L.nval, L.block, L.R, L.K,
+                                           L.dim, L.np);
+  note_launch();
+  STM_CUDA(cudaGetLastError());
+  const long long npr = (long long)L.K * L.C * L.np;
+  const int pblocks = (int)std::min<long long>((npr + 255) / 256, 152LL * 8);
+  k_build_pval<<<std::max(pblocks, 1), 256, 0, s>>>(L.rowptr, L.val, L.pvalT, L.block, L.R, L.C, L.K, L.dim, L.np,
+                                                    L.nv);
+  note_launch();
+  STM_CUDA(cudaGetLastError());
+  return STM_OK;
+}
+
+// VL lanes per node walk the node's positions; each position's K*d row values are contiguous, so VL
+// consecutive positions are one contiguous run of VL*K*d doubles (whole lines even for VL = 4) and
+// all lanes stay busy; the K*d partial sums go through the reduce-scatter butterfly (few adds).
+template <int VL, int K, int D>
+__global__ void __launch_bounds__(256, (K == 3 ? 3 : 4)) k_spmv_nodeblock(
+    const long long* __restrict__ rowptr, const double* __restrict__ val, const double* __restrict__ nval,
+    const double* __restrict__ pvalT,
+    const long long* __restrict__ nbase, const int* __restrict__ nbr_ptr, const int* __restrict__ nbr,
+    const int* __restrict__ ncell, const int* __restrict__ node_cells, const int* __restrict__ cell_nodes,
+    const int* __restrict__ job_nodes, long long block, int R, int C, int nv, const double* __restrict__ x,
+    const double* __restrict__ b, double* __restrict__ y, int mode) {
+  constexpr int GPW = 32 / VL;
+  constexpr int KD = K * D;
+  constexpr int NP = D + 1;
+  constexpr int MAXC = 1 << D;
+  constexpr int NAV = pow2ceil(KD);
+  static_assert(NAV <= VL || VL >= 4, "group too small");
+  const int lane = threadIdx.x & (VL - 1);
+  const int gw = (threadIdx.x & 31) / VL;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  int wmask_v;
+  constexpr int NAV_R = NAV < VL ? NAV : VL;
+  const int kv = scatter_index<VL, NAV_R>(lane, &wmask_v);
+  for (long long wb = warp * GPW; wb < R; wb += nwarps * GPW) {
+    const long long job = wb + gw;
+    const bool ok = job < R;
+    const int i = ok ? job_nodes[job] : 0;
+    double acc[NAV];
+#pragma unroll
+    for (int r = 0; r < NAV; ++r) acc[r] = 0.0;
+    if (ok) {
+      const int p0 = nbr_ptr[i], nn = nbr_ptr[i + 1] - p0, nc = ncell[i];
+      const double* blk = nval + nbase[i];
+      const int npv = KD * nn;
+      int j = lane, bm = 0;
+      while (j >= nn) { j -= nn; ++bm; }
+      for (int p = lane; p < npv; p += VL) {
+        const int bb = bm / D, m = bm - bb * D;
+        const double xv = __ldg(x + bb * block + (long long)m * R + nbr[p0 + j]);
+        const double* v = blk + (long long)p * KD;
+#pragma unroll
+        for (int r = 0; r < KD; ++r) acc[r] += __ldcs(v + r) * xv;
+        j += VL;
+        while (j >= nn) { j -= nn; ++bm; }
+      }
+      for (int tq = lane; tq < NP * nc; tq += VL) {
+        const int ci = tq / NP, q = tq - ci * NP;
+        const long long pc = (long long)D * R + (long long)node_cells[(long long)i * MAXC + ci] * NP + q;
+        const double* v = blk + (long long)(npv + tq) * KD;
+#pragma unroll
+        for (int a = 0; a < K; ++a) {
+          const double xp = __ldg(x + a * block + pc);
+#pragma unroll
+          for (int l = 0; l < D; ++l) acc[a * D + l] += __ldcs(v + a * D + l) * xp;
+        }
+      }
+    }
+    if constexpr (NAV <= VL) {
+      reduce_scatter<VL, NAV>(acc, lane);
+      if (ok && kv < KD && (lane & wmask_v) == 0) {
+        const int a = kv / D, l = kv - a * D;
+        const long long row = a * block + (long long)l * R + i;
+        if (mode == 0) y[row] = acc[0];
+        else if (mode == 1) y[row] = b[row] - acc[0];
+        else y[row] += acc[0];
+      }
+    } else {
+      // more accumulators than lanes: plain butterfly sums, lane 0 writes all rows
+#pragma unroll
+      for (int r = 0; r < NAV; ++r)
+#pragma unroll
+        for (int off = VL / 2; off > 0; off >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], off, VL);
+      if (ok && lane == 0)
+#pragma unroll
+        for (int r = 0; r < KD; ++r) {
+          const int a = r / D, l = r - a * D;
+          const long long row = a * block + (long long)l * R + i;
+          if (mode == 0) y[row] = acc[r];
+          else if (mode == 1) y[row] = b[row] - acc[r];
+          else y[row] += acc[r];
+        }
+    }
+  }
+  // Pressure rows: one lane per row pr = (a*C + c)*n_p + q over the warp-transposed copy, so entry t
+  // of 32 consecutive rows is one contiguous 256-byte load; all lanes busy, no cross-lane sums.
+  {
+    constexpr int NV = D == 2 ? 9 : 27;
+    const long long tid_g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nthreads = (long long)gridDim.x * blockDim.x;
+    const long long npr = (long long)K * C * NP;
+    for (long long pr = tid_g; pr < npr; pr += nthreads) {
+      const int a = (int)(pr / ((long long)C * NP));
+      const long long cq = pr - (long long)a * C * NP;
+      const long long c = cq / NP;
+      const long long row = a * block + (long long)D * R + cq;
+      const double* vr = pvalT + ((pr >> 5) * (D * NV)) * 32 + (pr & 31);
+      const int* cn = cell_nodes + c * NV;
+      const double* xa = x + a * block;
+      double s = 0.0;
+#pragma unroll
+      for (int m = 0; m < D; ++m) {
+#pragma unroll 9
+        for (int jj = 0; jj < NV; ++jj)
+          s += __ldcs(vr + (m * NV + jj) * 32) * __ldg(xa + (long long)m * R + __ldg(cn + jj));
+      }
+      if (mode == 0) y[row] = s;
+      else if (mode == 1) y[row] = b[row] - s;
+      else y[row] += s;
+    }
+  }
+}
+
+static int sms_count();
+
+template <int VL, int K, int D>
+static void launch_nodeblock(const Level& L, const double* x, const double* b, double* y, int mode, cudaStream_t s) {
+  const long long threads_needed = (long long)std::max((long long)L.R * VL, (long long)L.C * K * (D + 1));
+  const int blocks = (int)std::min<long long>((threads_needed + 255) / 256, (long long)sms_count() * 4);
+  k_spmv_nodeblock<VL, K, D><<<blocks, 256, 0, s>>>(L.rowptr, L.val, L.nval, L.pvalT, L.nbase, L.nbr_ptr, L.nbr, L.ncell,
+                                                    L.node_cells, L.cell_nodes, L.job_nodes, L.block, L.R, L.C, L.nv,
+                                                    x, b, y, mode);
+}
+
+stm_status spmv_nodeblock(const Level& L, const double* x, const double* b, double* y, int mode, cudaStream_t s) {
+  // short groups (4 lanes in 2D, 8 in 3D) need at least ~1024 resident threads per SM to keep
+  // enough loads in flight; smaller levels use 16 lanes per node
+  const bool big = (long long)L.R * (L.dim == 2 ? 4 : 8) >= (long long)sms_count() * 1024;
+  switch (L.dim * 10 + L.K + (big ? 0 : 100)) {
+    case 21: launch_nodeblock<4, 1, 2>(L, x, b, y, mode, s); break;
+    case 22: launch_nodeblock<4, 2, 2>(L, x, b, y, mode, s); break;
+    case 23: launch_nodeblock<4, 3, 2>(L, x, b, y, mode, s); break;
+    case 31: launch_nodeblock<8, 1, 3>(L, x, b, y, mode, s); break;
+    case 32: launch_nodeblock<8, 2, 3>(L, x, b, y, mode, s); break;
+    case 33: launch_nodeblock<8, 3, 3>(L, x, b, y, mode, s); break;
+    case 121: launch_nodeblock<16, 1, 2>(L, x, b, y, mode, s); break;
+    case 122: launch_nodeblock<16, 2, 2>(L, x, b, y, mode, s); break;
+    case 123: launch_nodeblock<16, 3, 2>(L, x, b, y, mode, s); break;
+    case 131: launch_nodeblock<16, 1, 3>(L, x, b, y, mode, s); break;
+    case 132: launch_nodeblock<16, 2, 3>(L, x, b, y, mode, s); break;
+    case 133: launch_nodeblock<16, 3, 3>(L, x, b, y, mode, s); break;
+    default:
+      set_error("node-block SpMV: unsupported (dim, k)");
+      return STM_ERR_INVALID_ARG;
+  }
+  note_launch();
+  STM_CUDA(cudaGetLastError());
+  return STM_OK;
+}
+
 static int sms_count() {
   static int n = 0;
   if (!n) {

@@ -157,6 +157,85 @@ __global__ void __launch_bounds__(256) k_vanka_local(const S* __restrict__ inv, 
   }
 }
 
+// Small cells (n <= 64 and at most 32 vector chunks per column): one warp per cell and no CTA
+// barriers. Lane (rc, cg) = (lane % LDV, lane / LDV) owns rows rc*V..rc*V+V-1 and the columns
+// j = cg (mod Q); t_T sits in the warp's own shared slice; the Q partial sums of a row meet through
+// shuffles. The next cell's DoF ids are loaded before the current inverse is streamed and its t
+// values right after, so the gather latency overlaps the stream and the epilogue.
+template <typename S, int VB>
+__global__ void __launch_bounds__(256, 4) k_vanka_warp(const S* __restrict__ inv, const int* __restrict__ idx,
+                                                    const double* __restrict__ t, double* __restrict__ Y,
+                                                    const int* __restrict__ cell_list, int ncells, int n, int ld,
+                                                    int LDV, int Q, double* __restrict__ d_scatter, double omega) {
+  using A = typename Acc<S>::T;
+  using CV = Conv<S, VB>;
+  constexpr int V = CV::V;
+  constexpr int UB = VB == 4 ? 12 : 6;  // column loads in flight per lane
+  __shared__ A tsh[8][64];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int rc = lane % LDV, cg = lane / LDV;
+  const int jstart = cg < Q ? cg : n;  // lanes beyond Q*LDV stream nothing
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  A* tl = tsh[wid];
+  long long ci = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (ci >= ncells) return;  // warp-uniform
+  int c = cell_list ? cell_list[ci] : (int)ci;
+  A ta = lane < n ? (A)t[idx[(long long)c * n + lane]] : A(0);
+  A tb = lane + 32 < n ? (A)t[idx[(long long)c * n + lane + 32]] : A(0);
+  for (; ci < ncells; ci += nwarps) {
+    __syncwarp();
+    tl[lane] = ta;
+    tl[lane + 32] = tb;
+    __syncwarp();
+    const long long cin = ci + nwarps;
+    const bool has_next = cin < ncells;
+    const int cn = has_next ? (cell_list ? cell_list[cin] : (int)cin) : 0;
+    const int ia = (has_next && lane < n) ? idx[(long long)cn * n + lane] : -1;
+    const int ib = (has_next && lane + 32 < n) ? idx[(long long)cn * n + lane + 32] : -1;
+    A acc[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = 0;
+    const S* M = inv + (size_t)c * n * ld + rc * V;
+    for (int j0 = jstart; j0 < n; j0 += UB * Q) {
+      Raw<VB> raw[UB];
+#pragma unroll
+      for (int u = 0; u < UB; ++u) {
+        const int j = j0 + u * Q;
+        if (j < n) raw[u] = ld_raw<VB>(M + (size_t)j * ld);
+      }
+#pragma unroll
+      for (int u = 0; u < UB; ++u) {
+        const int j = j0 + u * Q;
+        if (j < n) {
+          A e[V];
+          CV::run(raw[u], e);
+          const A tj = tl[j];
+#pragma unroll
+          for (int v = 0; v < V; ++v) acc[v] += e[v] * tj;
+        }
+      }
+    }
+    // next cell's t (its ids have arrived during the stream)
+    ta = ia >= 0 ? (A)t[ia] : A(0);
+    tb = ib >= 0 ? (A)t[ib] : A(0);
+    // lanes cg = 0 collect the Q partial sums of their rows
+    for (int off = (Q >> 1) * LDV; off >= LDV; off >>= 1)
+#pragma unroll
+      for (int v = 0; v < V; ++v) acc[v] += __shfl_down_sync(0xffffffffu, acc[v], off);
+    if (cg == 0) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const int row = rc * V + v;
+        if (row < n) {
+          if (d_scatter) d_scatter[idx[(long long)c * n + row]] += omega * (double)acc[v];
+          else Y[(long long)c * n + row] = (double)acc[v];
+        }
+      }
+    }
+    c = cn;
+  }
+}
+
 // Transposed local solves y_T = Inv_T^T t_T (adjoint smoother): one warp per column, a dot product
 // of the column with t_T.
 template <typename S>
@@ -219,10 +298,31 @@ static int sm_count() {
   return n;
 }
 
+template <typename S, int VB>
+static void launch_warp(const Level& L, const void* inv, const VGeom& g, const double* t, const int* cells, int nc,
+                        double* scatter, double omega, cudaStream_t s) {
+  static int per_sm = 0;
+  if (!per_sm) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_vanka_warp<S, VB>, 256, 0);
+    if (per_sm <= 0) per_sm = 1;
+  }
+  int Q = 1;
+  while (2 * Q * g.LDV <= 32) Q *= 2;
+  const int blocks = std::max(1, std::min((nc + 7) / 8, sm_count() * per_sm));
+  k_vanka_warp<S, VB><<<blocks, 256, 0, s>>>((const S*)inv, L.idx, t, L.Y, cells, nc, g.n, g.ld, g.LDV, Q, scatter,
+                                            omega);
+}
+
 template <typename S>
 static void launch_fwd(const Level& L, const void* inv, int vb, const VGeom& g, const double* t, const int* cells,
                        int nc, double* scatter, double omega, cudaStream_t s) {
   using A = typename Acc<S>::T;
+  if (g.n <= 64 && g.LDV <= 32) {
+    if (vb == 16) launch_warp<S, 16>(L, inv, g, t, cells, nc, scatter, omega, s);
+    else if (vb == 8 || sizeof(S) == 8) launch_warp<S, 8>(L, inv, g, t, cells, nc, scatter, omega, s);
+    else if constexpr (sizeof(S) < 8) launch_warp<S, 4>(L, inv, g, t, cells, nc, scatter, omega, s);
+    return;
+  }
   const size_t smem = sizeof(A) * ((size_t)g.P * g.n + (size_t)g.P * g.Q * g.ld) + 16;
   const int groups = (nc + g.P - 1) / g.P;
   const int blocks = std::min(groups, sm_count() * 8);

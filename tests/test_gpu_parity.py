@@ -243,3 +243,28 @@ def test_singular_cell_reported():
         h.factor_cells()
     assert e.value.status == _lib.STM_ERR_SINGULAR_CELL
     assert e.value.bad_level >= 1 and e.value.bad_cell >= 0
+
+
+@pytest.mark.parametrize("name", ["2d_k1_obs", "2d_k2_obs_3lev", "3d_k1_obs"])
+@pytest.mark.parametrize("prec", ["f32", "bf16"])
+def test_single_sweep_mixed_precision(name, prec):
+    """Additive step with FP32/BF16 inverses against the oracle with the same storage rounding
+    (inverse rounded to the storage type, residual to FP32, products summed in FP64); the GPU
+    accumulates in FP32, hence 1e-5 relative."""
+    from oracle import solvers
+    wl, o, h = pair(name, "additive", prec)
+    g = wl.n_levels - 1
+    lev = o.levels[g]
+    rng = np.random.default_rng(38)
+    r = rng.standard_normal(lev.N)
+    d = rng.standard_normal(lev.N)
+    dt = torch.bfloat16 if prec == "bf16" else torch.float32
+    inv_r = torch.from_numpy(o.inv[g]).to(dt).double().numpy()
+    t = (r - o.J[g] @ d).astype(np.float32).astype(np.float64)
+    y = np.einsum("cij,cj->ci", inv_r, t[lev.idx])
+    corr = np.zeros(lev.N)
+    np.add.at(corr, lev.idx.ravel(), y.ravel())
+    expect = d + wl.omega * corr / solvers.multiplicity(lev)
+    dg = dev(d)
+    h.vanka_sweep(g, dev(r), dg)
+    assert rel_max(dg.cpu().numpy(), expect) < 1e-5
