@@ -168,6 +168,38 @@ stm_status stm_gmres_solve_host(stm_hierarchy* h, const double* b_host, double* 
  * b_dev: FP64 [n_dofs of the finest level], overwritten. */
 stm_status stm_assemble_rhs(stm_hierarchy* h, double U, double nu, int which, double* b_dev, void* stream);
 
+/* Nonlinear slab problem F(X) = 0 (Sec. 3, Eq. nonlineq) with the data of stm_assemble_rhs:
+ *   F(X) = A X + c(X, X) - b(U, nu),  A the linear part of the slab operator, c the convection term,
+ * solved by damped Newton (Eqs. linNewEq, linNewEqU): step m assembles J(X^m) on every level (coarse
+ * levels take X^m at their nodes), factors the cells, solves J(X^m) D = -F(X^m) with the
+ * GMG-preconditioned FGMRES of stm_gmres_solve (gopts; transpose and use_x0 ignored), and sets
+ * X^{m+1} = X^m + lambda D with the first lambda in 1, 1/2, 1/4, ... (at most max_halvings halvings)
+ * that lowers ||F||_2. Stops when ||F|| <= max(abs_tol, ||F(X^0)|| / reduction) (Sec. 5.1 uses 1e-10
+ * and 1e4). F is evaluated as (b + c(X, X)) - J(X) X, which equals -F since J(X) X = A X + 2 c(X, X).
+ * X_dev: FP64 [n_dofs of the finest level], the initial iterate on entry and the last iterate on
+ * return (also on STM_ERR_NOT_CONVERGED). On return J is assembled at the last iterate and the cell
+ * factors are stale (call stm_factor_cells before another linear solve). Synchronises once per
+ * residual evaluation. Errors: STM_ERR_INVALID_ARG, STM_ERR_NONFINITE, STM_ERR_SINGULAR_CELL, the
+ * FGMRES errors, STM_ERR_NOT_CONVERGED after max_newton steps. */
+#define STM_NEWTON_MAX_STEPS 32
+typedef struct {
+  int max_newton;    /* Newton steps at most, <= STM_NEWTON_MAX_STEPS */
+  int max_halvings;  /* line-search halvings per step at most (0: undamped) */
+  double abs_tol;    /* stop when ||F|| <= abs_tol ... */
+  double reduction;  /* ... or when ||F|| <= ||F(X^0)|| / reduction (>= 1) */
+} stm_newton_opts;
+typedef struct {
+  int newton_iters;  /* steps taken */
+  int gmres_iters;   /* FGMRES iterations over all steps */
+  int converged;
+  int n_res;         /* valid entries of res (newton_iters + 1) */
+  double res[STM_NEWTON_MAX_STEPS + 1]; /* ||F(X^m)||_2, m = 0 .. newton_iters */
+  double lam[STM_NEWTON_MAX_STEPS];     /* accepted step lengths */
+  int gmres_step[STM_NEWTON_MAX_STEPS]; /* FGMRES iterations of each step */
+} stm_newton_info;
+stm_status stm_newton_solve(stm_hierarchy* h, double U, double nu, double* X_dev, const stm_newton_opts* nopts,
+                            const stm_gmres_opts* gopts, stm_newton_info* info, void* stream);
+
 /* Weights j of the drag-like functional J(X) = int_{I_n} int_wake v_1 dx dt = j . X, where the wake
  * is the union of finest cells inside the level-1 cell box [wake_lo, wake_hi) (all z in 3D).
  * j_dev: FP64 [n_dofs of the finest level], overwritten. */

@@ -34,6 +34,20 @@ class SolveInfo(C.Structure):
                 ("rel_res_true", C.c_double), ("rel_res_est", C.c_double)]
 
 
+NEWTON_MAX_STEPS = 32  # STM_NEWTON_MAX_STEPS
+
+
+class NewtonOpts(C.Structure):
+    _fields_ = [("max_newton", C.c_int), ("max_halvings", C.c_int), ("abs_tol", C.c_double),
+                ("reduction", C.c_double)]
+
+
+class NewtonInfo(C.Structure):
+    _fields_ = [("newton_iters", C.c_int), ("gmres_iters", C.c_int), ("converged", C.c_int), ("n_res", C.c_int),
+                ("res", C.c_double * (NEWTON_MAX_STEPS + 1)), ("lam", C.c_double * NEWTON_MAX_STEPS),
+                ("gmres_step", C.c_int * NEWTON_MAX_STEPS)]
+
+
 _P, _D, _I, _L, _V = C.c_void_p, C.c_double, C.c_int, C.c_longlong, C.c_void_p
 _LP = C.POINTER(C.c_longlong)
 _IP = C.POINTER(C.c_int)
@@ -54,6 +68,8 @@ SIGNATURES = {
     "stm_gmres_solve": ([_P, _P, _P, C.POINTER(GmresOpts), C.POINTER(SolveInfo), _P], _I),
     "stm_gmres_solve_host": ([_P, _DP, _DP, C.POINTER(GmresOpts), C.POINTER(SolveInfo), _P], _I),
     "stm_assemble_rhs": ([_P, _D, _D, _I, _P, _P], _I),
+    "stm_newton_solve": ([_P, _D, _D, _P, C.POINTER(NewtonOpts), C.POINTER(GmresOpts), C.POINTER(NewtonInfo), _P],
+                         _I),
     "stm_functional_weights": ([_P, _IP, _IP, _P, _P], _I),
     "stm_jacobian_dnu_apply": ([_P, _P, _P, _P], _I),
     "stm_dot": ([_P, _P, _P, _L, _DP, _P], _I),

@@ -345,13 +345,6 @@ static stm_status gmres_core(Hierarchy& H, const double* b, double* x, const stm
     }
     ++inf.restarts;
   }
-  int copy_timeout = 0;
-  STM_CUDA(cudaMemcpyAsync(&copy_timeout, H.dflag + 3, sizeof(int), cudaMemcpyDeviceToHost, s));
-  STM_CUDA(cudaStreamSynchronize(s));
-  if (copy_timeout) {
-    set_error("a bulk copy of cell inverses did not complete within its wait limit");
-    return STM_ERR_CUDA;
-  }
   inf.iters = it;
   inf.converged = converged ? 1 : 0;
   inf.rel_res_est = est;
@@ -394,6 +387,103 @@ stm_status stm_gmres_solve_host(stm_hierarchy* h, const double* b_host, double* 
   STM_CUDA(cudaMemcpyAsync(x_host, H.xbuf, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
   STM_CUDA(cudaStreamSynchronize(s));
   return st;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Damped Newton for the nonlinear slab problem (Sec. 3, Eqs. nonlineq, linNewEq, linNewEqU)
+// ---------------------------------------------------------------------------------------------
+static stm_status assemble_all(Hierarchy& H, const double* X, double nu, cudaStream_t s) {
+  clear_graphs(H);
+  STM_TRY(inject_linearisation(H, X, s));
+  for (int g = 0; g < (int)H.L.size(); ++g) STM_TRY(assemble_level(H, g, nu, s));
+  H.assembled = true;
+  H.factored = false;
+  return STM_OK;
+}
+
+// With J = J(X) assembled at X: negF = (b + c(X, X)) - J(X) X = -F(X) (F = A X + c(X, X) - b, and
+// J(X) X = A X + 2 c(X, X)); *norm = ||F(X)||_2.
+static stm_status newton_residual(Hierarchy& H, const double* X, double U, double nu, double* negF, double* norm,
+                                  cudaStream_t s) {
+  const long long N = H.L.back().N;
+  STM_TRY(assemble_cellvec(H, 0, U, nu, nullptr, nullptr, H.nw_B, s));
+  STM_TRY(jacobian_apply(H, (int)H.L.size() - 1, X, H.nw_B, negF, 1, 0, s));
+  STM_TRY(vec_norm_sq(negF, N, H.hcol, H.part, H.nblk_dot, s));
+  double t = 0.0;
+  STM_CUDA(cudaMemcpyAsync(&t, H.hcol, sizeof(double), cudaMemcpyDeviceToHost, s));
+  STM_CUDA(cudaStreamSynchronize(s));
+  *norm = std::sqrt(t);
+  if (!std::isfinite(*norm)) {
+    set_error("non-finite nonlinear residual");
+    return STM_ERR_NONFINITE;
+  }
+  return STM_OK;
+}
+
+stm_status stm_newton_solve(stm_hierarchy* h, double U, double nu, double* X, const stm_newton_opts* nopts,
+                            const stm_gmres_opts* gopts, stm_newton_info* info, void* stream) {
+  if (!h || !X || !nopts || !gopts) return bad_arg("NULL argument");
+  if (nopts->max_newton < 0 || nopts->max_newton > STM_NEWTON_MAX_STEPS || nopts->max_halvings < 0 ||
+      nopts->max_halvings > 60 || !(nopts->abs_tol >= 0.0) || !(nopts->reduction >= 1.0))
+    return bad_arg("max_newton in [0, STM_NEWTON_MAX_STEPS], max_halvings in [0, 60], abs_tol >= 0, reduction >= 1");
+  if (gopts->restart < 1 || gopts->restart > 200 || gopts->max_iter < 0 || !(gopts->rtol >= 0.0))
+    return bad_arg("restart in [1,200], max_iter >= 0, rtol >= 0");
+  Hierarchy& H = h->H;
+  cudaStream_t s = S(stream);
+  const long long N = H.L.back().N;
+  STM_TRY(ensure_krylov(H, gopts->restart));
+  double** bufs[] = {&H.nw_negF, &H.nw_D, &H.nw_Xt, &H.nw_B, &H.nw_Ft};
+  for (double** b : bufs)
+    if (!*b) STM_CUDA(cudaMalloc((void**)b, sizeof(double) * N));
+  stm_newton_info inf{};
+  stm_gmres_opts go = *gopts;
+  go.transpose = 0;
+  go.use_x0 = 0;
+  double res = 0.0;
+  STM_TRY(assemble_all(H, X, nu, s));
+  STM_TRY(newton_residual(H, X, U, nu, H.nw_negF, &res, s));
+  inf.res[0] = res;
+  inf.n_res = 1;
+  const double target = std::max(nopts->abs_tol, res / nopts->reduction);
+  bool converged = res <= target;
+  for (int m = 0; m < nopts->max_newton && !converged; ++m) {
+    int bl = -1;
+    long long bc = -1;
+    STM_TRY(stm_factor_cells(h, stream, &bl, &bc));
+    stm_solve_info si{};
+    const stm_status st = gmres_core(H, H.nw_negF, H.nw_D, go, &si, s);
+    inf.gmres_iters += si.iters;
+    inf.gmres_step[m] = si.iters;
+    if (st != STM_OK) {
+      if (info) *info = inf;  // the steps taken so far
+      return st;
+    }
+    double lam = 1.0, rt = 0.0;
+    for (int hv = 0;; ++hv) {
+      STM_TRY(vec_copy(H.nw_Xt, X, N, s));
+      STM_TRY(vec_axpy(H.nw_Xt, lam, H.nw_D, N, s));
+      STM_TRY(assemble_all(H, H.nw_Xt, nu, s));
+      STM_TRY(newton_residual(H, H.nw_Xt, U, nu, H.nw_Ft, &rt, s));
+      if (rt < res || hv == nopts->max_halvings) break;
+      lam *= 0.5;
+    }
+    // accept: X <- X + lam D, -F(X) <- the trial's
+    STM_TRY(vec_copy(X, H.nw_Xt, N, s));
+    std::swap(H.nw_negF, H.nw_Ft);
+    res = rt;
+    inf.lam[m] = lam;
+    inf.res[m + 1] = res;
+    inf.n_res = m + 2;
+    inf.newton_iters = m + 1;
+    converged = res <= target;
+  }
+  inf.converged = converged ? 1 : 0;
+  if (info) *info = inf;
+  if (!converged) {
+    set_error("Newton reached max_newton");
+    return STM_ERR_NOT_CONVERGED;
+  }
+  return STM_OK;
 }
 
 stm_status stm_assemble_rhs(stm_hierarchy* h, double U, double nu, int which, double* b_dev, void* stream) {

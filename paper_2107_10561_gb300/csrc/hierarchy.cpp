@@ -757,6 +757,7 @@ void free_hierarchy(Hierarchy& H) {
       if (q) cudaFree(q);
   }
   void* hp[] = {H.cinv, H.dflag, H.dbad, H.V, H.Z, H.w, H.hcol, H.part, H.yvec, H.bbuf, H.xbuf,
+                H.nw_negF, H.nw_D, H.nw_Xt, H.nw_B, H.nw_Ft,
                 H.mV, H.mZ, H.mW, H.mB, H.mX, H.mh, H.mpart, H.mf, H.my};
   for (void* q : hp)
     if (q) cudaFree(q);

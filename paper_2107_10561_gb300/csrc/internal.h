@@ -171,6 +171,8 @@ struct Hierarchy {
   double* yvec = nullptr;         // [m]
   double* bbuf = nullptr;         // host-API staging for b and x
   double* xbuf = nullptr;
+  // damped Newton (allocated on first use): -F, step D, trial iterate, b + c(X, X), trial's -F
+  double *nw_negF = nullptr, *nw_D = nullptr, *nw_Xt = nullptr, *nw_B = nullptr, *nw_Ft = nullptr;
   int nblk_dot = 0;
   // multi-right-hand-side FGMRES work space ([.][N][32])
   int mrestart_cap = 0;
@@ -263,6 +265,7 @@ stm_status batched_update(const double* V, int nv, const double* h, double* w, l
 stm_status gemv_accumulate(const double* Z, int nz, const double* y, double* x, long long n,
                            cudaStream_t s);
 stm_status vec_axpby_dev(double* hacc, const double* h2, int n, cudaStream_t s);
+stm_status vec_axpy(double* y, double a, const double* x, long long n, cudaStream_t s);  // y += a x
 stm_status vec_norm_sq(const double* x, long long n, double* out, double* part, int nblk,
                        cudaStream_t s);
 

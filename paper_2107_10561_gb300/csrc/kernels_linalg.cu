@@ -273,6 +273,16 @@ stm_status vec_fill(double* x, double v, long long n, cudaStream_t s) {
   STM_CUDA(cudaGetLastError());
   return STM_OK;
 }
+__global__ void k_axpy(double* __restrict__ y, double a, const double* __restrict__ x, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] += a * x[i];
+}
+stm_status vec_axpy(double* y, double a, const double* x, long long n, cudaStream_t s) {
+  k_axpy<<<(int)std::max<long long>(1, std::min<long long>((n + 255) / 256, sms() * 8LL)), 256, 0, s>>>(y, a, x, n);
+  note_launch();
+  STM_CUDA(cudaGetLastError());
+  return STM_OK;
+}
 stm_status vec_copy(double* y, const double* x, long long n, cudaStream_t s) {
   STM_CUDA(cudaMemcpyAsync(y, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   return STM_OK;

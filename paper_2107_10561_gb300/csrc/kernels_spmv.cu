@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(256, (K == 3 ? 3 : 4)) k_spmv_nodeblock(
     const long long* __restrict__ nbase, const int* __restrict__ nbr_ptr, const int* __restrict__ nbr,
     const int* __restrict__ ncell, const int* __restrict__ node_cells, const int* __restrict__ cell_nodes,
     const int* __restrict__ job_nodes, long long block, int R, int C, int nv, const double* __restrict__ x,
-    const double* __restrict__ b, double* __restrict__ y, int mode) {
+    const double* __restrict__ b, double* __restrict__ y, int mode, long long nwv) {
   constexpr int GPW = 32 / VL;
   constexpr int KD = K * D;
   constexpr int NP = D + 1;
@@ -263,7 +263,10 @@ __global__ void __launch_bounds__(256, (K == 3 ? 3 : 4)) k_spmv_nodeblock(
   int wmask_v;
   constexpr int NAV_R = NAV < VL ? NAV : VL;
   const int kv = scatter_index<VL, NAV_R>(lane, &wmask_v);
-  for (long long wb = warp * GPW; wb < R; wb += nwarps * GPW) {
+  // warps [0, nwv) take the velocity rows node by node, the others the pressure rows, so that on
+  // small levels the two latency chains run side by side
+  if (warp < nwv) {
+  for (long long wb = warp * GPW; wb < R; wb += nwv * GPW) {
     const long long job = wb + gw;
     const bool ok = job < R;
     const int i = ok ? job_nodes[job] : 0;
@@ -323,12 +326,12 @@ __global__ void __launch_bounds__(256, (K == 3 ? 3 : 4)) k_spmv_nodeblock(
         }
     }
   }
-  // Pressure rows: one lane per row pr = (a*C + c)*n_p + q over the warp-transposed copy, so entry t
-  // of 32 consecutive rows is one contiguous 256-byte load; all lanes busy, no cross-lane sums.
-  {
+  } else {
+    // Pressure rows: one lane per row pr = (a*C + c)*n_p + q over the warp-transposed copy, so entry
+    // t of 32 consecutive rows is one contiguous 256-byte load; all lanes busy, no cross-lane sums.
     constexpr int NV = D == 2 ? 9 : 27;
-    const long long tid_g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long nthreads = (long long)gridDim.x * blockDim.x;
+    const long long tid_g = (warp - nwv) * 32 + (threadIdx.x & 31);
+    const long long nthreads = (nwarps - nwv) * 32;
     const long long npr = (long long)K * C * NP;
     for (long long pr = tid_g; pr < npr; pr += nthreads) {
       const int a = (int)(pr / ((long long)C * NP));
@@ -356,18 +359,26 @@ static int sms_count();
 
 template <int VL, int K, int D>
 static void launch_nodeblock(const Level& L, const double* x, const double* b, double* y, int mode, cudaStream_t s) {
-  const long long threads_needed = (long long)std::max((long long)L.R * VL, (long long)L.C * K * (D + 1));
-  const int blocks = (int)std::min<long long>((threads_needed + 255) / 256, (long long)sms_count() * 4);
-  k_spmv_nodeblock<VL, K, D><<<blocks, 256, 0, s>>>(L.rowptr, L.val, L.nval, L.pvalT, L.nbase, L.nbr_ptr, L.nbr, L.ncell,
-                                                    L.node_cells, L.cell_nodes, L.job_nodes, L.block, L.R, L.C, L.nv,
-                                                    x, b, y, mode);
+  constexpr int GPW = 32 / VL;
+  const long long npr = (long long)K * L.C * (D + 1);
+  const long long need_v = (L.R + GPW - 1) / GPW, need_p = (npr + 31) / 32;
+  // one unit per warp (a group of GPW nodes, or 32 pressure rows): the block scheduler hands out
+  // the work dynamically as CTAs retire, so the tail is at most one unit long
+  const long long blocks = std::max<long long>(1, (need_v + need_p + 7) / 8);
+  const long long nwv = need_v;
+  k_spmv_nodeblock<VL, K, D><<<(int)blocks, 256, 0, s>>>(L.rowptr, L.val, L.nval, L.pvalT, L.nbase, L.nbr_ptr, L.nbr,
+                                                         L.ncell, L.node_cells, L.cell_nodes, L.job_nodes, L.block,
+                                                         L.R, L.C, L.nv, x, b, y, mode, nwv);
 }
 
 stm_status spmv_nodeblock(const Level& L, const double* x, const double* b, double* y, int mode, cudaStream_t s) {
   // short groups (4 lanes in 2D, 8 in 3D) need at least ~1024 resident threads per SM to keep
   // enough loads in flight; smaller levels use 16 lanes per node
-  const bool big = (long long)L.R * (L.dim == 2 ? 4 : 8) >= (long long)sms_count() * 1024;
-  switch (L.dim * 10 + L.K + (big ? 0 : 100)) {
+  const long long per_sm_threads = 1024;
+  int cls = 0;  // 0: 4 (2D) / 8 (3D) lanes per node, 100: 16 lanes, 200: 32 lanes
+  if ((long long)L.R * (L.dim == 2 ? 4 : 8) < (long long)sms_count() * per_sm_threads) cls = 100;
+  if ((long long)L.R * 16 < (long long)sms_count() * per_sm_threads / 4) cls = 200;
+  switch (L.dim * 10 + L.K + cls) {
     case 21: launch_nodeblock<4, 1, 2>(L, x, b, y, mode, s); break;
     case 22: launch_nodeblock<4, 2, 2>(L, x, b, y, mode, s); break;
     case 23: launch_nodeblock<4, 3, 2>(L, x, b, y, mode, s); break;
@@ -380,6 +391,12 @@ stm_status spmv_nodeblock(const Level& L, const double* x, const double* b, doub
     case 131: launch_nodeblock<16, 1, 3>(L, x, b, y, mode, s); break;
     case 132: launch_nodeblock<16, 2, 3>(L, x, b, y, mode, s); break;
     case 133: launch_nodeblock<16, 3, 3>(L, x, b, y, mode, s); break;
+    case 221: launch_nodeblock<32, 1, 2>(L, x, b, y, mode, s); break;
+    case 222: launch_nodeblock<32, 2, 2>(L, x, b, y, mode, s); break;
+    case 223: launch_nodeblock<32, 3, 2>(L, x, b, y, mode, s); break;
+    case 231: launch_nodeblock<32, 1, 3>(L, x, b, y, mode, s); break;
+    case 232: launch_nodeblock<32, 2, 3>(L, x, b, y, mode, s); break;
+    case 233: launch_nodeblock<32, 3, 3>(L, x, b, y, mode, s); break;
     default:
       set_error("node-block SpMV: unsupported (dim, k)");
       return STM_ERR_INVALID_ARG;

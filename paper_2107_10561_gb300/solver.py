@@ -173,6 +173,25 @@ class Hierarchy:
         _lib.check(self.lib.stm_assemble_rhs(self.h, float(U), float(nu), int(which), _ptr(b, self.n_dofs(), "b"),
                                              _stream(stream)), "stm_assemble_rhs")
 
+    def newton_solve(self, X, U, nu=None, max_newton=20, max_halvings=8, abs_tol=1e-10, reduction=1e4,
+                     rtol=1e-10, restart=30, max_iter=1000, stream=None, raise_on_fail=True):
+        """Damped Newton for the slab problem F(X) = A X + c(X, X) - b(U, nu) = 0 (stm_newton_solve).
+
+        X: device float64 [n_dofs], initial iterate, overwritten with the last iterate."""
+        nu = self.params.nu if nu is None else nu
+        no = _lib.NewtonOpts(int(max_newton), int(max_halvings), float(abs_tol), float(reduction))
+        go = self._opts(restart, max_iter, rtol, False, False)
+        inf = _lib.NewtonInfo()
+        st = self.lib.stm_newton_solve(self.h, float(U), float(nu), _ptr(X, self.n_dofs(), "X"), C.byref(no),
+                                       C.byref(go), C.byref(inf), _stream(stream))
+        info = {"newton_iters": inf.newton_iters, "gmres_iters": inf.gmres_iters, "converged": bool(inf.converged),
+                "res": [inf.res[i] for i in range(inf.n_res)], "lam": [inf.lam[i] for i in range(inf.newton_iters)],
+                "gmres_step": [inf.gmres_step[i] for i in range(inf.newton_iters)],
+                "status": _lib.STATUS_NAMES.get(st, st)}
+        if st != _lib.STM_OK and raise_on_fail:
+            _lib.check(st, "stm_newton_solve")
+        return info
+
     def functional_weights(self, wake_lo, wake_hi, j, stream=None):
         lo = (C.c_int * 3)(*(list(wake_lo) + [0] * (3 - len(wake_lo))))
         hi = (C.c_int * 3)(*(list(wake_hi) + [1] * (3 - len(wake_hi))))

@@ -1,0 +1,83 @@
+"""Damped Newton on the GPU (stm_newton_solve) against the oracle's Newton (Sec. 3, Eqs. nonlineq,
+linNewEq, linNewEqU; stopping rule of Sec. 5.1). Both start from the same seeded iterate; the oracle
+solves its linear systems exactly (sparse LU), the GPU with GMG-FGMRES to 1e-12."""
+import numpy as np
+import pytest
+
+import synth
+from helpers import gpu_hierarchy, lattice_to_gpu, rel_max
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "2d_k2_obs": synth.small_workload(2, 2, (8, 2), 2, obstacle=True),
+    "2d_k1_3lev": synth.small_workload(2, 1, (8, 2), 3, obstacle=True),
+    "3d_k1": synth.small_workload(3, 1, (4, 2, 2), 2, obstacle=False),
+}
+
+
+def _state(wl, amp):
+    """Seeded start: the synthetic linearisation point with `amp` times its usual perturbation, or the
+    zero state (amp = None)."""
+    st = synth.linearisation_point(wl, amp=amp if amp is not None else 0.1)
+    return st if amp is not None else np.zeros_like(st)
+
+
+def _oracle(wl, amp, U=0.3, **kw):
+    from oracle import newton
+    from oracle.fem import Level
+    f = 2 ** (wl.n_levels - 1)
+    lev = Level(wl.dim, wl.k, wl.fine_cells, wl.length, tuple(x * f for x in wl.obstacle_lo),
+                tuple(x * f for x in wl.obstacle_hi))
+    X0 = lev.dofs_from_lattice(_state(wl, amp))
+    X, info = newton.newton_solve(wl, X0, U, linear="lu", **kw)
+    return X0, X, info
+
+
+def _gpu(wl, amp, U=0.3, **kw):
+    h = gpu_hierarchy(wl, "f64", factor=False)
+    X = lattice_to_gpu(h, _state(wl, amp))
+    info = h.newton_solve(X, U, rtol=1e-12, raise_on_fail=False, **kw)
+    out = X.cpu().numpy()
+    h.close()
+    return out, info
+
+
+def _same_history(rg, ro, r0):
+    assert len(rg) == len(ro), (rg, ro)
+    for a, b in zip(rg, ro):
+        assert abs(a - b) <= 1e-6 * b + 1e-9 * r0, (rg, ro)
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_newton_matches_oracle(case):
+    wl = CASES[case]
+    _, Xo, io = _oracle(wl, 2.0, abs_tol=1e-10, reduction=1e30)
+    Xg, ig = _gpu(wl, 2.0, abs_tol=1e-10, reduction=1e30)
+    assert io["converged"] and ig["converged"], (io["res"], ig)
+    assert ig["newton_iters"] == len(io["lam"])
+    _same_history(ig["res"], io["res"], io["res"][0])
+    assert ig["lam"] == io["lam"]
+    assert rel_max(Xg, Xo) < 1e-8
+
+
+def test_damped_steps_match_oracle():
+    """From the zero state with a strong inflow (U = 30) the second and third steps are shortened
+    (lambda = 1/32, 1/4 on the oracle); step lengths and residuals follow the oracle step by step."""
+    wl = CASES["2d_k2_obs"]
+    _, Xo, io = _oracle(wl, None, U=30.0, abs_tol=1e-10, reduction=1e30, max_newton=3)
+    Xg, ig = _gpu(wl, None, U=30.0, abs_tol=1e-10, reduction=1e30, max_newton=3)
+    assert not io["converged"] and not ig["converged"] and ig["status"] == "STM_ERR_NOT_CONVERGED"
+    assert ig["lam"] == io["lam"] and min(io["lam"]) < 1.0
+    _same_history(ig["res"], io["res"], io["res"][0])
+    assert rel_max(Xg, Xo) < 1e-7
+
+
+def test_stopping_rule():
+    """Stops at the first iterate with ||F|| <= max(abs_tol, ||F_0|| / 1e4)."""
+    wl = CASES["2d_k1_3lev"]
+    Xg, ig = _gpu(wl, 2.0, abs_tol=1e-10, reduction=1e4)
+    r = ig["res"]
+    target = max(1e-10, r[0] / 1e4)
+    assert ig["converged"] and r[-1] <= target and all(x > target for x in r[:-1])
