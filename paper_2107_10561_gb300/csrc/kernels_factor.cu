@@ -177,12 +177,6 @@ stm_status factor_level(Hierarchy& H, int g, cudaStream_t s) {
 // ---------------------------------------------------------------------------------------------
 // Coarse level: explicit FP64 inverse of J_0 by Gauss-Jordan with partial pivoting in global memory
 // ---------------------------------------------------------------------------------------------
-__global__ void k_densify(const long long* __restrict__ rowptr, const int* __restrict__ col,
-                          const double* __restrict__ val, double* __restrict__ A, long long n) {
-  for (long long r = blockIdx.x; r < n; r += gridDim.x)
-    for (long long e = rowptr[r] + threadIdx.x; e < rowptr[r + 1]; e += blockDim.x) A[r * n + col[e]] = val[e];
-}
-
 // scal[0] = 1/pivot, scal[1] = old A[k][k]; piv[k] = pivot row
 __global__ void k_gj_pivot(double* A, long long n, int k, int* piv, double* scal, int* flag) {
   __shared__ double sb[32];
@@ -270,32 +264,301 @@ __global__ void k_gj_colswap(double* A, long long n, int k, const int* piv) {
   }
 }
 
-stm_status factor_coarse(Hierarchy& H, cudaStream_t s) {
-  Level& L = H.L[0];
-  const long long n = L.N;
-  H.N0 = n;
-  if (!H.cinv) STM_CUDA(cudaMalloc(&H.cinv, sizeof(double) * n * n));
-  STM_CUDA(cudaMemsetAsync(H.cinv, 0, sizeof(double) * n * n, s));
-  k_densify<<<(int)std::min<long long>(n, 152 * 32), 128, 0, s>>>(L.rowptr, L.colidx, L.val, H.cinv, n); note_launch();
-  STM_CUDA(cudaGetLastError());
-  int* piv = nullptr;
-  double* scal = nullptr;
-  STM_CUDA(cudaMalloc(&piv, sizeof(int) * n));
-  STM_CUDA(cudaMalloc(&scal, sizeof(double) * 2));
+// ---------------------------------------------------------------------------------------------
+// Coarse direct solver (Algorithm 1, level 1): the explicit inverse of J_0 from a block LU over
+// x-slabs. Velocity DoFs go to the slab of their node's lattice plane (planes 2b, 2b+1 -> slab b,
+// the last plane with the last slab), the pressure of cell i to slab i+1 (the last cell's to the
+// last slab). A Q2 cell spans the planes 2i..2i+2, so J_0 is block tridiagonal in this order, and
+// every slab's pressure is eliminated after the velocities of the cell that carries it, which keeps
+// the Schur complements regular (with the pressure of cell b in slab b, S_0 is singular: its
+// pressure sees only velocities whose neighbours across the slab face were cut away). Block LU
+// without pivoting across slabs, Gauss-Jordan with partial pivoting inside each Schur complement:
+//   S_0 = A_00,  S_b = A_bb - A_{b,b-1} W_{b-1},  W_b = S_b^{-1} A_{b,b+1},  G_b = S_b^{-1} A_{b,b-1};
+// then the inverse, L^{-1} forward (Z_bb = S_b^{-1}, Z_bj = -G_b Z_{b-1,j}) and U^{-1} backward
+// (X_b = Z_b - W_b X_{b+1}), and finally the slab permutation is undone.
+// ---------------------------------------------------------------------------------------------
+
+// C = beta C + alpha A B, row-major, FP64. 64x64 tile per 256-thread CTA, 4x4 outputs per thread.
+__global__ void __launch_bounds__(256) k_dgemm_rm(int m, int n, int k, double alpha, const double* __restrict__ A,
+                                                  long long lda, const double* __restrict__ B, long long ldb,
+                                                  double beta, double* __restrict__ C, long long ldc) {
+  __shared__ double As[16][64 + 1];
+  __shared__ double Bs[16][64];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int r0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
+  double acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+  for (int k0 = 0; k0 < k; k0 += 16) {
+    for (int e = threadIdx.x; e < 64 * 16; e += 256) {
+      const int rr = e / 16, kk = e - rr * 16;
+      const int gr = r0 + rr, gk = k0 + kk;
+      As[kk][rr] = (gr < m && gk < k) ? A[(long long)gr * lda + gk] : 0.0;
+      const int kb = e / 64, cc = e - kb * 64;
+      const int gkb = k0 + kb, gc = c0 + cc;
+      Bs[kb][cc] = (gkb < k && gc < n) ? B[(long long)gkb * ldb + gc] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        a[q] = As[kk][ty + 16 * q];
+        b[q] = Bs[kk][tx + 16 * q];
+      }
+#pragma unroll
+      for (int qa = 0; qa < 4; ++qa)
+#pragma unroll
+        for (int qb = 0; qb < 4; ++qb) acc[qa][qb] += a[qa] * b[qb];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int qa = 0; qa < 4; ++qa)
+#pragma unroll
+    for (int qb = 0; qb < 4; ++qb) {
+      const int gr = r0 + ty + 16 * qa, gc = c0 + tx + 16 * qb;
+      if (gr < m && gc < n) {
+        double* c = C + (long long)gr * ldc + gc;
+        *c = (beta == 0.0 ? 0.0 : beta * *c) + alpha * acc[qa][qb];
+      }
+    }
+}
+
+static void dgemm(int m, int n, int k, double alpha, const double* A, long long lda, const double* B, long long ldb,
+                  double beta, double* C, long long ldc, cudaStream_t s) {
+  if (m <= 0 || n <= 0) return;
+  dim3 grid((n + 63) / 64, (m + 63) / 64);
+  k_dgemm_rm<<<grid, 256, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+  note_launch();
+}
+
+// Dense slab blocks from the CSR of J_0: row r of slab b (permuted index pr = iperm[r]) scatters its
+// entries into D_b (same slab), Lo_b (slab b-1) or Up_b (slab b+1); anything else flags an error.
+__global__ void k_slab_blocks(const long long* __restrict__ rowptr, const int* __restrict__ col,
+                              const double* __restrict__ val, long long n, const int* __restrict__ iperm,
+                              const int* __restrict__ blk, const long long* __restrict__ off,
+                              const long long* __restrict__ dpos, const long long* __restrict__ lpos,
+                              const long long* __restrict__ upos, double* __restrict__ store, int* flag) {
+  for (long long r = blockIdx.x; r < n; r += gridDim.x) {
+    const int pr = iperm[r];
+    const int b = blk[pr];
+    const long long i = pr - off[b];
+    const long long nb = off[b + 1] - off[b];
+    for (long long e = rowptr[r] + threadIdx.x; e < rowptr[r + 1]; e += blockDim.x) {
+      const int pc = iperm[col[e]];
+      const int bc = blk[pc];
+      if (bc == b) {
+        store[dpos[b] + i * nb + (pc - off[b])] = val[e];
+      } else if (bc == b - 1) {
+        store[lpos[b] + i * (off[b] - off[b - 1]) + (pc - off[b - 1])] = val[e];
+      } else if (bc == b + 1) {
+        store[upos[b] + i * (off[b + 2] - off[b + 1]) + (pc - off[b + 1])] = val[e];
+      } else {
+        atomicExch(flag, 1);
+      }
+    }
+  }
+}
+
+// Single-CTA Gauss-Jordan inverse of a small dense block (in place, through shared memory).
+__global__ void __launch_bounds__(1024) k_block_inverse_smem(double* __restrict__ M, int n, int* flag) {
+  extern __shared__ double sm[];
+  double* A = sm;
+  short* perm = reinterpret_cast<short*>(A + (size_t)n * n);
+  __shared__ int s_piv, s_bad;
+  if (threadIdx.x == 0) s_bad = 0;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) A[e] = M[e];
+  __syncthreads();
+  if (!gj_invert_smem(A, perm, n, &s_piv, &s_bad)) {
+    if (threadIdx.x == 0) atomicExch(flag, 1);
+    return;
+  }
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) M[e] = A[e];
+}
+
+// Explicit inverse of a dense n x n block in global memory, one pivot at a time (larger blocks).
+static void block_inverse_global(double* M, long long n, int* piv, double* scal, int* flag, cudaStream_t s) {
   const int vb = (int)std::min<long long>((n + 255) / 256, 152 * 8);
   const int mb = (int)std::min<long long>((n * n + 255) / 256, 152 * 32);
   for (int k = 0; k < n; ++k) {
-    k_gj_pivot<<<1, 1024, 0, s>>>(H.cinv, n, k, piv, scal, H.dflag + 1); note_launch();
-    k_gj_swap_scale<<<vb, 256, 0, s>>>(H.cinv, n, k, piv, scal); note_launch();
-    k_gj_update<<<mb, 256, 0, s>>>(H.cinv, n, k, piv, scal); note_launch();
-    k_gj_column<<<vb, 256, 0, s>>>(H.cinv, n, k, piv, scal); note_launch();
+    k_gj_pivot<<<1, 1024, 0, s>>>(M, n, k, piv, scal, flag); note_launch();
+    k_gj_swap_scale<<<vb, 256, 0, s>>>(M, n, k, piv, scal); note_launch();
+    k_gj_update<<<mb, 256, 0, s>>>(M, n, k, piv, scal); note_launch();
+    k_gj_column<<<vb, 256, 0, s>>>(M, n, k, piv, scal); note_launch();
   }
-  for (int k = (int)n - 1; k >= 0; --k) k_gj_colswap<<<vb, 256, 0, s>>>(H.cinv, n, k, piv); note_launch();
-  STM_CUDA(cudaGetLastError());
-  STM_CUDA(cudaStreamSynchronize(s));
-  cudaFree(piv);
-  cudaFree(scal);
-  return STM_OK;
+  for (int k = (int)n - 1; k >= 0; --k) {
+    k_gj_colswap<<<vb, 256, 0, s>>>(M, n, k, piv);
+    note_launch();
+  }
+}
+
+__global__ void k_copy_block(const double* __restrict__ src, long long rows, long long cols, long long lds,
+                             double* __restrict__ dst, long long ldd) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < rows * cols;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / cols, j = e - i * cols;
+    dst[i * ldd + j] = src[i * lds + j];
+  }
+}
+
+// cinv[i][j] = Xp[iperm[i]][iperm[j]]
+__global__ void k_unpermute(const double* __restrict__ Xp, const int* __restrict__ iperm, long long n,
+                            double* __restrict__ out) {
+  for (long long i = blockIdx.y; i < n; i += gridDim.y) {
+    const double* src = Xp + (long long)iperm[i] * n;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x)
+      out[i * n + j] = src[iperm[j]];
+  }
+}
+
+// Slab ordering of level 0 (host, once).
+static void coarse_slabs(const Level& L, std::vector<int>& iperm, std::vector<int>& blk, std::vector<long long>& off) {
+  const int d = L.dim, nx = L.cells[0];
+  const long long n = L.N;
+  std::vector<int> slab(n);
+  for (int a = 0; a < L.K; ++a) {
+    for (int l = 0; l < d; ++l)
+      for (int nd = 0; nd < L.R; ++nd) {
+        const int lx = L.h_node_lat[nd] % L.lat[0];
+        slab[a * L.block + (long long)l * L.R + nd] = std::min(lx / 2, nx - 1);
+      }
+    for (int c = 0; c < L.C; ++c)
+      for (int q = 0; q < L.np; ++q)
+        slab[a * L.block + (long long)d * L.R + (long long)c * L.np + q] = std::min(L.h_cell_xyz[3 * c] + 1, nx - 1);
+  }
+  off.assign(nx + 2, 0);
+  for (long long r = 0; r < n; ++r) off[slab[r] + 1]++;
+  for (int b = 0; b < nx; ++b) off[b + 1] += off[b];
+  off[nx + 1] = off[nx];
+  iperm.assign(n, 0);
+  blk.assign(n, 0);
+  std::vector<long long> fill(off.begin(), off.begin() + nx);
+  for (long long r = 0; r < n; ++r) {
+    const long long pr = fill[slab[r]]++;
+    iperm[r] = (int)pr;
+    blk[pr] = slab[r];
+  }
+}
+
+stm_status factor_coarse(Hierarchy& H, cudaStream_t s) {
+  Level& L = H.L[0];
+  const long long n = L.N;
+  const int nx = L.cells[0];
+  H.N0 = n;
+  std::vector<int> iperm, blk;
+  std::vector<long long> off;
+  coarse_slabs(L, iperm, blk, off);
+  // dense block storage: D_b, Lo_b (b >= 1), Up_b (b < nx-1), W_b, G_b
+  std::vector<long long> dpos(nx), lpos(nx, 0), upos(nx, 0), wpos(nx, 0), gpos(nx, 0);
+  long long tot = 0;
+  long long maxnb = 0;
+  for (int b = 0; b < nx; ++b) {
+    const long long nb = off[b + 1] - off[b];
+    maxnb = std::max(maxnb, nb);
+    dpos[b] = tot; tot += nb * nb;
+    if (b > 0) { lpos[b] = tot; tot += nb * (off[b] - off[b - 1]); }
+    if (b + 1 < nx) { upos[b] = tot; tot += nb * (off[b + 2] - off[b + 1]); }
+  }
+  for (int b = 0; b < nx; ++b) {
+    const long long nb = off[b + 1] - off[b];
+    if (b + 1 < nx) { wpos[b] = tot; tot += nb * (off[b + 2] - off[b + 1]); }
+    if (b > 0) { gpos[b] = tot; tot += nb * (off[b] - off[b - 1]); }
+  }
+  int *d_iperm = nullptr, *d_blk = nullptr, *piv = nullptr;
+  long long *d_off = nullptr, *d_dpos = nullptr, *d_lpos = nullptr, *d_upos = nullptr;
+  double *store = nullptr, *Xp = nullptr, *scal = nullptr;
+  stm_status st = STM_OK;
+  auto fail = [&](stm_status e) { st = e; };
+  do {
+    if (cudaMalloc(&d_iperm, sizeof(int) * n) || cudaMalloc(&d_blk, sizeof(int) * n) ||
+        cudaMalloc(&d_off, sizeof(long long) * (nx + 2)) || cudaMalloc(&d_dpos, sizeof(long long) * nx) ||
+        cudaMalloc(&d_lpos, sizeof(long long) * nx) || cudaMalloc(&d_upos, sizeof(long long) * nx) ||
+        cudaMalloc(&store, sizeof(double) * tot) || cudaMalloc(&Xp, sizeof(double) * n * n) ||
+        cudaMalloc(&piv, sizeof(int) * maxnb) || cudaMalloc(&scal, sizeof(double) * 2)) {
+      cudaGetLastError();
+      set_error("coarse factorisation: out of device memory");
+      fail(STM_ERR_OOM);
+      break;
+    }
+    if (!H.cinv && cudaMalloc(&H.cinv, sizeof(double) * n * n)) {
+      cudaGetLastError();
+      set_error("coarse factorisation: out of device memory");
+      fail(STM_ERR_OOM);
+      break;
+    }
+    cudaMemcpyAsync(d_iperm, iperm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(d_blk, blk.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(d_off, off.data(), sizeof(long long) * (nx + 2), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(d_dpos, dpos.data(), sizeof(long long) * nx, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(d_lpos, lpos.data(), sizeof(long long) * nx, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(d_upos, upos.data(), sizeof(long long) * nx, cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(store, 0, sizeof(double) * tot, s);
+    cudaMemsetAsync(Xp, 0, sizeof(double) * n * n, s);
+    k_slab_blocks<<<(int)std::min<long long>(n, 152 * 32), 128, 0, s>>>(L.rowptr, L.colidx, L.val, n, d_iperm, d_blk,
+                                                                          d_off, d_dpos, d_lpos, d_upos, store,
+                                                                          H.dflag + 1);
+    note_launch();
+    int dev = 0, maxsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    // forward block LU
+    for (int b = 0; b < nx; ++b) {
+      const long long nb = off[b + 1] - off[b];
+      double* Db = store + dpos[b];
+      if (b > 0) {  // S_b = A_bb - A_{b,b-1} W_{b-1}
+        const long long np_ = off[b] - off[b - 1];
+        dgemm((int)nb, (int)nb, (int)np_, -1.0, store + lpos[b], np_, store + wpos[b - 1], nb, 1.0, Db, nb, s);
+      }
+      const size_t smem = sizeof(double) * nb * nb + sizeof(short) * nb + 16;
+      if (smem + 64 <= (size_t)maxsm) {
+        cudaFuncSetAttribute(k_block_inverse_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_block_inverse_smem<<<1, 1024, smem, s>>>(Db, (int)nb, H.dflag + 1);
+        note_launch();
+      } else {
+        block_inverse_global(Db, nb, piv, scal, H.dflag + 1, s);
+      }
+      if (b + 1 < nx) {  // W_b = S_b^{-1} A_{b,b+1}
+        const long long nn_ = off[b + 2] - off[b + 1];
+        dgemm((int)nb, (int)nn_, (int)nb, 1.0, Db, nb, store + upos[b], nn_, 0.0, store + wpos[b], nn_, s);
+      }
+      if (b > 0) {  // G_b = S_b^{-1} A_{b,b-1}
+        const long long np_ = off[b] - off[b - 1];
+        dgemm((int)nb, (int)np_, (int)nb, 1.0, Db, nb, store + lpos[b], np_, 0.0, store + gpos[b], np_, s);
+      }
+    }
+    // Z = L^{-1} (block lower triangular) into the block rows of Xp
+    for (int b = 0; b < nx; ++b) {
+      const long long nb = off[b + 1] - off[b];
+      double* rowb = Xp + off[b] * n;
+      k_copy_block<<<(int)std::min<long long>((nb * nb + 255) / 256, 152 * 8), 256, 0, s>>>(
+          store + dpos[b], nb, nb, nb, rowb + off[b], n);
+      note_launch();
+      if (b > 0) {
+        const long long np_ = off[b] - off[b - 1];
+        dgemm((int)nb, (int)off[b], (int)np_, -1.0, store + gpos[b], np_, Xp + off[b - 1] * n, n, 0.0, rowb, n, s);
+      }
+    }
+    // X = U^{-1} Z, last block row first
+    for (int b = nx - 2; b >= 0; --b) {
+      const long long nb = off[b + 1] - off[b], nn_ = off[b + 2] - off[b + 1];
+      dgemm((int)nb, (int)n, (int)nn_, -1.0, store + wpos[b], nn_, Xp + off[b + 1] * n, n, 1.0, Xp + off[b] * n, n, s);
+    }
+    dim3 ug((unsigned)std::min<long long>((n + 255) / 256, 64), (unsigned)std::min<long long>(n, 65535));
+    k_unpermute<<<ug, 256, 0, s>>>(Xp, d_iperm, n, H.cinv);
+    note_launch();
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+      set_error("coarse factorisation: CUDA error");
+      fail(STM_ERR_CUDA);
+    }
+  } while (false);
+  void* ptrs[] = {d_iperm, d_blk, piv, d_off, d_dpos, d_lpos, d_upos, store, Xp, scal};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  return st;
 }
 
 }  // namespace stm

@@ -51,3 +51,26 @@ def lattice_to_gpu(h, state, level=None):
 def rel_max(a, b):
     a, b = np.asarray(a), np.asarray(b)
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def poiseuille_state(lev, U, nu):
+    """Exact steady channel flow on an oracle level (2D): velocity U g_1 e_x at every time node,
+    g_1 = 4y(H-y)/H^2 (3D: times 4z(L2-z)/L2^2); pressure (8 nu U / H^2)(L - x) (zero at the do-nothing outflow) as Legendre P1
+    coefficients per cell: mean at the centre, x-slope coefficient -(8 nu U / H^2) h_x / (2 sqrt 3)."""
+    H, L = lev.length[1], lev.length[0]
+    lat = np.stack(np.unravel_index(lev.lat_of_node, lev.lshape[::-1])[::-1], axis=1)
+    y = lat[:, 1] * (lev.h[1] / 2.0)
+    g = 4.0 * y * (H - y) / H**2
+    if lev.dim == 3:  # the inflow profile's z factor (the state is then not a steady solution)
+        L2 = lev.length[2]
+        z = lat[:, 2] * (lev.h[2] / 2.0)
+        g = g * 4.0 * z * (L2 - z) / L2**2
+    G = 8.0 * nu * U / H**2
+    X = np.zeros(lev.N)
+    for a in range(lev.k + 1):
+        X[a * lev.block: a * lev.block + lev.R] = U * g
+        xc = (lev.cell_xyz[:, 0] + 0.5) * lev.h[0]
+        base = a * lev.block + lev.dim * lev.R + np.arange(lev.C) * lev.np_
+        X[base] = G * (L - xc)
+        X[base + 1] = -G * lev.h[0] / (2.0 * np.sqrt(3.0))
+    return X

@@ -5,6 +5,7 @@ import pytest
 from scipy import optimize
 
 import synth
+from helpers import poiseuille_state as _poiseuille_state
 from oracle import adjoint, fem, newton
 
 
@@ -99,3 +100,52 @@ def test_gmg_newton_equals_direct_newton():
     Xd, idd = newton.newton_solve(wl, X0, 0.3, linear="lu", abs_tol=1e-12, reduction=1e30)
     assert len(ig["res"]) == len(idd["res"])
     assert np.abs(Xg - Xd).max() <= 1e-9 * np.abs(Xd).max()
+
+
+# ---------------------------------------------------------------------------------------------
+# previous-slab load and time marching (Problem 3.1)
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("dim,k", [(2, 1), (2, 2), (3, 1)])
+def test_prev_slab_load_equals_analytic_poiseuille_term(dim, k):
+    """The Poiseuille field is exactly Q2, so the discrete previous-slab term of its interpolant equals
+    the analytic term <U g_1 e_x, psi(t_{n-1}^+)>."""
+    cells = (4, 2) if dim == 2 else (4, 2, 2)
+    wl = synth.small_workload(dim, k, cells, 1, obstacle=False)
+    lev = _fine(wl)
+    U = 0.3
+    X = _poiseuille_state(lev, U, wl.nu)
+    g_only = newton.inflow_load(lev, U, wl.nu, wl.tau)
+    analytic = adjoint.newton_rhs(lev, None, U, wl.nu, wl.tau, with_convection=False) - g_only
+    discrete = newton.prev_slab_load(lev, X)
+    assert np.abs(discrete - analytic).max() <= 1e-13 * np.abs(analytic).max()
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_poiseuille_is_a_discrete_steady_solution(k):
+    """In a channel without obstacle, Poiseuille flow with its linear pressure and do-nothing outflow
+    solves the Navier-Stokes slab problem exactly in Q2/P1disc x dG(k): F vanishes to rounding, which
+    pins every term of A, c and b (time derivative and jump, viscous and Nitsche forms, pressure
+    coupling, convection, inflow data, previous-slab term) at once."""
+    wl = synth.small_workload(2, k, (8, 2), 1, obstacle=False)
+    lev = _fine(wl)
+    U = 0.3
+    X = _poiseuille_state(lev, U, wl.nu)
+    for prev in (None, X):
+        prob = newton.SlabProblem(lev, U, wl.nu, wl.tau, X_prev=prev)
+        F = prob.residual(X)
+        assert np.linalg.norm(F) <= 1e-12 * np.linalg.norm(prob.b), np.linalg.norm(F)
+    # a wrong pressure level is not a solution (the outflow condition fixes it)
+    Xs = X.copy()
+    for a in range(lev.k + 1):
+        Xs[a * lev.block + lev.dim * lev.R::lev.np_][:lev.C] += 0.01
+    assert np.linalg.norm(newton.SlabProblem(lev, U, wl.nu, wl.tau).residual(Xs)) > 1e-6
+
+
+def test_time_march_from_poiseuille_stays():
+    wl = synth.small_workload(2, 1, (8, 2), 2, obstacle=False)
+    lev = _fine(wl)
+    X = _poiseuille_state(lev, 0.3, wl.nu)
+    states, _, infos = newton.time_march(wl, X, 0.3, 3, linear="lu", abs_tol=1e-12, reduction=1e30)
+    for Xn, inf in zip(states, infos):
+        assert inf["converged"]
+        assert np.abs(Xn - X).max() <= 1e-10 * np.abs(X).max()
