@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--multi-restart", type=int, default=20)
     ap.add_argument("--robustness", action="store_true",
                     help="viscosity / damping study: Newton and FGMRES counts for nu x omega_d (V(4,4), tau 0.005)")
+    ap.add_argument("--march", type=int, default=0,
+                    help="time-march this many slabs (damped Newton per slab) and report the wake functional")
     ap.add_argument("--newton", action="store_true",
                     help="time the damped Newton solve of the nonlinear slab problem instead of one linear solve")
     ap.add_argument("--oracle-child", default=None, help=argparse.SUPPRESS)
@@ -456,6 +458,54 @@ def gpu_leg_newton(args, local_rank):
     print(json.dumps(line))
 
 
+def gpu_leg_march(args, local_rank):
+    """Time marching (Problem 3.1): args.march slabs from the seeded state, slab n started from slab
+    n-1 with its last time node as initial value, each solved by damped Newton (stop at 1e-10 or a
+    reduction by 1e4) with GMG-FGMRES inner solves; the wake functional int_{I_n} int_wake v_1 per slab."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2107_10561_gb300 import Hierarchy, make_params
+    from paper_2107_10561_gb300 import build as _build
+
+    torch.cuda.set_device(local_rank)
+    _build.build()
+    wl = workload(args.workload)
+    prec = args.precisions.split(",")[-1]
+    p = make_params(wl.dim, wl.k, wl.n_levels, wl.coarse_cells, wl.length, wl.obstacle_lo, wl.obstacle_hi,
+                    wl.tau, wl.nu, wl.gamma1, wl.gamma2, prec, "additive", wl.omega, wl.nu1, wl.nu2)
+    h = Hierarchy(p)
+    idx = h.dof_lattice_index()
+    X0 = torch.from_numpy(np.ascontiguousarray(synth.linearisation_point(wl).reshape(-1)[idx])).cuda()
+    # wake: the two level-1 cell columns behind the obstacle at the obstacle's height (a full-height
+    # box would measure the flux, which the inflow fixes)
+    lo = (wl.obstacle_hi[0], wl.obstacle_lo[1]) + ((0,) if wl.dim == 3 else ())
+    hi = (min(wl.obstacle_hi[0] + 2, wl.coarse_cells[0]), wl.obstacle_hi[1]) + \
+        ((wl.coarse_cells[2],) if wl.dim == 3 else ())
+    j = torch.empty(h.n_dofs(), dtype=torch.float64, device="cuda")
+    h.functional_weights(lo, hi, j)
+    h.time_march(X0, wl.inflow_u, 1, j=j, rtol=args.rtol, restart=wl.restart)  # warm-up slab
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    states, infos, values = h.time_march(X0, wl.inflow_u, args.march, j=j, rtol=args.rtol, restart=wl.restart)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    h.close()
+    line = {"metric": "time-marching s per slab (damped Newton, GMG-FGMRES inner solves)",
+            "value": ms / 1e3 / args.march, "unit": "s", "n_gpus": 1, "steps": args.march, "warmup": 1,
+            "ms_per_step": ms / args.march, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": f"f64 + {prec} cell inverses" if prec != "f64" else "f64", "data": "synthetic",
+            "config": {"workload": f"{wl.name}: {args.march} slabs of tau = {wl.tau} from the seeded state, "
+                                   f"U = {wl.inflow_u}", "wake": {"lo": lo, "hi": hi}, "linear_rtol": args.rtol,
+                       "parallelism": "single GPU"},
+            "slabs": [{"newton_iters": i["newton_iters"], "gmres_step": i["gmres_step"], "res": i["res"],
+                       "wake_functional": v} for i, v in zip(infos, values)]}
+    print(json.dumps(line))
+
+
 def gpu_leg_robustness(args, local_rank):
     """Sec. 5.3 / Table 5.4 on the synthetic channel: for nu in {1e-3, 5e-4, 3e-4, 2e-4, 1e-4} and
     omega_d in {1, 0.7}, one damped-Newton slab solve from the seeded state with V(4,4) cycles and
@@ -539,6 +589,10 @@ def main():
     if args.robustness:
         if rank == 0:
             gpu_leg_robustness(args, local_rank)
+        return
+    if args.march:
+        if rank == 0:
+            gpu_leg_march(args, local_rank)
         return
     if workload(args.workload).extra.get("nrhs"):
         if rank == 0:

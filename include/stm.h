@@ -176,6 +176,9 @@ stm_status stm_assemble_rhs(stm_hierarchy* h, double U, double nu, int which, do
  * X^{m+1} = X^m + lambda D with the first lambda in 1, 1/2, 1/4, ... (at most max_halvings halvings)
  * that lowers ||F||_2. Stops when ||F|| <= max(abs_tol, ||F(X^0)|| / reduction) (Sec. 5.1 uses 1e-10
  * and 1e4). F is evaluated as (b + c(X, X)) - J(X) X, which equals -F since J(X) X = A X + 2 c(X, X).
+ * prev_dev: NULL, or the previous slab's FP64 finest-level DoF vector (time marching, Problem 3.1): the
+ * initial value v(t_{n-1}^-) is then the velocity of its last time node (right Radau: the slab end), and
+ * b holds <v_h(t_{n-1}^-), psi(t_{n-1}^+)> for that discrete field instead of the Poiseuille state.
  * X_dev: FP64 [n_dofs of the finest level], the initial iterate on entry and the last iterate on
  * return (also on STM_ERR_NOT_CONVERGED). On return J is assembled at the last iterate and the cell
  * factors are stale (call stm_factor_cells before another linear solve). Synchronises once per
@@ -197,8 +200,9 @@ typedef struct {
   double lam[STM_NEWTON_MAX_STEPS];     /* accepted step lengths */
   int gmres_step[STM_NEWTON_MAX_STEPS]; /* FGMRES iterations of each step */
 } stm_newton_info;
-stm_status stm_newton_solve(stm_hierarchy* h, double U, double nu, double* X_dev, const stm_newton_opts* nopts,
-                            const stm_gmres_opts* gopts, stm_newton_info* info, void* stream);
+stm_status stm_newton_solve(stm_hierarchy* h, double U, double nu, double* X_dev, const double* prev_dev,
+                            const stm_newton_opts* nopts, const stm_gmres_opts* gopts, stm_newton_info* info,
+                            void* stream);
 
 /* Weights j of the drag-like functional J(X) = int_{I_n} int_wake v_1 dx dt = j . X, where the wake
  * is the union of finest cells inside the level-1 cell box [wake_lo, wake_hi) (all z in 3D).

@@ -68,8 +68,8 @@ SIGNATURES = {
     "stm_gmres_solve": ([_P, _P, _P, C.POINTER(GmresOpts), C.POINTER(SolveInfo), _P], _I),
     "stm_gmres_solve_host": ([_P, _DP, _DP, C.POINTER(GmresOpts), C.POINTER(SolveInfo), _P], _I),
     "stm_assemble_rhs": ([_P, _D, _D, _I, _P, _P], _I),
-    "stm_newton_solve": ([_P, _D, _D, _P, C.POINTER(NewtonOpts), C.POINTER(GmresOpts), C.POINTER(NewtonInfo), _P],
-                         _I),
+    "stm_newton_solve": ([_P, _D, _D, _P, _P, C.POINTER(NewtonOpts), C.POINTER(GmresOpts), C.POINTER(NewtonInfo),
+                          _P], _I),
     "stm_functional_weights": ([_P, _IP, _IP, _P, _P], _I),
     "stm_jacobian_dnu_apply": ([_P, _P, _P, _P], _I),
     "stm_dot": ([_P, _P, _P, _L, _DP, _P], _I),

@@ -403,10 +403,10 @@ static stm_status assemble_all(Hierarchy& H, const double* X, double nu, cudaStr
 
 // With J = J(X) assembled at X: negF = (b + c(X, X)) - J(X) X = -F(X) (F = A X + c(X, X) - b, and
 // J(X) X = A X + 2 c(X, X)); *norm = ||F(X)||_2.
-static stm_status newton_residual(Hierarchy& H, const double* X, double U, double nu, double* negF, double* norm,
-                                  cudaStream_t s) {
+static stm_status newton_residual(Hierarchy& H, const double* X, double U, double nu, const double* vprev,
+                                  double* negF, double* norm, cudaStream_t s) {
   const long long N = H.L.back().N;
-  STM_TRY(assemble_cellvec(H, 0, U, nu, nullptr, nullptr, H.nw_B, s));
+  STM_TRY(assemble_cellvec(H, 0, U, nu, nullptr, nullptr, H.nw_B, s, vprev));
   STM_TRY(jacobian_apply(H, (int)H.L.size() - 1, X, H.nw_B, negF, 1, 0, s));
   STM_TRY(vec_norm_sq(negF, N, H.hcol, H.part, H.nblk_dot, s));
   double t = 0.0;
@@ -420,8 +420,9 @@ static stm_status newton_residual(Hierarchy& H, const double* X, double U, doubl
   return STM_OK;
 }
 
-stm_status stm_newton_solve(stm_hierarchy* h, double U, double nu, double* X, const stm_newton_opts* nopts,
-                            const stm_gmres_opts* gopts, stm_newton_info* info, void* stream) {
+stm_status stm_newton_solve(stm_hierarchy* h, double U, double nu, double* X, const double* prev,
+                            const stm_newton_opts* nopts, const stm_gmres_opts* gopts, stm_newton_info* info,
+                            void* stream) {
   if (!h || !X || !nopts || !gopts) return bad_arg("NULL argument");
   if (nopts->max_newton < 0 || nopts->max_newton > STM_NEWTON_MAX_STEPS || nopts->max_halvings < 0 ||
       nopts->max_halvings > 60 || !(nopts->abs_tol >= 0.0) || !(nopts->reduction >= 1.0))
@@ -435,13 +436,15 @@ stm_status stm_newton_solve(stm_hierarchy* h, double U, double nu, double* X, co
   double** bufs[] = {&H.nw_negF, &H.nw_D, &H.nw_Xt, &H.nw_B, &H.nw_Ft};
   for (double** b : bufs)
     if (!*b) STM_CUDA(cudaMalloc((void**)b, sizeof(double) * N));
+  // the previous slab's last time node (right Radau: the slab end) carries v(t_{n-1}^-)
+  const double* vprev = prev ? prev + (long long)(H.L.back().K - 1) * H.L.back().block : nullptr;
   stm_newton_info inf{};
   stm_gmres_opts go = *gopts;
   go.transpose = 0;
   go.use_x0 = 0;
   double res = 0.0;
   STM_TRY(assemble_all(H, X, nu, s));
-  STM_TRY(newton_residual(H, X, U, nu, H.nw_negF, &res, s));
+  STM_TRY(newton_residual(H, X, U, nu, vprev, H.nw_negF, &res, s));
   inf.res[0] = res;
   inf.n_res = 1;
   const double target = std::max(nopts->abs_tol, res / nopts->reduction);
@@ -463,7 +466,7 @@ stm_status stm_newton_solve(stm_hierarchy* h, double U, double nu, double* X, co
       STM_TRY(vec_copy(H.nw_Xt, X, N, s));
       STM_TRY(vec_axpy(H.nw_Xt, lam, H.nw_D, N, s));
       STM_TRY(assemble_all(H, H.nw_Xt, nu, s));
-      STM_TRY(newton_residual(H, H.nw_Xt, U, nu, H.nw_Ft, &rt, s));
+      STM_TRY(newton_residual(H, H.nw_Xt, U, nu, vprev, H.nw_Ft, &rt, s));
       if (rt < res || hv == nopts->max_halvings) break;
       lam *= 0.5;
     }

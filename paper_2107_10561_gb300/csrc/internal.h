@@ -235,7 +235,7 @@ stm_status vanka_step(Hierarchy& H, int g, const double* r, double* d, int trans
                       bool d_is_zero, cudaStream_t s);
 stm_status coarse_apply(Hierarchy& H, const double* r, double* d, int transpose, cudaStream_t s);
 stm_status assemble_cellvec(Hierarchy& H, int mode, double U, double nu, const int* wake_lo, const int* wake_hi,
-                            double* out, cudaStream_t s);
+                            double* out, cudaStream_t s, const double* vprev = nullptr);
 stm_status dnu_apply(Hierarchy& H, const double* x, double* y, cudaStream_t s);
 // multi-right-hand-side path (kernels_multi.cu), multi-vectors interleaved [N][32]
 stm_status multi_to_interleaved(const double* src, double* dst, long long N, int nrhs, cudaStream_t s);

@@ -3,7 +3,8 @@
 // With the linearisation point w fixed, one Newton step from w solves J(w; nu) X = b(U, nu) + c(w, w):
 //   b(U, nu) = int_{I_n} B_GamD(g, (psi, xi)) dt + <v(t_{n-1}^-), psi(t_{n-1}^+)>   (Problem 3.1,
 //   Eqs. Def:Lh, Def:B_GamD; f = 0), with the inflow data g = U g_1 on x = 0 (zero on walls and
-//   obstacle) and the previous-slab state U g_1 e_x (Poiseuille field, exact in Q2);
+//   obstacle) and the previous-slab state U g_1 e_x (Poiseuille field, exact in Q2), or, for time
+//   marching, the discrete velocity of the previous slab's last time node (right Radau: t_{n-1});
 //   c(w, w) = sum_{b,c} T_abc <(w^c . grad) w^b, psi>, the convection term at w (J(w) w - A(w) w).
 // The drag-like functional is J(X) = int_{I_n} int_wake v_1 dx dt = j . X.
 // b is linear in U and affine in nu; J is affine in nu with dJ/dnu = Mt (x) (K - G - G^T + gamma1/h S)
@@ -35,11 +36,12 @@ __global__ void __launch_bounds__(256) k_cellvec(const int* __restrict__ cells, 
                                                  const int* __restrict__ cell_xyz, const unsigned char* __restrict__ bmask,
                                                  const double* __restrict__ wnod, const double* __restrict__ ref,
                                                  RefOffsets ro, VecConst vc, int d, int K, int R, int n, int nt,
-                                                 double* __restrict__ out) {
+                                                 const double* __restrict__ vprev, double* __restrict__ out) {
   extern __shared__ double sm[];
   const int nv = ro.nv, np = ro.np, nq = ro.nq;
-  double* wq = sm;               // [K][nq][d]
-  double* gw = wq + K * nq * d;  // [K][nq][d][d]
+  double* wq = sm;                // [K][nq][d]
+  double* gw = wq + K * nq * d;   // [K][nq][d][d]
+  double* pq = gw + K * nq * d * d;  // [nq][d] previous-slab velocity at the quadrature points
   const double* W = ref + ro.W;
   const double* phi = ref + ro.phi;
   const double* gphi = ref + ro.gphi;
@@ -65,6 +67,14 @@ __global__ void __launch_bounds__(256) k_cellvec(const int* __restrict__ cells, 
         wq[(cc * nq + q) * d + l] = v;
         for (int m = 0; m < d; ++m) gw[((cc * nq + q) * d + l) * d + m] = g[m];
       }
+      if (vprev)
+        for (int e = threadIdx.x; e < nq * d; e += blockDim.x) {
+          const int l = e % d, q = e / d;
+          const double* vl = vprev + (long long)l * R;
+          double v = 0.0;
+          for (int s2 = 0; s2 < nv; ++s2) v += phi[q * nv + s2] * vl[cn[s2]];
+          pq[q * d + l] = v;
+        }
     }
     __syncthreads();
     for (int al = threadIdx.x; al < n; al += blockDim.x) {
@@ -91,7 +101,12 @@ __global__ void __launch_bounds__(256) k_cellvec(const int* __restrict__ cells, 
             if (mode == VEC_RHS_DNU) v += vc.U * vc.tint[a] * (-s_n + vc.g1 / vc.hT * s_p);
             else v += (mode == VEC_RHS ? vc.U : 1.0) * vc.tint[a] * (-vc.nu * s_n + (vc.g1 * vc.nu + vc.g2) / vc.hT * s_p);
           }
-          if (l == 0 && mode != VEC_RHS_DNU) {
+          if (mode == VEC_RHS && vprev) {
+            // <v_h(t_{n-1}^-), psi(t_{n-1}^+)> with the discrete previous-slab velocity
+            double s = 0.0;
+            for (int q = 0; q < nq; ++q) s += W[q] * phi[q * nv + i] * pq[q * d + l];
+            v += vc.chi0[a] * s;
+          } else if (l == 0 && mode != VEC_RHS_DNU) {
             double s = 0.0;
             for (int q = 0; q < nq; ++q) {
               const double y = o[1] + vc.h[1] * ref[ro.Xq + q * d + 1];
@@ -192,7 +207,7 @@ static VecConst make_vc(const Hierarchy& H, const Level& L, double U, double nu)
 }
 
 stm_status assemble_cellvec(Hierarchy& H, int mode, double U, double nu, const int* wake_lo, const int* wake_hi,
-                            double* out, cudaStream_t s) {
+                            double* out, cudaStream_t s, const double* vprev) {
   Level& L = H.L.back();
   VecConst vc = make_vc(H, L, U, nu);
   const int f = 1 << ((int)H.L.size() - 1);
@@ -205,14 +220,15 @@ stm_status assemble_cellvec(Hierarchy& H, int mode, double U, double nu, const i
     }
   }
   STM_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * L.N, s));
-  const size_t smem = sizeof(double) * (size_t)L.K * L.ro.nq * L.dim * (1 + L.dim);
+  const size_t smem = sizeof(double) * ((size_t)L.K * L.ro.nq * L.dim * (1 + L.dim) + (size_t)L.ro.nq * L.dim);
   if (smem > 48 * 1024) STM_CUDA(cudaFuncSetAttribute(k_cellvec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   for (int col = 0; col < (1 << L.dim); ++col) {
     const int nc = L.colour_off[col + 1] - L.colour_off[col];
     if (!nc) continue;
     k_cellvec<<<std::min(nc, 152 * 8), 256, smem, s>>>(L.colour_cells + L.colour_off[col], nc, mode, L.idx,
                                                        L.cell_nodes, L.cell_xyz, L.bmask, L.wnod, L.ref, L.ro, vc,
-                                                       L.dim, L.K, L.R, L.n, L.nt, out);
+                                                       L.dim, L.K, L.R, L.n, L.nt, mode == 0 ? vprev : nullptr,
+                                                       out);
     note_launch();
     STM_CUDA(cudaGetLastError());
   }

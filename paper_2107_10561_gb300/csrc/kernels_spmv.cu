@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(256, (K == 3 ? 3 : 4)) k_spmv_nodeblock(
     const long long* __restrict__ nbase, const int* __restrict__ nbr_ptr, const int* __restrict__ nbr,
     const int* __restrict__ ncell, const int* __restrict__ node_cells, const int* __restrict__ cell_nodes,
     const int* __restrict__ job_nodes, long long block, int R, int C, int nv, const double* __restrict__ x,
-    const double* __restrict__ b, double* __restrict__ y, int mode, long long nwv) {
+    const double* __restrict__ b, double* __restrict__ y, int mode, int vpc) {
   constexpr int GPW = 32 / VL;
   constexpr int KD = K * D;
   constexpr int NP = D + 1;
@@ -258,15 +258,18 @@ __global__ void __launch_bounds__(256, (K == 3 ? 3 : 4)) k_spmv_nodeblock(
   static_assert(NAV <= VL || VL >= 4, "group too small");
   const int lane = threadIdx.x & (VL - 1);
   const int gw = (threadIdx.x & 31) / VL;
-  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const int wslot = threadIdx.x >> 5, nslot = blockDim.x >> 5;
   int wmask_v;
   constexpr int NAV_R = NAV < VL ? NAV : VL;
   const int kv = scatter_index<VL, NAV_R>(lane, &wmask_v);
-  // warps [0, nwv) take the velocity rows node by node, the others the pressure rows, so that on
-  // small levels the two latency chains run side by side
-  if (warp < nwv) {
-  for (long long wb = warp * GPW; wb < R; wb += nwv * GPW) {
+  // vpc < 8: the first vpc warps of every CTA take the velocity rows node by node, the others the
+  // pressure rows, so the two kinds of work (FP64-heavy, load-heavy) run side by side on every SM and
+  // their latency chains overlap; vpc = 8: every warp takes velocity groups, then pressure rows
+  const bool both = vpc >= nslot;
+  if (both || wslot < vpc) {
+  const int vs = both ? nslot : vpc;
+  const long long vw = (long long)blockIdx.x * vs + wslot, nvw = (long long)gridDim.x * vs;
+  for (long long wb = vw * GPW; wb < R; wb += nvw * GPW) {
     const long long job = wb + gw;
     const bool ok = job < R;
     const int i = ok ? job_nodes[job] : 0;
@@ -326,12 +329,14 @@ __global__ void __launch_bounds__(256, (K == 3 ? 3 : 4)) k_spmv_nodeblock(
         }
     }
   }
-  } else {
+  }
+  if (both || wslot >= vpc) {
     // Pressure rows: one lane per row pr = (a*C + c)*n_p + q over the warp-transposed copy, so entry
     // t of 32 consecutive rows is one contiguous 256-byte load; all lanes busy, no cross-lane sums.
     constexpr int NV = D == 2 ? 9 : 27;
-    const long long tid_g = (warp - nwv) * 32 + (threadIdx.x & 31);
-    const long long nthreads = (nwarps - nwv) * 32;
+    const int pslots = both ? nslot : nslot - vpc;
+    const long long tid_g = ((long long)blockIdx.x * pslots + (both ? wslot : wslot - vpc)) * 32 + (threadIdx.x & 31);
+    const long long nthreads = (long long)gridDim.x * pslots * 32;
     const long long npr = (long long)K * C * NP;
     for (long long pr = tid_g; pr < npr; pr += nthreads) {
       const int a = (int)(pr / ((long long)C * NP));
@@ -362,13 +367,23 @@ static void launch_nodeblock(const Level& L, const double* x, const double* b, d
   constexpr int GPW = 32 / VL;
   const long long npr = (long long)K * L.C * (D + 1);
   const long long need_v = (L.R + GPW - 1) / GPW, need_p = (npr + 31) / 32;
-  // one unit per warp (a group of GPW nodes, or 32 pressure rows): the block scheduler hands out
-  // the work dynamically as CTAs retire, so the tail is at most one unit long
-  const long long blocks = std::max<long long>(1, (need_v + need_p + 7) / 8);
-  const long long nwv = need_v;
+  int vpc;
+  long long blocks;
+  if (D == 2 && VL == 4) {
+    // large 2D levels (velocity rows ~96% of the entries): every warp takes velocity groups, then
+    // pressure rows, over a grid of up to 4 CTAs per SM (measured best there)
+    vpc = 8;
+    blocks = std::min<long long>(std::max((long long)L.R * VL, npr), (long long)sms_count() * 4 * 256);
+    blocks = std::max<long long>(1, (blocks + 255) / 256);
+  } else {
+    // 3D and small 2D levels: one unit per warp (a group of GPW nodes, or 32 pressure rows), the two
+    // kinds mixed in every CTA in proportion to their counts; CTAs are handed out as others retire
+    vpc = (int)std::min<long long>(7, std::max<long long>(1, (8 * need_v + (need_v + need_p) / 2) / (need_v + need_p)));
+    blocks = std::max<long long>(1, std::max((need_v + vpc - 1) / vpc, (need_p + (8 - vpc) - 1) / (8 - vpc)));
+  }
   k_spmv_nodeblock<VL, K, D><<<(int)blocks, 256, 0, s>>>(L.rowptr, L.val, L.nval, L.pvalT, L.nbase, L.nbr_ptr, L.nbr,
                                                          L.ncell, L.node_cells, L.cell_nodes, L.job_nodes, L.block,
-                                                         L.R, L.C, L.nv, x, b, y, mode, nwv);
+                                                         L.R, L.C, L.nv, x, b, y, mode, vpc);
 }
 
 stm_status spmv_nodeblock(const Level& L, const double* x, const double* b, double* y, int mode, cudaStream_t s) {

@@ -174,15 +174,17 @@ class Hierarchy:
                                              _stream(stream)), "stm_assemble_rhs")
 
     def newton_solve(self, X, U, nu=None, max_newton=20, max_halvings=8, abs_tol=1e-10, reduction=1e4,
-                     rtol=1e-10, restart=30, max_iter=1000, stream=None, raise_on_fail=True):
+                     rtol=1e-10, restart=30, max_iter=1000, prev=None, stream=None, raise_on_fail=True):
         """Damped Newton for the slab problem F(X) = A X + c(X, X) - b(U, nu) = 0 (stm_newton_solve).
 
-        X: device float64 [n_dofs], initial iterate, overwritten with the last iterate."""
+        X: device float64 [n_dofs], initial iterate, overwritten with the last iterate.
+        prev: None (initial value U g_1 e_x) or the previous slab's device DoF vector (time marching)."""
         nu = self.params.nu if nu is None else nu
         no = _lib.NewtonOpts(int(max_newton), int(max_halvings), float(abs_tol), float(reduction))
         go = self._opts(restart, max_iter, rtol, False, False)
         inf = _lib.NewtonInfo()
-        st = self.lib.stm_newton_solve(self.h, float(U), float(nu), _ptr(X, self.n_dofs(), "X"), C.byref(no),
+        pp = None if prev is None else _ptr(prev, self.n_dofs(), "prev")
+        st = self.lib.stm_newton_solve(self.h, float(U), float(nu), _ptr(X, self.n_dofs(), "X"), pp, C.byref(no),
                                        C.byref(go), C.byref(inf), _stream(stream))
         info = {"newton_iters": inf.newton_iters, "gmres_iters": inf.gmres_iters, "converged": bool(inf.converged),
                 "res": [inf.res[i] for i in range(inf.n_res)], "lam": [inf.lam[i] for i in range(inf.newton_iters)],
@@ -191,6 +193,22 @@ class Hierarchy:
         if st != _lib.STM_OK and raise_on_fail:
             _lib.check(st, "stm_newton_solve")
         return info
+
+    def time_march(self, X_init, U, n_slabs, j=None, **newton_kw):
+        """Slabs 1..n_slabs in sequence (Problem 3.1): slab n starts from the previous slab's state and
+        takes its last time node as initial value. Returns the slab states (device tensors), the Newton
+        infos and, with functional weights j (device), the history j . X_n."""
+        import torch
+        states, infos, values = [], [], []
+        prev = X_init
+        for _ in range(n_slabs):
+            X = prev.clone()
+            infos.append(self.newton_solve(X, U, prev=prev, **newton_kw))
+            states.append(X)
+            if j is not None:
+                values.append(float(torch.dot(j, X)))
+            prev = X
+        return states, infos, values
 
     def functional_weights(self, wake_lo, wake_hi, j, stream=None):
         lo = (C.c_int * 3)(*(list(wake_lo) + [0] * (3 - len(wake_lo))))

@@ -81,3 +81,53 @@ def test_stopping_rule():
     r = ig["res"]
     target = max(1e-10, r[0] / 1e4)
     assert ig["converged"] and r[-1] <= target and all(x > target for x in r[:-1])
+
+
+def test_time_march_matches_oracle():
+    """Three slabs in sequence (Problem 3.1), each started from the previous slab's state with the
+    previous slab's last time node as initial value; slab states and the wake functional follow the
+    oracle's time marching."""
+    from oracle import adjoint, newton
+    from oracle.fem import Level
+    wl = CASES["2d_k2_obs"]
+    f = 2 ** (wl.n_levels - 1)
+    lev = Level(wl.dim, wl.k, wl.fine_cells, wl.length, tuple(x * f for x in wl.obstacle_lo),
+                tuple(x * f for x in wl.obstacle_hi))
+    st = _state(wl, 0.1)
+    # wake: two cell columns behind the obstacle, at the obstacle's height only (a full-height box
+    # would integrate the flux, which the inflow fixes in every slab)
+    lo, hi = (2, 1), (4, 2)
+    jo = adjoint.functional_weights(lev, tuple(x * f for x in lo), tuple(x * f for x in hi), wl.tau)
+    so, vo, io = newton.time_march(wl, lev.dofs_from_lattice(st), 0.3, 3, j=jo, linear="lu", abs_tol=1e-11,
+                                   reduction=1e30)
+    h = gpu_hierarchy(wl, "f64", factor=False)
+    jg = torch.empty(h.n_dofs(), dtype=torch.float64, device="cuda")
+    h.functional_weights(lo, hi, jg)
+    assert rel_max(jg.cpu().numpy(), jo) < 1e-12
+    sg, ig, vg = h.time_march(lattice_to_gpu(h, st), 0.3, 3, j=jg, rtol=1e-12, abs_tol=1e-11, reduction=1e30)
+    h.close()
+    for n in range(3):
+        assert ig[n]["converged"] and ig[n]["newton_iters"] == len(io[n]["lam"])
+        assert rel_max(sg[n].cpu().numpy(), so[n]) < 1e-8, n
+        assert abs(vg[n] - vo[n]) <= 1e-9 * abs(vo[n]), (vg, vo)
+    # the slabs differ: the wake is still developing
+    assert abs(vo[2] - vo[0]) > 1e-6 * abs(vo[0])
+
+
+def test_poiseuille_is_steady_on_gpu():
+    """Channel without obstacle: the exact Poiseuille state (velocity and linear pressure) has a nonlinear
+    residual at rounding level on the GPU too, both with the analytic and the discrete initial value, so
+    Newton takes no step."""
+    from helpers import poiseuille_state
+    from oracle import newton
+    from oracle.fem import Level
+    wl = synth.small_workload(2, 2, (8, 2), 2, obstacle=False)
+    lev = Level(wl.dim, wl.k, wl.fine_cells, wl.length, (0, 0), (0, 0))
+    Xp = poiseuille_state(lev, 0.3, wl.nu)
+    bnorm = np.linalg.norm(newton.SlabProblem(lev, 0.3, wl.nu, wl.tau).b)
+    h = gpu_hierarchy(wl, "f64", factor=False)
+    for use_prev in (False, True):
+        X = torch.from_numpy(Xp).cuda()
+        info = h.newton_solve(X, 0.3, abs_tol=1e-10 * bnorm, prev=X.clone() if use_prev else None)
+        assert info["newton_iters"] == 0 and info["res"][0] <= 1e-12 * bnorm, info
+    h.close()
