@@ -8,7 +8,8 @@
 // pressure, a fine cell's Legendre P1 coefficients follow from its parent's (child position o_m):
 //   c0' = c0 + sum_m sqrt(3) (o_m - 1/2) c_m,    c_m' = c_m / 2.
 // The restriction applies P^T with the transposed node lists and the 2^d children of each coarse
-// cell. One thread per node or cell; no atomics.
+// cell. A group of lanes per node splits its list (so the chains of dependent loads stay short),
+// one thread per cell; no atomics.
 #include "internal.h"
 
 namespace stm {
@@ -29,35 +30,44 @@ struct TransferGeom {
   int fR, cR, fC, cC;        // velocity nodes and cells
 };
 
-// fine += P coarse
-template <int K, int D>
+// fine += P coarse. Velocity: G lanes per fine node share its (coarse node, weight) list and meet
+// through shuffles (short dependent-load chains); then one thread per fine cell for the pressure.
+// The velocity range is padded to whole warps so that every warp is entirely in one part.
+template <int K, int D, int G>
 __global__ void k_prolong(const int* __restrict__ vptr, const int* __restrict__ vnode, const double* __restrict__ vw,
                           const int* __restrict__ parent, const unsigned char* __restrict__ bits, TransferGeom g,
                           const double* __restrict__ xc, double* __restrict__ yf) {
   constexpr int NP = D + 1;
   const double s3 = 1.7320508075688772;  // sqrt(3), P1 Legendre normalisation
-  const long long items = (long long)g.fR + g.fC;
+  const long long vthreads = ((long long)g.fR * G + 31) / 32 * 32;
+  const long long items = vthreads + g.fC;
   for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < items;
        it += (long long)gridDim.x * blockDim.x) {
-    if (it < g.fR) {
-      const int nd = (int)it;
+    if (it < vthreads) {
+      const long long nd = it / G;
+      const int gl = (int)(it % G);
       double acc[K * D];
 #pragma unroll
       for (int r = 0; r < K * D; ++r) acc[r] = 0.0;
-      for (int e = vptr[nd]; e < vptr[nd + 1]; ++e) {
-        const int cn = vnode[e];
-        const double w = vw[e];
+      if (nd < g.fR)
+        for (int e = vptr[nd] + gl; e < vptr[nd + 1]; e += G) {
+          const int cn = vnode[e];
+          const double w = vw[e];
 #pragma unroll
-        for (int a = 0; a < K; ++a)
+          for (int a = 0; a < K; ++a)
 #pragma unroll
-          for (int l = 0; l < D; ++l) acc[a * D + l] += w * __ldg(xc + a * g.cblock + (long long)l * g.cR + cn);
-      }
+            for (int l = 0; l < D; ++l) acc[a * D + l] += w * __ldg(xc + a * g.cblock + (long long)l * g.cR + cn);
+        }
 #pragma unroll
-      for (int a = 0; a < K; ++a)
+      for (int off = G / 2; off > 0; off >>= 1)
 #pragma unroll
-        for (int l = 0; l < D; ++l) yf[a * g.fblock + (long long)l * g.fR + nd] += acc[a * D + l];
+        for (int r = 0; r < K * D; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], off, G);
+      if (nd < g.fR)
+#pragma unroll
+        for (int r = 0; r < K * D; ++r)
+          if (r % G == gl) yf[(r / D) * g.fblock + (long long)(r % D) * g.fR + nd] += acc[r];
     } else {
-      const int cf = (int)(it - g.fR);
+      const int cf = (int)(it - vthreads);
       const int pc = parent[cf];
       const int b = bits[cf];
 #pragma unroll
@@ -75,36 +85,43 @@ __global__ void k_prolong(const int* __restrict__ vptr, const int* __restrict__ 
   }
 }
 
-// coarse = P^T fine
-template <int K, int D>
+// coarse = P^T fine; G lanes per coarse node over its transposed list (up to 5^d entries), as above
+template <int K, int D, int G>
 __global__ void k_restrict(const int* __restrict__ cptr, const int* __restrict__ cnode, const double* __restrict__ cw,
                            const int* __restrict__ children, TransferGeom g, const double* __restrict__ tf,
                            double* __restrict__ rc) {
   constexpr int NP = D + 1;
   constexpr int NCH = 1 << D;
   const double s3 = 1.7320508075688772;
-  const long long items = (long long)g.cR + g.cC;
+  const long long vthreads = ((long long)g.cR * G + 31) / 32 * 32;
+  const long long items = vthreads + g.cC;
   for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < items;
        it += (long long)gridDim.x * blockDim.x) {
-    if (it < g.cR) {
-      const int cn = (int)it;
+    if (it < vthreads) {
+      const long long cn = it / G;
+      const int gl = (int)(it % G);
       double acc[K * D];
 #pragma unroll
       for (int r = 0; r < K * D; ++r) acc[r] = 0.0;
-      for (int e = cptr[cn]; e < cptr[cn + 1]; ++e) {
-        const int nd = cnode[e];
-        const double w = cw[e];
+      if (cn < g.cR)
+        for (int e = cptr[cn] + gl; e < cptr[cn + 1]; e += G) {
+          const int nd = cnode[e];
+          const double w = cw[e];
 #pragma unroll
-        for (int a = 0; a < K; ++a)
+          for (int a = 0; a < K; ++a)
 #pragma unroll
-          for (int l = 0; l < D; ++l) acc[a * D + l] += w * __ldg(tf + a * g.fblock + (long long)l * g.fR + nd);
-      }
+            for (int l = 0; l < D; ++l) acc[a * D + l] += w * __ldg(tf + a * g.fblock + (long long)l * g.fR + nd);
+        }
 #pragma unroll
-      for (int a = 0; a < K; ++a)
+      for (int off = G / 2; off > 0; off >>= 1)
 #pragma unroll
-        for (int l = 0; l < D; ++l) rc[a * g.cblock + (long long)l * g.cR + cn] = acc[a * D + l];
+        for (int r = 0; r < K * D; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], off, G);
+      if (cn < g.cR)
+#pragma unroll
+        for (int r = 0; r < K * D; ++r)
+          if (r % G == gl) rc[(r / D) * g.cblock + (long long)(r % D) * g.cR + cn] = acc[r];
     } else {
-      const int pc = (int)(it - g.cR);
+      const int pc = (int)(it - vthreads);
 #pragma unroll
       for (int a = 0; a < K; ++a) {
         double acc[NP];
@@ -131,18 +148,36 @@ static TransferGeom geom(const Level& F, const Level& Cl) {
   return TransferGeom{F.block, Cl.block, F.R, Cl.R, F.C, Cl.C};
 }
 
+// Lanes per node: fine-node lists hold up to 3^d entries, coarse-node lists up to 5^d. Groups of
+// lanes shorten the chains of dependent loads on the smaller levels; on large levels (at least
+// kManyNodes nodes) one thread per node keeps the stores of consecutive nodes contiguous, which
+// measured faster there.
+constexpr long long kManyNodes = 32768;
+
+template <int K, int D, int G>
+static void launch_prolong_g(const Level& F, const TransferGeom& g, const double* xc, double* yf, cudaStream_t s) {
+  const long long items = ((long long)g.fR * G + 31) / 32 * 32 + g.fC;
+  const int blocks = (int)std::max<long long>(1, std::min<long long>((items + 255) / 256, sm_count_tr() * 8LL));
+  k_prolong<K, D, G><<<blocks, 256, 0, s>>>(F.tv_ptr, F.tv_node, F.tv_w, F.cparent, F.cbits, g, xc, yf);
+}
+
 template <int K, int D>
 static void launch_prolong(const Level& F, const TransferGeom& g, const double* xc, double* yf, cudaStream_t s) {
-  const long long items = (long long)g.fR + g.fC;
+  if (g.fR >= kManyNodes) launch_prolong_g<K, D, 1>(F, g, xc, yf, s);
+  else launch_prolong_g<K, D, D == 2 ? 4 : 8>(F, g, xc, yf, s);
+}
+
+template <int K, int D, int G>
+static void launch_restrict_g(const Level& F, const TransferGeom& g, const double* tf, double* rc, cudaStream_t s) {
+  const long long items = ((long long)g.cR * G + 31) / 32 * 32 + g.cC;
   const int blocks = (int)std::max<long long>(1, std::min<long long>((items + 255) / 256, sm_count_tr() * 8LL));
-  k_prolong<K, D><<<blocks, 256, 0, s>>>(F.tv_ptr, F.tv_node, F.tv_w, F.cparent, F.cbits, g, xc, yf);
+  k_restrict<K, D, G><<<blocks, 256, 0, s>>>(F.tc_ptr, F.tc_node, F.tc_w, F.cchildren, g, tf, rc);
 }
 
 template <int K, int D>
 static void launch_restrict(const Level& F, const TransferGeom& g, const double* tf, double* rc, cudaStream_t s) {
-  const long long items = (long long)g.cR + g.cC;
-  const int blocks = (int)std::max<long long>(1, std::min<long long>((items + 255) / 256, sm_count_tr() * 8LL));
-  k_restrict<K, D><<<blocks, 256, 0, s>>>(F.tc_ptr, F.tc_node, F.tc_w, F.cchildren, g, tf, rc);
+  if (g.cR >= kManyNodes) launch_restrict_g<K, D, 1>(F, g, tf, rc, s);
+  else launch_restrict_g<K, D, D == 2 ? 8 : 16>(F, g, tf, rc, s);
 }
 
 stm_status transfer_prolong_add(const Level& F, const Level& Cl, const double* coarse, double* fine, cudaStream_t s) {
