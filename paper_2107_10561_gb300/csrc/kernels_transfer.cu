@@ -152,7 +152,7 @@ static TransferGeom geom(const Level& F, const Level& Cl) {
 // lanes shorten the chains of dependent loads on the smaller levels; on large levels (at least
 // kManyNodes nodes) one thread per node keeps the stores of consecutive nodes contiguous, which
 // measured faster there.
-constexpr long long kManyNodes = 32768;
+constexpr long long kManyNodes = 16384;
 
 template <int K, int D, int G>
 static void launch_prolong_g(const Level& F, const TransferGeom& g, const double* xc, double* yf, cudaStream_t s) {
