@@ -324,7 +324,65 @@ def gpu_leg(args, rank, world, local_rank):
         h.gmres_solve_host(bh, xh, rtol=args.rtol, restart=wl.restart)
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / args.steps
-    return wl, sizes, results, head, clocks, e2e_s, dist, fp64_peak
+    rows = other_rows(args, wl, hs, head, state, rhs_lat) if rank == 0 else {}
+    return wl, sizes, results, head, clocks, e2e_s, dist, fp64_peak, rows
+
+
+def other_rows(args, wl, hs, head, state, rhs_lat):
+    """Timings of the rows that the headline solve does not isolate, on the same workload and the
+    head precision: one V-cycle (Algorithm 1, direct launches), the adjoint solve J^T lambda = b
+    (transposed Vanka, P/P^T, coarse inverse^T), and the solve with the coloured multiplicative and
+    the literal overwrite smoother (Sec. 4.2)."""
+    import numpy as np
+    import torch
+
+    from paper_2107_10561_gb300 import Hierarchy, make_params
+
+    out = {}
+    h, b, x = hs[head]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    d = torch.zeros_like(b)
+    h.vcycle(b, d)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(10):
+        h.vcycle(b, d)
+    ev1.record()
+    torch.cuda.synchronize()
+    out["vcycle_ms"] = ev0.elapsed_time(ev1) / 10
+    x.zero_()
+    h.gmres_solve(b, x, rtol=args.rtol, restart=wl.restart, transpose=True)  # warm-up (J^T values)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(args.steps):
+        x.zero_()
+        info = h.gmres_solve(b, x, rtol=args.rtol, restart=wl.restart, transpose=True)
+    ev1.record()
+    torch.cuda.synchronize()
+    out["adjoint_solve"] = {"ms": ev0.elapsed_time(ev1) / args.steps, "iters": info["iters"],
+                            "rel_res_true": info["rel_res_true"]}
+    for smoother in ("coloured", "overwrite"):
+        p = make_params(wl.dim, wl.k, wl.n_levels, wl.coarse_cells, wl.length, wl.obstacle_lo, wl.obstacle_hi,
+                        wl.tau, wl.nu, wl.gamma1, wl.gamma2, head, smoother, wl.omega, wl.nu1, wl.nu2)
+        hv = Hierarchy(p)
+        idx = hv.dof_lattice_index()
+        X = torch.from_numpy(np.ascontiguousarray(state.reshape(-1)[idx])).cuda()
+        bv = torch.from_numpy(np.ascontiguousarray(rhs_lat.reshape(-1)[idx])).cuda()
+        hv.assemble_jacobian(X)
+        hv.factor_cells()
+        xv = torch.zeros_like(bv)
+        hv.gmres_solve(bv, xv, rtol=args.rtol, restart=wl.restart, raise_on_fail=False)
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(args.steps):
+            xv.zero_()
+            info = hv.gmres_solve(bv, xv, rtol=args.rtol, restart=wl.restart, raise_on_fail=False)
+        ev1.record()
+        torch.cuda.synchronize()
+        out[f"{smoother}_solve"] = {"ms": ev0.elapsed_time(ev1) / args.steps, "iters": info["iters"],
+                                    "converged": info["status"] == "STM_OK"}
+        hv.close()
+    return out
 
 
 def gpu_leg_multi(args, local_rank):
@@ -598,7 +656,7 @@ def main():
         if rank == 0:
             gpu_leg_multi(args, local_rank)
         return
-    wl, sizes, results, head, clocks, e2e_s, dist, fp64_peak = gpu_leg(args, rank, world, local_rank)
+    wl, sizes, results, head, clocks, e2e_s, dist, fp64_peak, rows = gpu_leg(args, rank, world, local_rank)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -643,6 +701,7 @@ def main():
                              "s_per_solve_profiled_pass": v["ms_per_solve_profiled"] / 1e3}
                          for p, v in results.items()},
         "gpu_launches": int(r["launches_per_step"] * args.steps),
+        "other_rows": rows,
         "roofline": spmv_roofline(r, wl, sizes, fp64_peak, args.workload),
         "roofline_vanka_sweep": {"kernel": f"{vk} (y_T = J_T^{{-1}} t_T), finest level, {head} inverses",
                                  "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",

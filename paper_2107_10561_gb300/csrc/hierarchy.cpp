@@ -492,10 +492,12 @@ static stm_status build_level(const stm_params& p, int g, Level& L, std::vector<
     nbase[nd + 1] = nbase[nd] + (long long)(L.K * d) * ((long long)L.K * d * nn[nd] + (long long)np * ncell[nd]);
   STM_TRY(upload(&L.nbase, nbase));
   STM_CUDA(cudaMalloc((void**)&L.nval, sizeof(double) * nbase[R]));
+  L.nval_len = nbase[R];
   {
     const long long prows = ((long long)L.K * C * np + 31) / 32 * 32;
-    STM_CUDA(cudaMalloc((void**)&L.pvalT, sizeof(double) * prows * d * L.nv));
-    STM_CUDA(cudaMemset(L.pvalT, 0, sizeof(double) * prows * d * L.nv));
+    L.pval_len = prows * d * L.nv;
+    STM_CUDA(cudaMalloc((void**)&L.pvalT, sizeof(double) * L.pval_len));
+    STM_CUDA(cudaMemset(L.pvalT, 0, sizeof(double) * L.pval_len));
   }
   std::vector<int> job_nodes(R);
   std::iota(job_nodes.begin(), job_nodes.end(), 0);
@@ -748,7 +750,7 @@ void free_hierarchy(Hierarchy& H) {
   H.cap_stream = nullptr;
   for (Level& L : H.L) {
     void* ptrs[] = {L.idx, L.cell_nodes, L.cell_xyz, L.bmask, L.rank, L.cellrank, L.nn, L.ncell, L.rowptr, L.nbr_ptr, L.nbr,
-                    L.node_cells, L.job_nodes, L.nbase, L.nval, L.pvalT,
+                    L.node_cells, L.job_nodes, L.nbase, L.nval, L.pvalT, L.nvalJT, L.pvalJT,
                     L.colidx, L.val, L.valT, L.ref, L.inj, L.wnod, L.inv, L.wmult, L.own_ptr,
                     L.own_pos, L.last_owner, L.colour_cells, L.Y, L.P_rowptr, L.P_col, L.P_val,
                     L.Rt_rowptr, L.Rt_col, L.Rt_val, L.tv_ptr, L.tv_node, L.tv_w, L.tc_ptr, L.tc_node,
@@ -756,7 +758,7 @@ void free_hierarchy(Hierarchy& H) {
     for (void* q : ptrs)
       if (q) cudaFree(q);
   }
-  void* hp[] = {H.cinv, H.dflag, H.dbad, H.V, H.Z, H.w, H.hcol, H.part, H.yvec, H.bbuf, H.xbuf,
+  void* hp[] = {H.cinv, H.cpart, H.dflag, H.dbad, H.V, H.Z, H.w, H.hcol, H.part, H.yvec, H.bbuf, H.xbuf,
                 H.nw_negF, H.nw_D, H.nw_Xt, H.nw_B, H.nw_Ft,
                 H.mV, H.mZ, H.mW, H.mB, H.mX, H.mh, H.mpart, H.mf, H.my};
   for (void* q : hp)

@@ -17,6 +17,7 @@ namespace stm {
 constexpr int STM_KCLASS_COUNT = 6;
 
 constexpr int kMaxDim = 3;
+constexpr int kCoarseTChunk = 512;  // rows per partial sum of the transposed coarse solve
 constexpr int kQ1 = 4;  // Gauss points per direction (exact for every integrand of the forms)
 
 // Thread-local error message and helpers -----------------------------------------------------
@@ -111,6 +112,8 @@ struct Level {
   // pressure rows pr = (a*C + c)*n_p + q of J, warp-transposed for the forward SpMV: entry
   // t = m*nv + j of row pr at pvalT[((pr/32)*d*nv + t)*32 + pr%32] (rows padded to a multiple of 32)
   double* pvalT = nullptr;
+  double *nvalJT = nullptr, *pvalJT = nullptr;  // the same two copies for J^T (built with valT)
+  long long nval_len = 0, pval_len = 0;          // entries of nval and pvalT
   int* ncell = nullptr;           // [R] number of cells containing the node
   long long* rowptr = nullptr;    // [N+1]
   int* colidx = nullptr;          // [nnz]
@@ -159,6 +162,7 @@ struct Hierarchy {
   // coarse direct solver: explicit FP64 inverse of J_0, row-major [N0][N0]
   double* cinv = nullptr;
   long long N0 = 0;
+  double* cpart = nullptr;  // [ceil(N0 / kCoarseTChunk)][N0] partial sums of the transposed coarse solve
   int* dflag = nullptr;           // device flags: [0] singular flag, [1..2] bad cell (int64 split)
   long long* dbad = nullptr;
   // FGMRES work space (finest level)
@@ -225,10 +229,11 @@ stm_status csr_apply(const long long* rowptr, const int* col, const double* val,
 // Matrix-free transfers between level g-1 and level g (kernels_transfer.cu)
 stm_status transfer_restrict(const Level& F, const Level& Cl, const double* fine, double* coarse, cudaStream_t s);
 stm_status transfer_prolong_add(const Level& F, const Level& Cl, const double* coarse, double* fine, cudaStream_t s);
-stm_status spmv_structured(const Level& L, const double* v, const double* x, const double* b, double* y, int mode,
-                           cudaStream_t s);
-stm_status spmv_nodeblock(const Level& L, const double* x, const double* b, double* y, int mode, cudaStream_t s);
+stm_status spmv_nodeblock(const Level& L, const double* nval, const double* pvalT, const double* x, const double* b,
+                          double* y, int mode, cudaStream_t s);
 stm_status build_nodeblock(Level& L, cudaStream_t s);
+// node-block and warp-transposed pressure-row copies of any value array on J's pattern (J or J^T)
+stm_status build_nodeblock_from(const Level& L, const double* val, double* nval, double* pvalT, cudaStream_t s);
 stm_status jacobian_apply(Hierarchy& H, int g, const double* x, const double* b, double* y,
                           int mode, int transpose, cudaStream_t s);
 stm_status vanka_step(Hierarchy& H, int g, const double* r, double* d, int transpose,

@@ -250,6 +250,14 @@ stm_status assemble_level(Hierarchy& H, int g, double nu, cudaStream_t s) {
     cudaFree(L.valT);
     L.valT = nullptr;
   }
+  if (L.nvalJT) {
+    cudaFree(L.nvalJT);
+    L.nvalJT = nullptr;
+  }
+  if (L.pvalJT) {
+    cudaFree(L.pvalJT);
+    L.pvalJT = nullptr;
+  }
   return build_nodeblock(L, s);
 }
 

@@ -490,6 +490,13 @@ stm_status factor_coarse(Hierarchy& H, cudaStream_t s) {
       fail(STM_ERR_OOM);
       break;
     }
+    // scratch of the transposed coarse solve, allocated here so that solves can be graph-captured
+    if (!H.cpart && cudaMalloc(&H.cpart, sizeof(double) * ((n + kCoarseTChunk - 1) / kCoarseTChunk) * n)) {
+      cudaGetLastError();
+      set_error("coarse factorisation: out of device memory");
+      fail(STM_ERR_OOM);
+      break;
+    }
     cudaMemcpyAsync(d_iperm, iperm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(d_blk, blk.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(d_off, off.data(), sizeof(long long) * (nx + 2), cudaMemcpyHostToDevice, s);

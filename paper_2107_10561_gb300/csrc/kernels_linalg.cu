@@ -117,21 +117,20 @@ stm_status ensure_transpose(Hierarchy& H, int g, cudaStream_t s) {
     set_error("J pattern is not structurally symmetric");
     return STM_ERR_STATE;
   }
-  return STM_OK;
+  // node-block and pressure-row copies of J^T for the transposed SpMV
+  STM_CUDA(cudaMalloc(&L.nvalJT, sizeof(double) * L.nval_len));
+  STM_CUDA(cudaMalloc(&L.pvalJT, sizeof(double) * L.pval_len));
+  STM_CUDA(cudaMemsetAsync(L.pvalJT, 0, sizeof(double) * L.pval_len, s));
+  return build_nodeblock_from(L, L.valT, L.nvalJT, L.pvalJT, s);
 }
 
 stm_status jacobian_apply(Hierarchy& H, int g, const double* x, const double* b, double* y, int mode,
                           int transpose, cudaStream_t s) {
   Level& L = H.L[g];
-  const double* v = L.val;
-  if (transpose) {
-    stm_status st = ensure_transpose(H, g, s);
-    if (st != STM_OK) return st;
-    v = L.valT;
-  }
+  if (transpose) STM_TRY(ensure_transpose(H, g, s));
   ProfScope ps(&H, STM_KCLASS_JACOBIAN_SPMV, s, 8.0 * (double)L.nnz + 24.0 * (double)L.N, g);
-  if (!transpose) return spmv_nodeblock(L, x, b, y, mode, s);
-  return spmv_structured(L, v, x, b, y, mode, s);
+  if (!transpose) return spmv_nodeblock(L, L.nval, L.pvalT, x, b, y, mode, s);
+  return spmv_nodeblock(L, L.nvalJT, L.pvalJT, x, b, y, mode, s);
 }
 
 // Dense coarse solve: d = Cinv r (row-major) or d = Cinv^T r.
@@ -147,11 +146,21 @@ __global__ void k_dense_gemv(const double* __restrict__ A, long long n, const do
     if (lane == 0) y[row] = s;
   }
 }
-__global__ void k_dense_gemv_t(const double* __restrict__ A, long long n, const double* __restrict__ x,
-                               double* __restrict__ y) {
+// d = Cinv^T r in two passes: CTA (x, y) takes 128 columns over one chunk of kCoarseTChunk rows (one
+// thread per column, coalesced rows), then every column adds its chunk partials in chunk order.
+__global__ void k_dense_gemv_t_part(const double* __restrict__ A, long long n, const double* __restrict__ x,
+                                    double* __restrict__ part) {
+  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const long long i0 = (long long)blockIdx.y * kCoarseTChunk, i1 = min(n, i0 + (long long)kCoarseTChunk);
+  double s = 0.0;
+  for (long long i = i0; i < i1; ++i) s += A[i * n + j] * x[i];
+  part[(long long)blockIdx.y * n + j] = s;
+}
+__global__ void k_dense_gemv_t_sum(const double* __restrict__ part, long long n, int chunks, double* __restrict__ y) {
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
     double s = 0.0;
-    for (long long i = 0; i < n; ++i) s += A[i * n + j] * x[i];
+    for (int c = 0; c < chunks; ++c) s += part[(long long)c * n + j];
     y[j] = s;
   }
 }
@@ -163,8 +172,12 @@ stm_status coarse_apply(Hierarchy& H, const double* r, double* d, int transpose,
     const int blocks = (int)std::min<long long>((n + 7) / 8, (long long)sms() * 16);
     k_dense_gemv<<<blocks, 256, 0, s>>>(H.cinv, n, r, d); note_launch();
   } else {
-    const int blocks = (int)std::min<long long>((n + 127) / 128, (long long)sms() * 8);
-    k_dense_gemv_t<<<blocks, 128, 0, s>>>(H.cinv, n, r, d); note_launch();
+    const int chunks = (int)((n + kCoarseTChunk - 1) / kCoarseTChunk);
+    dim3 grid((unsigned)((n + 127) / 128), (unsigned)chunks);
+    k_dense_gemv_t_part<<<grid, 128, 0, s>>>(H.cinv, n, r, H.cpart); note_launch();
+    k_dense_gemv_t_sum<<<(int)std::min<long long>((n + 255) / 256, (long long)sms() * 8), 256, 0, s>>>(H.cpart, n, chunks,
+                                                                                                     d);
+    note_launch();
   }
   STM_CUDA(cudaGetLastError());
   return STM_OK;
@@ -299,21 +312,35 @@ stm_status vec_scale_to(double* y, const double* x, const double* sc, int inv, l
 }
 
 // part[v][blk] = partial sum of V[v] . w over the block's chunk; then out[v] = sum_blk part (fixed order)
+// Four dot products per pass over w (w read once for each group of four); per product the same
+// reduction tree as a single one: warp shuffles, then the warp sums in warp order.
 __global__ void k_dots_partial(const double* __restrict__ V, int nv, const double* __restrict__ w, long long n,
                                double* __restrict__ part) {
-  __shared__ double red[32];
-  for (int v = 0; v < nv; ++v) {
-    const double* a = V + (long long)v * n;
-    double s = 0.0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-      s += a[i] * w[i];
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  constexpr int CH = 4;
+  __shared__ double red[CH][32];
+  for (int v0 = 0; v0 < nv; v0 += CH) {
+    const int nc = min(CH, nv - v0);
+    double s[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) s[u] = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+      const double wi = w[i];
+#pragma unroll
+      for (int u = 0; u < CH; ++u)
+        if (u < nc) s[u] += V[(long long)(v0 + u) * n + i] * wi;
+    }
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      for (int off = 16; off > 0; off >>= 1) s[u] += __shfl_down_sync(0xffffffffu, s[u], off);
+      if ((threadIdx.x & 31) == 0) red[u][threadIdx.x >> 5] = s[u];
+    }
     __syncthreads();
     if (threadIdx.x < 32) {
-      s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-      for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-      if (threadIdx.x == 0) part[(long long)v * gridDim.x + blockIdx.x] = s;
+      for (int u = 0; u < nc; ++u) {
+        double t = threadIdx.x < (blockDim.x >> 5) ? red[u][threadIdx.x] : 0.0;
+        for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+        if (threadIdx.x == 0) part[(long long)(v0 + u) * gridDim.x + blockIdx.x] = t;
+      }
     }
     __syncthreads();
   }

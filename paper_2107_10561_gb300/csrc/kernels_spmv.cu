@@ -1,18 +1,20 @@
-// Structured product with the slab Jacobian J_g (FP64): y = J x, y = b - J x or y += J x.
+// Structured product with the slab Jacobian J_g or its transpose (FP64): y = J x, y = b - J x or
+// y += J x.
 //
 // Every velocity row (a, l, i) of J couples node i with the same neighbour list nbr(i) in every
 // (time b, component m) block, plus the pressures of the cells around i at time a (Problem 3.1,
-// Eq. newton_system_matrix_dG_1 with a diagonal time mass). A VL-lane group therefore takes one
-// node and computes all K*d of its velocity rows together: each neighbour's K*d entries of x are
-// loaded once and reused by all K*d rows, and the column indices are never read (the values are
-// addressed through the row pointers and the neighbour list). Pressure rows (a, cell, q) are
-// taken one cell per group, all K*n_p rows at once. Values are streamed (cache-streaming loads).
-// FP64 issue slots are the limit on this part (one FP64 warp instruction every ~17 cycles per SM).
-// A group (16 lanes in 2D, 32 in 3D) walks the flattened positions of its rows, so each step reads
-// whole 128-byte lines of every row and few lanes idle; the rows' partial sums are combined by a
-// reduce-scatter butterfly (few FP64 adds); node jobs are ordered by neighbour count (job_nodes) so
-// that the groups of one warp run equal trip counts.
-// Results equal the plain CSR product up to FP64 summation order.
+// Eq. newton_system_matrix_dG_1 with a diagonal time mass); a pressure row (a, cell, q) holds the
+// velocities of its cell at time a. The pattern is structurally symmetric, so J^T uses the same
+// structure with permuted values.
+// The values are copied once per assembly into two layouts built for this product:
+//   - node blocks: the K*d velocity rows of node i share one column structure, so position p of the
+//     node holds those rows' K*d values contiguously; VL lanes per node walk consecutive positions
+//     (one contiguous run), load each x entry once for all K*d rows, and combine the K*d partial
+//     sums through a reduce-scatter butterfly (few FP64 adds); nodes are ordered by neighbour
+//     count so that the groups of one warp run equal trip counts;
+//   - warp-transposed pressure rows: one lane per row, entry t of 32 consecutive rows contiguous.
+// Column indices are never read. FP64 issue slots are the limit (one FP64 warp instruction every
+// 16 cycles per SM). Results equal the plain CSR product up to FP64 summation order.
 #include "internal.h"
 
 namespace stm {
@@ -61,118 +63,6 @@ __device__ __forceinline__ int scatter_index(int lane, int* writer_mask) {
   }
   *writer_mask = wm;
   return k;
-}
-
-template <int VL, int K, int D>
-__global__ void __launch_bounds__(256, 4) k_spmv_struct(
-    const long long* __restrict__ rowptr, const double* __restrict__ val, const int* __restrict__ nbr_ptr,
-    const int* __restrict__ nbr, const int* __restrict__ ncell, const int* __restrict__ node_cells,
-    const int* __restrict__ cell_nodes, const int* __restrict__ job_nodes, long long block, int R, int C, int nv,
-    const double* __restrict__ x, const double* __restrict__ b, double* __restrict__ y, int mode) {
-  constexpr int GPW = 32 / VL;
-  constexpr int KD = K * D;
-  constexpr int NP = D + 1;  // P1 pressure modes per cell
-  constexpr int KP = K * NP;
-  constexpr int MAXC = 1 << D;
-  constexpr int NAV = pow2ceil(KD);
-  constexpr int NAP = pow2ceil(KP);
-  const int lane = threadIdx.x & (VL - 1);
-  const int gw = (threadIdx.x & 31) / VL;
-  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  int wmask_v, wmask_p;
-  const int kv = scatter_index<VL, NAV>(lane, &wmask_v);
-  const int kp = scatter_index<VL, NAP>(lane, &wmask_p);
-
-  // phase 1: the K*D velocity rows of one node per group (warp-uniform loop)
-  for (long long wb = warp * GPW; wb < R; wb += nwarps * GPW) {
-    const long long job = wb + gw;
-    const bool ok = job < R;
-    const int i = ok ? job_nodes[job] : 0;
-    double acc[NAV];
-#pragma unroll
-    for (int r = 0; r < NAV; ++r) acc[r] = 0.0;
-    if (ok) {
-      const int p0 = nbr_ptr[i], nn = nbr_ptr[i + 1] - p0, nc = ncell[i];
-      long long rp[KD];
-#pragma unroll
-      for (int a = 0; a < K; ++a)
-#pragma unroll
-        for (int l = 0; l < D; ++l) rp[a * D + l] = rowptr[a * block + (long long)l * R + i];
-      // flattened velocity positions p = (b*D + m)*nn + j of the row, VL consecutive per step
-      const int npos = KD * nn;
-      int j = lane, bm = 0;
-      while (j >= nn) { j -= nn; ++bm; }
-      for (int p = lane; p < npos; p += VL) {
-        const int bb = bm / D, m = bm - bb * D;
-        const double xv = __ldg(x + bb * block + (long long)m * R + nbr[p0 + j]);
-#pragma unroll
-        for (int a = 0; a < K; ++a) {
-          const int off = p + (bb > a ? NP * nc : 0);
-#pragma unroll
-          for (int l = 0; l < D; ++l) acc[a * D + l] += __ldcs(val + rp[a * D + l] + off) * xv;
-        }
-        j += VL;
-        while (j >= nn) { j -= nn; ++bm; }
-      }
-      // pressure columns of time a: n_p entries per cell of node i, after the time-a velocity block
-      for (int t = lane; t < NP * nc; t += VL) {
-        const int ci = t / NP, q = t - ci * NP;
-        const long long pc = (long long)D * R + (long long)node_cells[(long long)i * MAXC + ci] * NP + q;
-#pragma unroll
-        for (int a = 0; a < K; ++a) {
-          const double xp = __ldg(x + a * block + pc);
-          const int off = (a + 1) * D * nn + t;
-#pragma unroll
-          for (int l = 0; l < D; ++l) acc[a * D + l] += __ldcs(val + rp[a * D + l] + off) * xp;
-        }
-      }
-    }
-    reduce_scatter<VL, NAV>(acc, lane);
-    if (ok && kv < KD && (lane & wmask_v) == 0) {
-      const int a = kv / D, l = kv - a * D;
-      const long long row = a * block + (long long)l * R + i;
-      const double v = acc[0];
-      if (mode == 0) y[row] = v;
-      else if (mode == 1) y[row] = b[row] - v;
-      else y[row] += v;
-    }
-  }
-
-  // phase 2: the K*n_p pressure rows of one cell per group; entries ordered m * nv + j
-  for (long long wb = warp * GPW; wb < C; wb += nwarps * GPW) {
-    const long long c = wb + gw;
-    const bool ok = c < C;
-    double acc[NAP];
-#pragma unroll
-    for (int r = 0; r < NAP; ++r) acc[r] = 0.0;
-    if (ok) {
-      long long rp[KP];
-#pragma unroll
-      for (int a = 0; a < K; ++a)
-#pragma unroll
-        for (int q = 0; q < NP; ++q) rp[a * NP + q] = rowptr[a * block + (long long)D * R + c * NP + q];
-      for (int t = lane; t < D * nv; t += VL) {
-        const int m = t / nv, jj = t - m * nv;
-        const int node = cell_nodes[c * nv + jj];
-#pragma unroll
-        for (int a = 0; a < K; ++a) {
-          const double xa = __ldg(x + a * block + (long long)m * R + node);
-#pragma unroll
-          for (int q = 0; q < NP; ++q) acc[a * NP + q] += __ldcs(val + rp[a * NP + q] + t) * xa;
-        }
-      }
-    }
-    reduce_scatter<VL, NAP>(acc, lane);
-    if (ok && kp < KP && (lane & wmask_p) == 0) {
-      const int a = kp / NP, q = kp - a * NP;
-      const long long row = a * block + (long long)D * R + c * NP + q;
-      const double v = acc[0];
-      if (mode == 0) y[row] = v;
-      else if (mode == 1) y[row] = b[row] - v;
-      else y[row] += v;
-    }
-  }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -224,15 +114,17 @@ __global__ void k_build_pval(const long long* __restrict__ rowptr, const double*
   }
 }
 
-stm_status build_nodeblock(Level& L, cudaStream_t s) {
+stm_status build_nodeblock(Level& L, cudaStream_t s) { return build_nodeblock_from(L, L.val, L.nval, L.pvalT, s); }
+
+stm_status build_nodeblock_from(const Level& L, const double* val, double* nval, double* pvalT, cudaStream_t s) {
   const int blocks = (int)std::min<long long>(((long long)L.R * 32 + 255) / 256, 152LL * 8);
-  k_build_nodeblock<<<blocks, 256, 0, s>>>(L.rowptr, L.val, L.nbr_ptr, L.ncell, L.nbase, L.nval, L.block, L.R, L.K,
+  k_build_nodeblock<<<blocks, 256, 0, s>>>(L.rowptr, val, L.nbr_ptr, L.ncell, L.nbase, nval, L.block, L.R, L.K,
                                            L.dim, L.np);
   note_launch();
   STM_CUDA(cudaGetLastError());
   const long long npr = (long long)L.K * L.C * L.np;
   const int pblocks = (int)std::min<long long>((npr + 255) / 256, 152LL * 8);
-  k_build_pval<<<std::max(pblocks, 1), 256, 0, s>>>(L.rowptr, L.val, L.pvalT, L.block, L.R, L.C, L.K, L.dim, L.np,
+  k_build_pval<<<std::max(pblocks, 1), 256, 0, s>>>(L.rowptr, val, pvalT, L.block, L.R, L.C, L.K, L.dim, L.np,
                                                     L.nv);
   note_launch();
   STM_CUDA(cudaGetLastError());
@@ -363,7 +255,8 @@ __global__ void __launch_bounds__(256, (K == 3 ? 3 : 4)) k_spmv_nodeblock(
 static int sms_count();
 
 template <int VL, int K, int D>
-static void launch_nodeblock(const Level& L, const double* x, const double* b, double* y, int mode, cudaStream_t s) {
+static void launch_nodeblock(const Level& L, const double* nval, const double* pvalT, const double* x, const double* b,
+                             double* y, int mode, cudaStream_t s) {
   constexpr int GPW = 32 / VL;
   const long long npr = (long long)K * L.C * (D + 1);
   const long long need_v = (L.R + GPW - 1) / GPW, need_p = (npr + 31) / 32;
@@ -381,12 +274,13 @@ static void launch_nodeblock(const Level& L, const double* x, const double* b, d
     vpc = (int)std::min<long long>(7, std::max<long long>(1, (8 * need_v + (need_v + need_p) / 2) / (need_v + need_p)));
     blocks = std::max<long long>(1, std::max((need_v + vpc - 1) / vpc, (need_p + (8 - vpc) - 1) / (8 - vpc)));
   }
-  k_spmv_nodeblock<VL, K, D><<<(int)blocks, 256, 0, s>>>(L.rowptr, L.val, L.nval, L.pvalT, L.nbase, L.nbr_ptr, L.nbr,
+  k_spmv_nodeblock<VL, K, D><<<(int)blocks, 256, 0, s>>>(L.rowptr, L.val, nval, pvalT, L.nbase, L.nbr_ptr, L.nbr,
                                                          L.ncell, L.node_cells, L.cell_nodes, L.job_nodes, L.block,
                                                          L.R, L.C, L.nv, x, b, y, mode, vpc);
 }
 
-stm_status spmv_nodeblock(const Level& L, const double* x, const double* b, double* y, int mode, cudaStream_t s) {
+stm_status spmv_nodeblock(const Level& L, const double* nval, const double* pvalT, const double* x, const double* b,
+                          double* y, int mode, cudaStream_t s) {
   // short groups (4 lanes in 2D, 8 in 3D) need at least ~1024 resident threads per SM to keep
   // enough loads in flight; smaller levels use 16 lanes per node
   const long long per_sm_threads = 1024;
@@ -394,24 +288,24 @@ stm_status spmv_nodeblock(const Level& L, const double* x, const double* b, doub
   if ((long long)L.R * (L.dim == 2 ? 4 : 8) < (long long)sms_count() * per_sm_threads) cls = 100;
   if ((long long)L.R * 16 < (long long)sms_count() * per_sm_threads / 4) cls = 200;
   switch (L.dim * 10 + L.K + cls) {
-    case 21: launch_nodeblock<4, 1, 2>(L, x, b, y, mode, s); break;
-    case 22: launch_nodeblock<4, 2, 2>(L, x, b, y, mode, s); break;
-    case 23: launch_nodeblock<4, 3, 2>(L, x, b, y, mode, s); break;
-    case 31: launch_nodeblock<8, 1, 3>(L, x, b, y, mode, s); break;
-    case 32: launch_nodeblock<8, 2, 3>(L, x, b, y, mode, s); break;
-    case 33: launch_nodeblock<8, 3, 3>(L, x, b, y, mode, s); break;
-    case 121: launch_nodeblock<16, 1, 2>(L, x, b, y, mode, s); break;
-    case 122: launch_nodeblock<16, 2, 2>(L, x, b, y, mode, s); break;
-    case 123: launch_nodeblock<16, 3, 2>(L, x, b, y, mode, s); break;
-    case 131: launch_nodeblock<16, 1, 3>(L, x, b, y, mode, s); break;
-    case 132: launch_nodeblock<16, 2, 3>(L, x, b, y, mode, s); break;
-    case 133: launch_nodeblock<16, 3, 3>(L, x, b, y, mode, s); break;
-    case 221: launch_nodeblock<32, 1, 2>(L, x, b, y, mode, s); break;
-    case 222: launch_nodeblock<32, 2, 2>(L, x, b, y, mode, s); break;
-    case 223: launch_nodeblock<32, 3, 2>(L, x, b, y, mode, s); break;
-    case 231: launch_nodeblock<32, 1, 3>(L, x, b, y, mode, s); break;
-    case 232: launch_nodeblock<32, 2, 3>(L, x, b, y, mode, s); break;
-    case 233: launch_nodeblock<32, 3, 3>(L, x, b, y, mode, s); break;
+    case 21: launch_nodeblock<4, 1, 2>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 22: launch_nodeblock<4, 2, 2>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 23: launch_nodeblock<4, 3, 2>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 31: launch_nodeblock<8, 1, 3>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 32: launch_nodeblock<8, 2, 3>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 33: launch_nodeblock<8, 3, 3>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 121: launch_nodeblock<16, 1, 2>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 122: launch_nodeblock<16, 2, 2>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 123: launch_nodeblock<16, 3, 2>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 131: launch_nodeblock<16, 1, 3>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 132: launch_nodeblock<16, 2, 3>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 133: launch_nodeblock<16, 3, 3>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 221: launch_nodeblock<32, 1, 2>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 222: launch_nodeblock<32, 2, 2>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 223: launch_nodeblock<32, 3, 2>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 231: launch_nodeblock<32, 1, 3>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 232: launch_nodeblock<32, 2, 3>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 233: launch_nodeblock<32, 3, 3>(L, nval, pvalT, x, b, y, mode, s); break;
     default:
       set_error("node-block SpMV: unsupported (dim, k)");
       return STM_ERR_INVALID_ARG;
@@ -430,34 +324,6 @@ static int sms_count() {
     if (n <= 0) n = 152;
   }
   return n;
-}
-
-template <int VL, int K, int D>
-static void launch_struct(const Level& L, const double* v, const double* x, const double* b, double* y, int mode,
-                          cudaStream_t s) {
-  const long long threads_needed = (long long)std::max(L.R, L.C) * VL;
-  const int blocks = (int)std::min<long long>((threads_needed + 255) / 256, (long long)sms_count() * 8);
-  k_spmv_struct<VL, K, D><<<blocks, 256, 0, s>>>(L.rowptr, v, L.nbr_ptr, L.nbr, L.ncell, L.node_cells, L.cell_nodes,
-                                                 L.job_nodes, L.block, L.R, L.C, L.nv, x, b, y, mode);
-}
-
-stm_status spmv_structured(const Level& L, const double* v, const double* x, const double* b, double* y, int mode,
-                           cudaStream_t s) {
-  const int key = L.dim * 10 + L.K;
-  switch (key) {
-    case 21: launch_struct<16, 1, 2>(L, v, x, b, y, mode, s); break;
-    case 22: launch_struct<16, 2, 2>(L, v, x, b, y, mode, s); break;
-    case 23: launch_struct<16, 3, 2>(L, v, x, b, y, mode, s); break;
-    case 31: launch_struct<32, 1, 3>(L, v, x, b, y, mode, s); break;
-    case 32: launch_struct<32, 2, 3>(L, v, x, b, y, mode, s); break;
-    case 33: launch_struct<32, 3, 3>(L, v, x, b, y, mode, s); break;
-    default:
-      set_error("structured SpMV: unsupported (dim, k)");
-      return STM_ERR_INVALID_ARG;
-  }
-  note_launch();
-  STM_CUDA(cudaGetLastError());
-  return STM_OK;
 }
 
 }  // namespace stm

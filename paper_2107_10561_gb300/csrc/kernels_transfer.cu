@@ -150,9 +150,9 @@ static TransferGeom geom(const Level& F, const Level& Cl) {
 
 // Lanes per node: fine-node lists hold up to 3^d entries, coarse-node lists up to 5^d. Groups of
 // lanes shorten the chains of dependent loads on the smaller levels; on large levels (at least
-// kManyNodes nodes) one thread per node keeps the stores of consecutive nodes contiguous, which
-// measured faster there.
-constexpr long long kManyNodes = 16384;
+// many_nodes(d) nodes) one thread per node keeps the stores of consecutive nodes contiguous, which
+// measured faster there. The 3D lists are longer, so the groups pay off up to larger levels.
+constexpr long long many_nodes(int d) { return d == 2 ? 16384 : 65536; }
 
 template <int K, int D, int G>
 static void launch_prolong_g(const Level& F, const TransferGeom& g, const double* xc, double* yf, cudaStream_t s) {
@@ -163,7 +163,7 @@ static void launch_prolong_g(const Level& F, const TransferGeom& g, const double
 
 template <int K, int D>
 static void launch_prolong(const Level& F, const TransferGeom& g, const double* xc, double* yf, cudaStream_t s) {
-  if (g.fR >= kManyNodes) launch_prolong_g<K, D, 1>(F, g, xc, yf, s);
+  if (g.fR >= many_nodes(D)) launch_prolong_g<K, D, 1>(F, g, xc, yf, s);
   else launch_prolong_g<K, D, D == 2 ? 4 : 8>(F, g, xc, yf, s);
 }
 
@@ -176,7 +176,7 @@ static void launch_restrict_g(const Level& F, const TransferGeom& g, const doubl
 
 template <int K, int D>
 static void launch_restrict(const Level& F, const TransferGeom& g, const double* tf, double* rc, cudaStream_t s) {
-  if (g.cR >= kManyNodes) launch_restrict_g<K, D, 1>(F, g, tf, rc, s);
+  if (g.cR >= many_nodes(D)) launch_restrict_g<K, D, 1>(F, g, tf, rc, s);
   else launch_restrict_g<K, D, D == 2 ? 8 : 16>(F, g, tf, rc, s);
 }
 

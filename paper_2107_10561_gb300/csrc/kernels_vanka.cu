@@ -236,37 +236,43 @@ __global__ void __launch_bounds__(256, 4) k_vanka_warp(const S* __restrict__ inv
   }
 }
 
-// Transposed local solves y_T = Inv_T^T t_T (adjoint smoother): one warp per column, a dot product
-// of the column with t_T.
-template <typename S>
+// Transposed local solves y_T = Inv_T^T t_T (adjoint smoother). Column j of the stored inverse is
+// contiguous, and (Inv^T t)_j is that column dotted with t_T, so one thread per column streams it
+// with VB-byte vector loads against t_T in shared memory: no cross-thread sums. A cell takes T
+// threads (n rounded up to a warp), a CTA P cells.
+template <typename S, int VB>
 __global__ void __launch_bounds__(256) k_vanka_local_t(const S* __restrict__ inv, const int* __restrict__ idx,
                                                        const double* __restrict__ t, double* __restrict__ Y,
                                                        const int* __restrict__ cell_list, int ncells, int n, int ld,
-                                                       double* __restrict__ d_scatter, double omega) {
+                                                       int T, int P, double* __restrict__ d_scatter, double omega) {
   using A = typename Acc<S>::T;
+  using CV = Conv<S, VB>;
+  constexpr int V = CV::V;
   extern __shared__ double smd[];
-  double* tl = smd;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int ci = blockIdx.x; ci < ncells; ci += gridDim.x) {
-    const int c = cell_list ? cell_list[ci] : ci;
+  A* tl = reinterpret_cast<A*>(smd);  // [P][ld], rows n..ld-1 zero like the stored padding
+  const int slot = threadIdx.x / T, j = threadIdx.x - slot * T;
+  for (int base = blockIdx.x * P; base < ncells; base += gridDim.x * P) {
+    const int ci = base + slot;
+    const bool has = slot < P && ci < ncells;
+    const int c = has ? (cell_list ? cell_list[ci] : ci) : 0;
     const int* ic = idx + (long long)c * n;
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) tl[i] = t[ic[i]];
+    if (has)
+      for (int i = j; i < ld; i += T) tl[slot * ld + i] = i < n ? (A)t[ic[i]] : A(0);
     __syncthreads();
-    const S* M = inv + (size_t)c * n * ld;
-    for (int j = wid; j < n; j += nw) {
-      const S* col = M + (size_t)j * ld;
+    if (has && j < n) {
+      const S* col = inv + (size_t)c * n * ld + (size_t)j * ld;
+      const A* tc = tl + slot * ld;
       A acc = 0;
-      for (int i = lane; i < n; i += 32) {
-        if constexpr (sizeof(S) == 8) acc += __ldg((const double*)(col + i)) * tl[i];
-        else if constexpr (sizeof(S) == 4) acc += __ldg((const float*)(col + i)) * (A)tl[i];
-        else acc += __bfloat162float(col[i]) * (A)tl[i];
+#pragma unroll 8
+      for (int i0 = 0; i0 < ld; i0 += V) {
+        A e[V];
+        CV::run(ld_raw<VB>(col + i0), e);
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc += e[v] * tc[i0 + v];
       }
-      for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-      if (lane == 0) {
-        if (d_scatter) d_scatter[ic[j]] += omega * (double)acc;
-        else Y[(long long)c * n + j] = (double)acc;
-      }
+      if (d_scatter) d_scatter[ic[j]] += omega * (double)acc;
+      else Y[(long long)c * n + j] = (double)acc;
     }
   }
 }
@@ -350,17 +356,41 @@ static stm_status launch_local(Hierarchy& H, Level& L, int level, const double* 
     else if (prec == STM_F32) launch_fwd<float>(L, L.inv, lay.vb, g, t, cells, nc, scatter, omega, s);
     else launch_fwd<__nv_bfloat16>(L, L.inv, lay.vb, g, t, cells, nc, scatter, omega, s);
   } else {
-    const int blocks = std::min(nc, sm_count() * 8);
-    const size_t smem = sizeof(double) * L.n + 16;
-    if (prec == STM_F64)
-      k_vanka_local_t<double><<<blocks, 256, smem, s>>>((const double*)L.inv, L.idx, t, L.Y, cells, nc, L.n, lay.ld,
-                                                        scatter, omega);
-    else if (prec == STM_F32)
-      k_vanka_local_t<float><<<blocks, 256, smem, s>>>((const float*)L.inv, L.idx, t, L.Y, cells, nc, L.n, lay.ld,
-                                                       scatter, omega);
-    else
-      k_vanka_local_t<__nv_bfloat16><<<blocks, 256, smem, s>>>((const __nv_bfloat16*)L.inv, L.idx, t, L.Y, cells, nc,
-                                                               L.n, lay.ld, scatter, omega);
+    const int T = (L.n + 31) / 32 * 32;
+    const int P = std::max(1, 256 / T);
+    const int blocks = std::min((nc + P - 1) / P, sm_count() * 8);
+    if (prec == STM_F64) {
+      const size_t smem = sizeof(double) * (size_t)P * lay.ld + 16;
+      if (lay.vb == 16)
+        k_vanka_local_t<double, 16><<<blocks, T * P, smem, s>>>((const double*)L.inv, L.idx, t, L.Y, cells, nc, L.n,
+                                                                lay.ld, T, P, scatter, omega);
+      else
+        k_vanka_local_t<double, 8><<<blocks, T * P, smem, s>>>((const double*)L.inv, L.idx, t, L.Y, cells, nc, L.n,
+                                                               lay.ld, T, P, scatter, omega);
+    } else if (prec == STM_F32) {
+      const size_t smem = sizeof(float) * (size_t)P * lay.ld + 16;
+      if (lay.vb == 16)
+        k_vanka_local_t<float, 16><<<blocks, T * P, smem, s>>>((const float*)L.inv, L.idx, t, L.Y, cells, nc, L.n,
+                                                               lay.ld, T, P, scatter, omega);
+      else if (lay.vb == 8)
+        k_vanka_local_t<float, 8><<<blocks, T * P, smem, s>>>((const float*)L.inv, L.idx, t, L.Y, cells, nc, L.n,
+                                                              lay.ld, T, P, scatter, omega);
+      else
+        k_vanka_local_t<float, 4><<<blocks, T * P, smem, s>>>((const float*)L.inv, L.idx, t, L.Y, cells, nc, L.n,
+                                                              lay.ld, T, P, scatter, omega);
+    } else {
+      const size_t smem = sizeof(float) * (size_t)P * lay.ld + 16;
+      const __nv_bfloat16* iv = (const __nv_bfloat16*)L.inv;
+      if (lay.vb == 16)
+        k_vanka_local_t<__nv_bfloat16, 16><<<blocks, T * P, smem, s>>>(iv, L.idx, t, L.Y, cells, nc, L.n, lay.ld, T,
+                                                                       P, scatter, omega);
+      else if (lay.vb == 8)
+        k_vanka_local_t<__nv_bfloat16, 8><<<blocks, T * P, smem, s>>>(iv, L.idx, t, L.Y, cells, nc, L.n, lay.ld, T,
+                                                                      P, scatter, omega);
+      else
+        k_vanka_local_t<__nv_bfloat16, 4><<<blocks, T * P, smem, s>>>(iv, L.idx, t, L.Y, cells, nc, L.n, lay.ld, T,
+                                                                      P, scatter, omega);
+    }
   }
   note_launch();
   STM_CUDA(cudaGetLastError());
