@@ -204,6 +204,15 @@ def spmv_roofline(r, wl, sizes, fp64_peak, workload_name):
             "hbm_gbs_algorithmic": f["bytes"] / (f["ms"] * 1e-3) / 1e9}
 
 
+def max_over_ranks(value, dist, device):
+    """Replicas (one independent slab solve per GPU): the job's time per step is the slowest rank's."""
+    import torch
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -282,9 +291,7 @@ def gpu_leg(args, rank, world, local_rank):
         torch.cuda.synchronize()
         ms = ev0.elapsed_time(ev1) / args.steps
         if dist:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+            ms = max_over_ranks(ms, dist, "cuda")
         r = results[prec]
         r["ms_per_solve"] = ms
         r["launches_per_step"] = (Hierarchy.kernel_launches() - launches0) / args.steps
