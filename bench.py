@@ -85,8 +85,9 @@ def oracle_child(spec_path):
         x, info = H.solve(b, rtol=spec["rtol"], maxit=spec["maxit"])
         times.append(time.perf_counter() - t0)
         iters.append(info["iters"])
-    json.dump({"setup_s": setup, "solve_s": times, "iters": iters, "converged": bool(info["converged"])},
-              open(spec["out"], "w"))
+    sizes = {"n_dofs": int(H.fine.N), "n_cells": int(H.fine.C), "n_local": int(H.fine.n)}
+    json.dump({"setup_s": setup, "solve_s": times, "iters": iters, "converged": bool(info["converged"]),
+               "sizes": sizes}, open(spec["out"], "w"))
 
 
 def run_oracle(wl_name, rtol, solves, maxit=1000, threads=1):
@@ -639,9 +640,11 @@ def main():
                 "value": t, "unit": "s", "n_gpus": args.gpus, "steps": samples, "warmup": 0,
                 "ms_per_step": 1e3 * t, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64", "data": "synthetic",
-                "config": {"workload": args.workload, "rtol": args.rtol},
+                "config": dict(describe(wl, [o["sizes"]]), rtol=args.rtol,
+                               parallelism="CPU oracle, one thread (rank 0 of the job)"),
                 "cpu_baseline": {"value": t, "unit": "s", "cores": 1, "kind": "oracle",
-                                 "sample": f"{samples} full FP64 oracle FGMRES solves ({o['iters']} iterations) after "
+                                 "sample": f"{samples} full FP64 oracle FGMRES solve(s) of the same workload ({o['iters'][-1]} "
+                                           f"iterations each, single-threaded numpy/scipy) after "
                                            f"an untimed {o['setup_s']:.1f} s oracle setup"},
                 "e2e": {"value": t, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
