@@ -4,8 +4,9 @@
 Step = one flexible-GMRES solve (V(2,2) additive-Vanka V-cycle per iteration) of the dG(k)
 Q2/P1disc slab Newton system to 1e-8 relative residual, from x = 0, with the hierarchy assembled
 and factored once beforehand (assembly and factorisation times are reported under "setup").
-The headline `value` is seconds per solve with mixed-precision cell inverses (the faster of FP32
-and BF16 storage); the plain FP64 path is timed in the same run ("fp64_s").
+The headline `value` is seconds per solve of the fastest mixed-precision run: FP32 or BF16 cell
+inverses, optionally with FP32 defects inside the V-cycle ("bf16+f32d"); the FGMRES products and
+stopping test are FP64 in every run, and the plain FP64 path is timed in the same run ("fp64_s").
 
 Prints ONE JSON line (rank 0). `--impl reference` times the CPU oracle (the plain FP64 reference
 implementation written from the paper) on the same workload instead.
@@ -35,7 +36,8 @@ def parse():
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--rtol", type=float, default=1e-8)
-    ap.add_argument("--precisions", default="f64,f32,bf16")
+    ap.add_argument("--precisions", default="f64,f32,bf16,bf16+f32d",
+                    help="cell-inverse storage per run; INV+f32d also takes the V-cycle defects in FP32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--multi-restart", type=int, default=20)
     ap.add_argument("--robustness", action="store_true",
@@ -205,6 +207,25 @@ def spmv_roofline(r, wl, sizes, fp64_peak, workload_name):
             "hbm_gbs_algorithmic": f["bytes"] / (f["ms"] * 1e-3) / 1e9}
 
 
+def defect_roofline(r, sizes, hbm, peak_source, workload_name):
+    """The V-cycle's defect r - J_g d over the FP32 copies of J_g, finest level (HBM bound).
+
+    achieved = (4 nnz + 24 N) algorithmic bytes per launch (FP32 values; x, b, y in FP64) / average
+    event time per launch; peak = the measured copy bandwidth."""
+    f = r["finest"]["defect_f32"]
+    if f["ms"] <= 0 or f["launches"] == 0:
+        return None
+    us = 1e3 * f["ms"] / f["launches"]
+    by = f["bytes"] / f["launches"]
+    achieved = by / (us * 1e-6) / 1e9
+    traffic = recorded_traffic(workload_name, "k_spmv_nodeblock_f32")
+    return {"kernel": "k_spmv_nodeblock<float> (r - J_g d over FP32 values, finest level)", "bound": "hbm",
+            "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": traffic["per_launch_bytes"] if traffic else None,
+            "traffic_source": traffic["source"] if traffic else "no capture of the current kernel source",
+            "peak_source": peak_source, "bytes_per_launch": by, "avg_launch_us": us}
+
+
 def max_over_ranks(value, dist, device):
     """Replicas (one independent slab solve per GPU): the job's time per step is the slowest rank's."""
     import torch
@@ -212,6 +233,33 @@ def max_over_ranks(value, dist, device):
     t = torch.tensor([float(value)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def split_precision(tok):
+    """'bf16+f32d' -> ('bf16', 'f32'): cell-inverse storage and V-cycle defect precision."""
+    inv, _, d = tok.partition("+")
+    if inv not in ("f64", "f32", "bf16") or d not in ("", "f32d"):
+        raise ValueError(f"precision {tok!r}: expected f64|f32|bf16, optionally +f32d")
+    return inv, ("f32" if d else "f64")
+
+
+def hier_params(wl, tok, smoother="additive"):
+    from paper_2107_10561_gb300 import make_params
+
+    inv, dp = split_precision(tok)
+    return make_params(wl.dim, wl.k, wl.n_levels, wl.coarse_cells, wl.length, wl.obstacle_lo, wl.obstacle_hi,
+                       wl.tau, wl.nu, wl.gamma1, wl.gamma2, inv, smoother, wl.omega, wl.nu1, wl.nu2,
+                       defect_precision=dp)
+
+
+def dtype_label(tok):
+    inv, dp = split_precision(tok)
+    if inv == "f64" and dp == "f64":
+        return "f64"
+    parts = [f"{inv} cell inverses (f32 accumulate)"] if inv != "f64" else []
+    if dp == "f32":
+        parts.append("f32 V-cycle defects")
+    return "f64 Krylov/Arnoldi SpMV/coarse + " + " + ".join(parts)
 
 
 def peaks():
@@ -245,8 +293,7 @@ def gpu_leg(args, rank, world, local_rank):
     results = {}
     hs = {}
     for prec in args.precisions.split(","):
-        p = make_params(wl.dim, wl.k, wl.n_levels, wl.coarse_cells, wl.length, wl.obstacle_lo, wl.obstacle_hi,
-                        wl.tau, wl.nu, wl.gamma1, wl.gamma2, prec, "additive", wl.omega, wl.nu1, wl.nu2)
+        p = hier_params(wl, prec, "additive")
         h = Hierarchy(p)
         idx = h.dof_lattice_index()
         X = torch.from_numpy(np.ascontiguousarray(state.reshape(-1)[idx])).cuda()
@@ -282,7 +329,7 @@ def gpu_leg(args, rank, world, local_rank):
             dist.barrier()
         torch.cuda.synchronize()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.nvtx.range_push(f"timed_solves_{prec}")  # lets a profiler select exactly these launches
+        torch.cuda.nvtx.range_push(f"timed_solves_{prec.replace('+', '_')}")  # lets a profiler select exactly these launches
         ev0.record(stream)
         for _ in range(args.steps):
             x.zero_()
@@ -310,11 +357,11 @@ def gpu_leg(args, rank, world, local_rank):
         pv1.record(stream)
         torch.cuda.synchronize()
         r["ms_per_solve_profiled"] = pv0.elapsed_time(pv1) / args.steps
-        r["kernels"] = {k: h.profile_read(k) for k in ("vanka_local", "jacobian_spmv", "vanka_combine", "transfer",
+        r["kernels"] = {k: h.profile_read(k) for k in ("vanka_local", "jacobian_spmv", "defect_f32", "vanka_combine", "transfer",
                                                        "coarse", "krylov")}
-        r["finest"] = {k: h.profile_read(k, wl.n_levels - 1) for k in ("vanka_local", "jacobian_spmv")}
+        r["finest"] = {k: h.profile_read(k, wl.n_levels - 1) for k in ("vanka_local", "jacobian_spmv", "defect_f32")}
         r["per_level"] = {k: [h.profile_read(k, g) for g in range(wl.n_levels)]
-                          for k in ("vanka_local", "jacobian_spmv", "vanka_combine", "transfer")}
+                          for k in ("vanka_local", "jacobian_spmv", "defect_f32", "vanka_combine", "transfer")}
         h.profile_enable(False)
     clocks = sampler.stop()
     fp64_peak = Hierarchy.measure_fp64_peak()
@@ -370,8 +417,7 @@ def other_rows(args, wl, hs, head, state, rhs_lat):
     out["adjoint_solve"] = {"ms": ev0.elapsed_time(ev1) / args.steps, "iters": info["iters"],
                             "rel_res_true": info["rel_res_true"]}
     for smoother in ("coloured", "overwrite"):
-        p = make_params(wl.dim, wl.k, wl.n_levels, wl.coarse_cells, wl.length, wl.obstacle_lo, wl.obstacle_hi,
-                        wl.tau, wl.nu, wl.gamma1, wl.gamma2, head, smoother, wl.omega, wl.nu1, wl.nu2)
+        p = hier_params(wl, head, smoother)
         hv = Hierarchy(p)
         idx = hv.dof_lattice_index()
         X = torch.from_numpy(np.ascontiguousarray(state.reshape(-1)[idx])).cuda()
@@ -407,8 +453,7 @@ def gpu_leg_multi(args, local_rank):
     wl = workload(args.workload)
     nrhs = wl.extra["nrhs"]
     prec = args.precisions.split(",")[-1]
-    p = make_params(wl.dim, wl.k, wl.n_levels, wl.coarse_cells, wl.length, wl.obstacle_lo, wl.obstacle_hi,
-                    wl.tau, wl.nu, wl.gamma1, wl.gamma2, prec, "additive", wl.omega, wl.nu1, wl.nu2)
+    p = hier_params(wl, prec, "additive")
     t0 = time.perf_counter()
     h = Hierarchy(p)
     build_s = time.perf_counter() - t0
@@ -458,7 +503,7 @@ def gpu_leg_multi(args, local_rank):
     line = {"metric": "GMG-GMRES s to 1e-8 rel. res (mixed vs FP64, one GB300); Vanka sweep GB/s",
             "value": ms / 1e3, "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": f"f64 Krylov/SpMM/coarse + {prec} cell inverses ({'tensor cores, ' if prec == 'bf16' else ''}f32 accumulate)",
+            "dtype": f"f64 Krylov/SpMM/coarse + {split_precision(prec)[0]} cell inverses ({'tensor cores, ' if split_precision(prec)[0] == 'bf16' else ''}f32 accumulate); FP64 defects",
             "data": "synthetic", "config": cfg, "per_rhs_s": ms / 1e3 / nrhs,
             "iters": [i["iters"] for i in infos], "max_rel_res_true": max(i["rel_res_true"] for i in infos),
             "setup": {"build_hierarchy_s": build_s, "assemble_ms": e0.elapsed_time(e1), "factor_ms": e1.elapsed_time(e2)},
@@ -488,8 +533,7 @@ def gpu_leg_newton(args, local_rank):
     wl = workload(args.workload)
     out = {}
     for prec in args.precisions.split(","):
-        p = make_params(wl.dim, wl.k, wl.n_levels, wl.coarse_cells, wl.length, wl.obstacle_lo, wl.obstacle_hi,
-                        wl.tau, wl.nu, wl.gamma1, wl.gamma2, prec, "additive", wl.omega, wl.nu1, wl.nu2)
+        p = hier_params(wl, prec, "additive")
         h = Hierarchy(p)
         idx = h.dof_lattice_index()
         X0 = torch.from_numpy(np.ascontiguousarray(synth.linearisation_point(wl).reshape(-1)[idx])).cuda()
@@ -516,7 +560,7 @@ def gpu_leg_newton(args, local_rank):
     line = {"metric": "damped-Newton slab solve s (GMG-FGMRES inner solves)", "value": r["ms"] / 1e3, "unit": "s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"],
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": f"f64 + {head} cell inverses" if head != "f64" else "f64", "data": "synthetic", "config": cfg,
+            "dtype": dtype_label(head), "data": "synthetic", "config": cfg,
             "by_precision": {p: {"s": v["ms"] / 1e3, "newton_iters": v["info"]["newton_iters"],
                                  "gmres_iters": v["info"]["gmres_iters"], "res": v["info"]["res"],
                                  "lam": v["info"]["lam"]} for p, v in out.items()},
@@ -539,8 +583,7 @@ def gpu_leg_march(args, local_rank):
     _build.build()
     wl = workload(args.workload)
     prec = args.precisions.split(",")[-1]
-    p = make_params(wl.dim, wl.k, wl.n_levels, wl.coarse_cells, wl.length, wl.obstacle_lo, wl.obstacle_hi,
-                    wl.tau, wl.nu, wl.gamma1, wl.gamma2, prec, "additive", wl.omega, wl.nu1, wl.nu2)
+    p = hier_params(wl, prec, "additive")
     h = Hierarchy(p)
     idx = h.dof_lattice_index()
     X0 = torch.from_numpy(np.ascontiguousarray(synth.linearisation_point(wl).reshape(-1)[idx])).cuda()
@@ -563,7 +606,7 @@ def gpu_leg_march(args, local_rank):
     line = {"metric": "time-marching s per slab (damped Newton, GMG-FGMRES inner solves)",
             "value": ms / 1e3 / args.march, "unit": "s", "n_gpus": 1, "steps": args.march, "warmup": 1,
             "ms_per_step": ms / args.march, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": f"f64 + {prec} cell inverses" if prec != "f64" else "f64", "data": "synthetic",
+            "dtype": dtype_label(prec), "data": "synthetic",
             "config": {"workload": f"{wl.name}: {args.march} slabs of tau = {wl.tau} from the seeded state, "
                                    f"U = {wl.inflow_u}", "wake": {"lo": lo, "hi": hi}, "linear_rtol": args.rtol,
                        "parallelism": "single GPU"},
@@ -595,8 +638,7 @@ def gpu_leg_robustness(args, local_rank):
     for nu in (1e-3, 5e-4, 3e-4, 2e-4, 1e-4):
         for omega in (1.0, 0.7):
             wl = dataclasses.replace(base, nu=nu, omega=omega, nu1=4, nu2=4, tau=0.005)
-            p = make_params(wl.dim, wl.k, wl.n_levels, wl.coarse_cells, wl.length, wl.obstacle_lo, wl.obstacle_hi,
-                            wl.tau, wl.nu, wl.gamma1, wl.gamma2, prec, "additive", wl.omega, wl.nu1, wl.nu2)
+            p = hier_params(wl, prec, "additive")
             h = Hierarchy(p)
             idx = h.dof_lattice_index()
             X = torch.from_numpy(np.ascontiguousarray(synth.linearisation_point(wl).reshape(-1)[idx])).cuda()
@@ -613,7 +655,7 @@ def gpu_leg_robustness(args, local_rank):
             h.close()
     line = {"metric": "Newton steps and FGMRES iterations per Newton step vs nu and omega_d (Table 5.4 setting)",
             "value": time.perf_counter() - t_all, "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 0,
-            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": f"f64 + {prec} inverses",
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": dtype_label(prec),
             "data": "synthetic",
             "config": {"workload": f"{base.name}, tau 0.005, V(4,4), additive Vanka, inner rtol {args.rtol}, "
                                    "FGMRES(30) capped at 1000 iterations", "parallelism": "single GPU"},
@@ -677,19 +719,19 @@ def main():
     vl = r["finest"]["vanka_local"]
     achieved = vl["bytes"] / (vl["ms"] * 1e-3) / 1e9 if vl["ms"] > 0 else None
     vk = "k_vanka_warp" if sizes[-1]["n_local"] <= 64 else "k_vanka_local"
-    traffic = recorded_traffic(args.workload, vk, head)
+    traffic = recorded_traffic(args.workload, vk, split_precision(head)[0])
     cfg = describe(wl, sizes)
     cfg["rtol"] = args.rtol
     inv_bytes = {"f64": 8, "f32": 4, "bf16": 2}
     l2_note = (f"inputs larger than L2: finest J {sizes[-1]['nnz'] * 12 / 1e6:.0f} MB, finest inverses "
-               f"{sizes[-1]['n_cells'] * sizes[-1]['n_local'] ** 2 * inv_bytes[head] / 1e6:.0f} MB ({head})")
+               f"{sizes[-1]['n_cells'] * sizes[-1]['n_local'] ** 2 * inv_bytes[split_precision(head)[0]] / 1e6:.0f} MB ({head})")
     cfg["l2"] = l2_note
     cfg["parallelism"] = f"replicas x{world}" if world > 1 else "single GPU"
     line = {
         "metric": "GMG-GMRES s to 1e-8 rel. res (mixed vs FP64, one GB300); Vanka sweep GB/s",
         "value": r["ms_per_solve"] / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": r["ms_per_solve"], "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": f"f64 Krylov/SpMV/coarse + {head} cell inverses (f32 accumulate)" if head != "f64" else "f64",
+        "dtype": dtype_label(head),
         "data": "synthetic", "config": cfg,
         "fp64_s": results["f64"]["ms_per_solve"] / 1e3 if "f64" in results else None,
         "speedup_vs_fp64": (results["f64"]["ms_per_solve"] / r["ms_per_solve"]) if "f64" in results else None,
@@ -705,6 +747,10 @@ def main():
                              if v["finest"]["jacobian_spmv"]["ms"] > 0 else None,
                              "finest_vanka_us": 1e3 * v["finest"]["vanka_local"]["ms"] / max(v["finest"]["vanka_local"]["launches"], 1),
                              "finest_spmv_us": 1e3 * v["finest"]["jacobian_spmv"]["ms"] / max(v["finest"]["jacobian_spmv"]["launches"], 1),
+                             "finest_defect_f32_us": (1e3 * v["finest"]["defect_f32"]["ms"] / v["finest"]["defect_f32"]["launches"])
+                             if v["finest"]["defect_f32"]["launches"] else None,
+                             "finest_defect_f32_gbs": (v["finest"]["defect_f32"]["bytes"] / (v["finest"]["defect_f32"]["ms"] * 1e-3) / 1e9)
+                             if v["finest"]["defect_f32"]["ms"] > 0 else None,
                              "kernel_ms_per_solve": {k: kv["ms"] / args.steps for k, kv in v["kernels"].items()},
                              "us_per_launch_by_level": {k: [round(1e3 * e["ms"] / e["launches"], 2) if e["launches"] else None
                                                             for e in lv] for k, lv in v["per_level"].items()},
@@ -712,7 +758,10 @@ def main():
                          for p, v in results.items()},
         "gpu_launches": int(r["launches_per_step"] * args.steps),
         "other_rows": rows,
-        "roofline": spmv_roofline(r, wl, sizes, fp64_peak, args.workload),
+        "roofline": None,
+        "roofline_spmv_f64": spmv_roofline(r, wl, sizes, fp64_peak, args.workload),
+        "roofline_defect_f32": defect_roofline(r, sizes, hbm, "MEASURED_PEAKS.json hbm_gbs (of measured)" if pk
+                                               else "fallback 6800 GB/s", args.workload),
         "roofline_vanka_sweep": {"kernel": f"{vk} (y_T = J_T^{{-1}} t_T), finest level, {head} inverses",
                                  "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                                  "frac": (achieved / hbm) if achieved else None,
@@ -729,6 +778,13 @@ def main():
                 "d2h_bytes_per_step": sizes[-1]["n_dofs"] * 8,
                 "path": f"stm_gmres_solve_host ({head}), pinned host b and x"},
     }
+    # the dominant kernel: the finest-level class with the most event time per solve
+    shares = {"roofline_vanka_sweep": r["finest"]["vanka_local"]["ms"],
+              "roofline_spmv_f64": r["finest"]["jacobian_spmv"]["ms"],
+              "roofline_defect_f32": r["finest"]["defect_f32"]["ms"]}
+    dom = max((k for k in shares if line[k]), key=lambda k: shares[k])
+    line["roofline"] = dict(line[dom], dominant_of={k: round(v / args.steps, 3) for k, v in shares.items()},
+                            dominant_of_unit="ms per solve, finest level, profiled pass")
     if not args.no_cpu_baseline and world == 1:
         try:
             o = run_oracle(args.workload, args.rtol, 1)

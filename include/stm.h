@@ -73,6 +73,14 @@ typedef struct {
   int smoother;          /* stm_smoother                                                  */
   double omega;          /* damping omega_d of the local update (Sec. 5.3)                */
   int nu1, nu2;          /* pre-/post-smoothing steps of the V-cycle                      */
+  int defect_precision;  /* stm_precision of the V-cycle's defects r - J_g d (smoothing steps
+                            and the defect before restriction): STM_F64, or STM_F32 = FP32 copies
+                            of J_g's values (kept in step with every assembly), FP32 products
+                            and sums, FP64 vectors. STM_BF16 is rejected. The FGMRES products
+                            and true residuals are FP64 in every case; flexible GMRES (Sec. 3)
+                            keeps each preconditioned vector, so an inexact V-cycle only changes
+                            the iteration count. The multi-RHS V-cycle keeps FP64 defects.
+                            Zero-initialised structs get STM_F64.                              */
 } stm_params;
 
 /* Host setup of all levels (numbering, cell->DoF maps, colours, multiplicities, CSR patterns of
@@ -107,6 +115,14 @@ stm_status stm_factor_cells(stm_hierarchy* h, void* stream, int* bad_level, long
 /* y = J_g x (transpose = 0) or y = J_g^T x (transpose = 1); x, y: n_dofs of `level`. */
 stm_status stm_spmv(stm_hierarchy* h, int level, const double* x_dev, double* y_dev, int transpose,
                     void* stream);
+
+/* The V-cycle's defect t = r - J_g d (transpose = 1: r - J_g^T d) on `level`, computed as inside
+ * Algorithm 1 (before each smoothing step with d != 0 and before the restriction): in FP64, or
+ * with params.defect_precision = STM_F32 over FP32 copies of J_g's values (d rounded to FP32 to
+ * nearest, FP32 products and sums, r and t in FP64). r, d, t: n_dofs of `level`, device; t must not
+ * alias r or d. STM_ERR_STATE before stm_assemble_jacobian. */
+stm_status stm_defect(stm_hierarchy* h, int level, const double* r_dev, const double* d_dev, double* t_dev,
+                      int transpose, void* stream);
 
 /* One smoothing step d <- S(d, r) on level g >= 1 with params.smoother and params.omega
  * (Eq. LocVanka with damping; residual r - J_g d recomputed inside). transpose = 1 smooths for
@@ -274,21 +290,25 @@ stm_status stm_vanka_apply_noalloc(long long n_cells, int n_local, long long n_d
  *   JACOBIAN_SPMV residual / product with J_g: 8 nnz + 24 N bytes (values, x, y, b; column
  *                 indices are representation overhead and not counted);
  *   VANKA_COMBINE second pass of the additive/overwrite smoother; TRANSFER P and P^T products;
- *   COARSE        dense coarse solve; KRYLOV Gram-Schmidt, norms and updates of FGMRES. */
+ *   COARSE        dense coarse solve; KRYLOV Gram-Schmidt, norms and updates of FGMRES;
+ *   DEFECT_F32    the V-cycle's defect r - J_g d over the FP32 copies (defect_precision =
+ *                 STM_F32): 4 nnz + 24 N bytes. */
 typedef enum {
   STM_KCLASS_VANKA_LOCAL = 0,
   STM_KCLASS_JACOBIAN_SPMV = 1,
   STM_KCLASS_VANKA_COMBINE = 2,
   STM_KCLASS_TRANSFER = 3,
   STM_KCLASS_COARSE = 4,
-  STM_KCLASS_KRYLOV = 5
+  STM_KCLASS_KRYLOV = 5,
+  STM_KCLASS_DEFECT_F32 = 6
 } stm_kernel_class;
 
 /* Turn event timing of kernel launches on (1) or off (0); turning it on clears the records. */
 stm_status stm_profile_enable(stm_hierarchy* h, int enable);
 /* Synchronises the device and returns, for one kernel class on one level (-1: all levels), the
  * summed event time (ms), the number of timed launches and the summed algorithmic bytes since
- * profiling was enabled. Per-level figures exist for VANKA_LOCAL, VANKA_COMBINE, JACOBIAN_SPMV. */
+ * profiling was enabled. Per-level figures exist for VANKA_LOCAL, VANKA_COMBINE, JACOBIAN_SPMV,
+ * DEFECT_F32. */
 stm_status stm_profile_read(stm_hierarchy* h, int kernel_class, int level, double* total_ms, long long* launches,
                             double* bytes);
 /* Measured FP64 FMA throughput of the current device in TFLOP/s (8 independent FMA chains per thread,

@@ -13,7 +13,7 @@ STATUS_NAMES = {0: "STM_OK", 1: "STM_ERR_INVALID_ARG", 2: "STM_ERR_CUDA", 3: "ST
                 7: "STM_ERR_STATE"}
 PRECISION = {"f64": 0, "f32": 1, "bf16": 2}
 SMOOTHER = {"additive": 0, "coloured": 1, "overwrite": 2}
-KCLASS = {"vanka_local": 0, "jacobian_spmv": 1, "vanka_combine": 2, "transfer": 3, "coarse": 4, "krylov": 5}
+KCLASS = {"vanka_local": 0, "jacobian_spmv": 1, "vanka_combine": 2, "transfer": 3, "coarse": 4, "krylov": 5, "defect_f32": 6}
 
 
 class StmParams(C.Structure):
@@ -21,7 +21,7 @@ class StmParams(C.Structure):
                 ("length", C.c_double * 3), ("obstacle_lo", C.c_int * 3), ("obstacle_hi", C.c_int * 3),
                 ("tau", C.c_double), ("nu", C.c_double), ("gamma1", C.c_double), ("gamma2", C.c_double),
                 ("inv_precision", C.c_int), ("smoother", C.c_int), ("omega", C.c_double),
-                ("nu1", C.c_int), ("nu2", C.c_int)]
+                ("nu1", C.c_int), ("nu2", C.c_int), ("defect_precision", C.c_int)]
 
 
 class GmresOpts(C.Structure):
@@ -60,6 +60,7 @@ SIGNATURES = {
     "stm_assemble_jacobian": ([_P, _P, _D, _P], _I),
     "stm_factor_cells": ([_P, _P, _IP, _LP], _I),
     "stm_spmv": ([_P, _I, _P, _P, _I, _P], _I),
+    "stm_defect": ([_P, _I, _P, _P, _P, _I, _P], _I),
     "stm_vanka_sweep": ([_P, _I, _P, _P, _I, _P], _I),
     "stm_restrict": ([_P, _I, _P, _P, _P], _I),
     "stm_prolongate_add": ([_P, _I, _P, _P, _P], _I),

@@ -42,6 +42,7 @@ stm_status stm_build_hierarchy(const stm_params* params, stm_hierarchy** out) {
       return bad_arg("obstacle range outside the coarse grid");
   }
   if (p.inv_precision < STM_F64 || p.inv_precision > STM_BF16) return bad_arg("inv_precision");
+  if (p.defect_precision != STM_F64 && p.defect_precision != STM_F32) return bad_arg("defect_precision must be F64 or F32");
   if (p.smoother < STM_VANKA_ADDITIVE || p.smoother > STM_VANKA_PAPER_OVERWRITE) return bad_arg("smoother");
   if (!(p.tau > 0.0) || !(p.nu >= 0.0) || p.nu1 < 0 || p.nu2 < 0) return bad_arg("tau, nu, nu1, nu2");
   stm_hierarchy* h = new (std::nothrow) stm_hierarchy();
@@ -158,6 +159,18 @@ stm_status stm_spmv(stm_hierarchy* h, int level, const double* x, double* y, int
     return STM_ERR_STATE;
   }
   return jacobian_apply(h->H, level, x, nullptr, y, 0, transpose, S(stream));
+}
+
+stm_status stm_defect(stm_hierarchy* h, int level, const double* r, const double* d, double* t, int transpose,
+                      void* stream) {
+  if (!h || !r || !d || !t) return bad_arg("NULL argument");
+  if (t == r || t == d) return bad_arg("t must not alias r or d");
+  STM_TRY(need_level(h->H, level, 0));
+  if (!h->H.assembled) {
+    set_error("defect before assemble_jacobian");
+    return STM_ERR_STATE;
+  }
+  return smoother_defect(h->H, level, d, r, t, transpose, S(stream));
 }
 
 stm_status stm_vanka_sweep(stm_hierarchy* h, int level, const double* r, double* d, int transpose, void* stream) {

@@ -14,7 +14,7 @@
 #include "stm.h"
 
 namespace stm {
-constexpr int STM_KCLASS_COUNT = 6;
+constexpr int STM_KCLASS_COUNT = 7;
 
 constexpr int kMaxDim = 3;
 constexpr int kCoarseTChunk = 512;  // rows per partial sum of the transposed coarse solve
@@ -113,6 +113,9 @@ struct Level {
   // t = m*nv + j of row pr at pvalT[((pr/32)*d*nv + t)*32 + pr%32] (rows padded to a multiple of 32)
   double* pvalT = nullptr;
   double *nvalJT = nullptr, *pvalJT = nullptr;  // the same two copies for J^T (built with valT)
+  // FP32 copies of nval/pvalT (and of nvalJT/pvalJT) in the same layout, for the V-cycle's defects
+  // r - J_g d with defect_precision = STM_F32; null otherwise
+  float *nval32 = nullptr, *pval32 = nullptr, *nvalJT32 = nullptr, *pvalJT32 = nullptr;
   long long nval_len = 0, pval_len = 0;          // entries of nval and pvalT
   int* ncell = nullptr;           // [R] number of cells containing the node
   long long* rowptr = nullptr;    // [N+1]
@@ -234,8 +237,17 @@ stm_status spmv_nodeblock(const Level& L, const double* nval, const double* pval
 stm_status build_nodeblock(Level& L, cudaStream_t s);
 // node-block and warp-transposed pressure-row copies of any value array on J's pattern (J or J^T)
 stm_status build_nodeblock_from(const Level& L, const double* val, double* nval, double* pvalT, cudaStream_t s);
+// the same product over FP32 copies of the values: FP32 products and sums, FP64 x, b and y
+stm_status spmv_nodeblock(const Level& L, const float* nval, const float* pvalT, const double* x, const double* b,
+                          double* y, int mode, cudaStream_t s);
+// FP32 copies of J_g's (or J_g^T's) node-block arrays (allocated on first use, same layout)
+stm_status build_values_f32(Level& L, int transpose, cudaStream_t s);
 stm_status jacobian_apply(Hierarchy& H, int g, const double* x, const double* b, double* y,
                           int mode, int transpose, cudaStream_t s);
+// the V-cycle's defect y = b - J_g x (or J_g^T): over the FP32 copies with defect_precision =
+// STM_F32, else jacobian_apply in FP64
+stm_status smoother_defect(Hierarchy& H, int g, const double* x, const double* b, double* y, int transpose,
+                           cudaStream_t s);
 stm_status vanka_step(Hierarchy& H, int g, const double* r, double* d, int transpose,
                       bool d_is_zero, cudaStream_t s);
 stm_status coarse_apply(Hierarchy& H, const double* r, double* d, int transpose, cudaStream_t s);

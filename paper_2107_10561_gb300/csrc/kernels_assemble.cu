@@ -258,7 +258,10 @@ stm_status assemble_level(Hierarchy& H, int g, double nu, cudaStream_t s) {
     cudaFree(L.pvalJT);
     L.pvalJT = nullptr;
   }
-  return build_nodeblock(L, s);
+  STM_TRY(build_nodeblock(L, s));
+  // FP32 defect copies follow the new values (J^T's are rebuilt with J^T)
+  if (H.p.defect_precision == STM_F32) STM_TRY(build_values_f32(L, 0, s));
+  return STM_OK;
 }
 
 }  // namespace stm

@@ -121,7 +121,9 @@ stm_status ensure_transpose(Hierarchy& H, int g, cudaStream_t s) {
   STM_CUDA(cudaMalloc(&L.nvalJT, sizeof(double) * L.nval_len));
   STM_CUDA(cudaMalloc(&L.pvalJT, sizeof(double) * L.pval_len));
   STM_CUDA(cudaMemsetAsync(L.pvalJT, 0, sizeof(double) * L.pval_len, s));
-  return build_nodeblock_from(L, L.valT, L.nvalJT, L.pvalJT, s);
+  STM_TRY(build_nodeblock_from(L, L.valT, L.nvalJT, L.pvalJT, s));
+  if (H.p.defect_precision == STM_F32) STM_TRY(build_values_f32(L, 1, s));
+  return STM_OK;
 }
 
 stm_status jacobian_apply(Hierarchy& H, int g, const double* x, const double* b, double* y, int mode,
@@ -131,6 +133,26 @@ stm_status jacobian_apply(Hierarchy& H, int g, const double* x, const double* b,
   ProfScope ps(&H, STM_KCLASS_JACOBIAN_SPMV, s, 8.0 * (double)L.nnz + 24.0 * (double)L.N, g);
   if (!transpose) return spmv_nodeblock(L, L.nval, L.pvalT, x, b, y, mode, s);
   return spmv_nodeblock(L, L.nvalJT, L.pvalJT, x, b, y, mode, s);
+}
+
+// The outer solver is flexible GMRES (Sec. 3): it keeps every preconditioned vector z_j = V(v_j), so
+// the V-cycle need not be an exact fixed linear map. With defect_precision = STM_F32 the V-cycle's
+// defects run over FP32 copies of J_g: half the bytes and no FP64 arithmetic, with rounding (about
+// 1e-7 of |J_g||d|) below that of FP32 or BF16 cell inverses. The Arnoldi products and the true
+// residual stay FP64.
+stm_status smoother_defect(Hierarchy& H, int g, const double* x, const double* b, double* y, int transpose,
+                           cudaStream_t s) {
+  if (H.p.defect_precision != STM_F32) return jacobian_apply(H, g, x, b, y, 1, transpose, s);
+  Level& L = H.L[g];
+  if (transpose) STM_TRY(ensure_transpose(H, g, s));
+  const float* nv = transpose ? L.nvalJT32 : L.nval32;
+  const float* pv = transpose ? L.pvalJT32 : L.pval32;
+  if (!nv || !pv) {
+    set_error("FP32 defect copies missing: assemble the Jacobian first");
+    return STM_ERR_STATE;
+  }
+  ProfScope ps(&H, STM_KCLASS_DEFECT_F32, s, 4.0 * (double)L.nnz + 24.0 * (double)L.N, g);
+  return spmv_nodeblock(L, nv, pv, x, b, y, 1, s);
 }
 
 // Dense coarse solve: d = Cinv r (row-major) or d = Cinv^T r.
@@ -198,7 +220,7 @@ stm_status vcycle(Hierarchy& H, const double* r_fine, double* d_fine, int transp
       if (st != STM_OK) return st;
     }
     // t = r - J d, restrict to the next coarser level
-    stm_status st = (nu1 > 0) ? jacobian_apply(H, g, d, r, L.t, 1, transpose, s) : vec_copy(L.t, r, L.N, s);
+    stm_status st = (nu1 > 0) ? smoother_defect(H, g, d, r, L.t, transpose, s) : vec_copy(L.t, r, L.N, s);
     if (st != STM_OK) return st;
     Level& Lc = H.L[g - 1];
     {

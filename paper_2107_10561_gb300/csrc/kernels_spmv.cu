@@ -1,5 +1,6 @@
-// Structured product with the slab Jacobian J_g or its transpose (FP64): y = J x, y = b - J x or
-// y += J x.
+// Structured product with the slab Jacobian J_g or its transpose: y = J x, y = b - J x or y += J x,
+// in FP64, or over FP32 copies of the values for the V-cycle's defects (FP32 products and sums, x
+// rounded to FP32 on load, b and y in FP64).
 //
 // Every velocity row (a, l, i) of J couples node i with the same neighbour list nbr(i) in every
 // (time b, component m) block, plus the pressures of the cells around i at time a (Problem 3.1,
@@ -13,8 +14,9 @@
 //     sums through a reduce-scatter butterfly (few FP64 adds); nodes are ordered by neighbour
 //     count so that the groups of one warp run equal trip counts;
 //   - warp-transposed pressure rows: one lane per row, entry t of 32 consecutive rows contiguous.
-// Column indices are never read. FP64 issue slots are the limit (one FP64 warp instruction every
-// 16 cycles per SM). Results equal the plain CSR product up to FP64 summation order.
+// Column indices are never read. In FP64, issue slots of the FP64 pipe are the limit (one FP64 warp
+// instruction every 16 cycles per SM); results equal the plain CSR product up to FP64 summation
+// order. In FP32 the arithmetic is cheap and the loads in flight per SM set the pace.
 #include "internal.h"
 
 namespace stm {
@@ -25,8 +27,8 @@ __host__ __device__ constexpr int pow2ceil(int v) { return v <= 1 ? 1 : 2 * pow2
 // acc[0] of lane L holds the full group sum of accumulator scatter_index(L). Each halving step
 // trades half of the accumulators with the partner lane, so the FP64 adds total NA - 1 + the
 // remaining log2(VL/NA) steps instead of NA * log2(VL).
-template <int VL, int NA>
-__device__ __forceinline__ void reduce_scatter(double* acc, int lane) {
+template <int VL, int NA, typename T>
+__device__ __forceinline__ void reduce_scatter(T* acc, int lane) {
   static_assert(NA <= VL, "one accumulator per lane at most");
   int cnt = NA;
 #pragma unroll
@@ -37,8 +39,8 @@ __device__ __forceinline__ void reduce_scatter(double* acc, int lane) {
 #pragma unroll
       for (int k = 0; k < NA / 2; ++k) {
         if (k < half) {
-          const double send = upper ? acc[k] : acc[k + half];
-          const double keep = upper ? acc[k + half] : acc[k];
+          const T send = upper ? acc[k] : acc[k + half];
+          const T keep = upper ? acc[k + half] : acc[k];
           acc[k] = keep + __shfl_xor_sync(0xffffffffu, send, off, VL);
         }
       }
@@ -131,13 +133,44 @@ stm_status build_nodeblock_from(const Level& L, const double* val, double* nval,
   return STM_OK;
 }
 
+// x is FP64 in both products; the FP32 one rounds it to nearest (hardware conversion)
+template <typename TV>
+__device__ __forceinline__ TV from_f64(double v);
+template <>
+__device__ __forceinline__ double from_f64<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ float from_f64<float>(double v) { return __double2float_rn(v); }
+
+// Loads the K*d values of one node-block position (FP64: one by one; FP32 with K*d even: as float2,
+// the position starts on an 8-byte boundary since every node block holds a multiple of K*d values).
+template <int KD>
+__device__ __forceinline__ void load_position(const double* v, double* out) {
+#pragma unroll
+  for (int r = 0; r < KD; ++r) out[r] = __ldcs(v + r);
+}
+template <int KD>
+__device__ __forceinline__ void load_position(const float* v, float* out) {
+  if constexpr (KD % 2 == 0) {
+#pragma unroll
+    for (int r = 0; r < KD; r += 2) {
+      const float2 w = __ldcs(reinterpret_cast<const float2*>(v + r));
+      out[r] = w.x;
+      out[r + 1] = w.y;
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < KD; ++r) out[r] = __ldcs(v + r);
+  }
+}
+
 // VL lanes per node walk the node's positions; each position's K*d row values are contiguous, so VL
-// consecutive positions are one contiguous run of VL*K*d doubles (whole lines even for VL = 4) and
+// consecutive positions are one contiguous run of VL*K*d values (whole lines even for VL = 4) and
 // all lanes stay busy; the K*d partial sums go through the reduce-scatter butterfly (few adds).
-template <int VL, int K, int D>
-__global__ void __launch_bounds__(256, (K == 3 ? 3 : 4)) k_spmv_nodeblock(
-    const long long* __restrict__ rowptr, const double* __restrict__ val, const double* __restrict__ nval,
-    const double* __restrict__ pvalT,
+// TV is the value and arithmetic type: double (the FP64 product), or float (FP32 copies of the
+// values, FP32 products and sums; x and b are read in FP64 and y is written in FP64).
+template <typename TV, int VL, int K, int D>
+__global__ void __launch_bounds__(256, ((sizeof(TV) == 4 && VL > 8) || K < 3) ? 4 : 3) k_spmv_nodeblock(
+    const TV* __restrict__ nval, const TV* __restrict__ pvalT,
     const long long* __restrict__ nbase, const int* __restrict__ nbr_ptr, const int* __restrict__ nbr,
     const int* __restrict__ ncell, const int* __restrict__ node_cells, const int* __restrict__ cell_nodes,
     const int* __restrict__ job_nodes, long long block, int R, int C, int nv, const double* __restrict__ x,
@@ -165,31 +198,74 @@ __global__ void __launch_bounds__(256, (K == 3 ? 3 : 4)) k_spmv_nodeblock(
     const long long job = wb + gw;
     const bool ok = job < R;
     const int i = ok ? job_nodes[job] : 0;
-    double acc[NAV];
+    TV acc[NAV];
 #pragma unroll
-    for (int r = 0; r < NAV; ++r) acc[r] = 0.0;
+    for (int r = 0; r < NAV; ++r) acc[r] = TV(0);
     if (ok) {
       const int p0 = nbr_ptr[i], nn = nbr_ptr[i + 1] - p0, nc = ncell[i];
-      const double* blk = nval + nbase[i];
+      const TV* blk = nval + nbase[i];
       const int npv = KD * nn;
       int j = lane, bm = 0;
       while (j >= nn) { j -= nn; ++bm; }
-      for (int p = lane; p < npv; p += VL) {
-        const int bb = bm / D, m = bm - bb * D;
-        const double xv = __ldg(x + bb * block + (long long)m * R + nbr[p0 + j]);
-        const double* v = blk + (long long)p * KD;
+      if constexpr (sizeof(TV) == 8) {
+        for (int p = lane; p < npv; p += VL) {
+          const int bb = bm / D, m = bm - bb * D;
+          const TV xv = __ldg(x + bb * block + (long long)m * R + nbr[p0 + j]);
+          TV vv[KD];
+          load_position<KD>(blk + (long long)p * KD, vv);
 #pragma unroll
-        for (int r = 0; r < KD; ++r) acc[r] += __ldcs(v + r) * xv;
-        j += VL;
-        while (j >= nn) { j -= nn; ++bm; }
+          for (int r = 0; r < KD; ++r) acc[r] += vv[r] * xv;
+          j += VL;
+          while (j >= nn) { j -= nn; ++bm; }
+        }
+      } else {
+        // FP32 values: half the bytes per position, so U positions per step keep U position loads
+        // in flight per lane before the first FMA waits; positions past the end read nothing.
+        // U = 3 on the large-level classes (80 registers); U = 2 keeps 64 registers and more warps
+        // for the 16- and 32-lane classes of smaller levels (measured per level)
+        constexpr int U = VL <= 8 ? 3 : 2;
+        int jk[U], bk[U];
+        jk[0] = j;
+        bk[0] = bm;
+#pragma unroll
+        for (int k = 1; k < U; ++k) {
+          jk[k] = jk[k - 1] + VL;
+          bk[k] = bk[k - 1];
+          while (jk[k] >= nn) { jk[k] -= nn; ++bk[k]; }
+        }
+        for (int p = lane; p < npv; p += U * VL) {
+          TV v[U][KD], xk[U];
+#pragma unroll
+          for (int k = 0; k < U; ++k) {
+#pragma unroll
+            for (int r = 0; r < KD; ++r) v[k][r] = TV(0);
+            xk[k] = TV(0);
+            if (k == 0 || p + k * VL < npv) load_position<KD>(blk + (long long)(p + k * VL) * KD, v[k]);
+          }
+#pragma unroll
+          for (int k = 0; k < U; ++k)
+            if (k == 0 || p + k * VL < npv) {
+              const int bb = bk[k] / D, m = bk[k] - bb * D;
+              xk[k] = from_f64<TV>(__ldg(x + bb * block + (long long)m * R + nbr[p0 + jk[k]]));
+            }
+#pragma unroll
+          for (int k = 0; k < U; ++k)
+#pragma unroll
+            for (int r = 0; r < KD; ++r) acc[r] += v[k][r] * xk[k];
+#pragma unroll
+          for (int k = 0; k < U; ++k) {
+            jk[k] += U * VL;
+            while (jk[k] >= nn) { jk[k] -= nn; ++bk[k]; }
+          }
+        }
       }
       for (int tq = lane; tq < NP * nc; tq += VL) {
         const int ci = tq / NP, q = tq - ci * NP;
         const long long pc = (long long)D * R + (long long)node_cells[(long long)i * MAXC + ci] * NP + q;
-        const double* v = blk + (long long)(npv + tq) * KD;
+        const TV* v = blk + (long long)(npv + tq) * KD;
 #pragma unroll
         for (int a = 0; a < K; ++a) {
-          const double xp = __ldg(x + a * block + pc);
+          const TV xp = from_f64<TV>(__ldg(x + a * block + pc));
 #pragma unroll
           for (int l = 0; l < D; ++l) acc[a * D + l] += __ldcs(v + a * D + l) * xp;
         }
@@ -200,9 +276,10 @@ __global__ void __launch_bounds__(256, (K == 3 ? 3 : 4)) k_spmv_nodeblock(
       if (ok && kv < KD && (lane & wmask_v) == 0) {
         const int a = kv / D, l = kv - a * D;
         const long long row = a * block + (long long)l * R + i;
-        if (mode == 0) y[row] = acc[0];
-        else if (mode == 1) y[row] = b[row] - acc[0];
-        else y[row] += acc[0];
+        const double sum = (double)acc[0];
+        if (mode == 0) y[row] = sum;
+        else if (mode == 1) y[row] = b[row] - sum;
+        else y[row] += sum;
       }
     } else {
       // more accumulators than lanes: plain butterfly sums, lane 0 writes all rows
@@ -215,9 +292,10 @@ __global__ void __launch_bounds__(256, (K == 3 ? 3 : 4)) k_spmv_nodeblock(
         for (int r = 0; r < KD; ++r) {
           const int a = r / D, l = r - a * D;
           const long long row = a * block + (long long)l * R + i;
-          if (mode == 0) y[row] = acc[r];
-          else if (mode == 1) y[row] = b[row] - acc[r];
-          else y[row] += acc[r];
+          const double sum = (double)acc[r];
+          if (mode == 0) y[row] = sum;
+          else if (mode == 1) y[row] = b[row] - sum;
+          else y[row] += sum;
         }
     }
   }
@@ -235,27 +313,28 @@ __global__ void __launch_bounds__(256, (K == 3 ? 3 : 4)) k_spmv_nodeblock(
       const long long cq = pr - (long long)a * C * NP;
       const long long c = cq / NP;
       const long long row = a * block + (long long)D * R + cq;
-      const double* vr = pvalT + ((pr >> 5) * (D * NV)) * 32 + (pr & 31);
+      const TV* vr = pvalT + ((pr >> 5) * (D * NV)) * 32 + (pr & 31);
       const int* cn = cell_nodes + c * NV;
       const double* xa = x + a * block;
-      double s = 0.0;
+      TV s = TV(0);
 #pragma unroll
       for (int m = 0; m < D; ++m) {
 #pragma unroll 9
         for (int jj = 0; jj < NV; ++jj)
-          s += __ldcs(vr + (m * NV + jj) * 32) * __ldg(xa + (long long)m * R + __ldg(cn + jj));
+          s += __ldcs(vr + (m * NV + jj) * 32) * from_f64<TV>(__ldg(xa + (long long)m * R + __ldg(cn + jj)));
       }
-      if (mode == 0) y[row] = s;
-      else if (mode == 1) y[row] = b[row] - s;
-      else y[row] += s;
+      const double sum = (double)s;
+      if (mode == 0) y[row] = sum;
+      else if (mode == 1) y[row] = b[row] - sum;
+      else y[row] += sum;
     }
   }
 }
 
 static int sms_count();
 
-template <int VL, int K, int D>
-static void launch_nodeblock(const Level& L, const double* nval, const double* pvalT, const double* x, const double* b,
+template <typename TV, int VL, int K, int D>
+static void launch_nodeblock(const Level& L, const TV* nval, const TV* pvalT, const double* x, const double* b,
                              double* y, int mode, cudaStream_t s) {
   constexpr int GPW = 32 / VL;
   const long long npr = (long long)K * L.C * (D + 1);
@@ -264,7 +343,9 @@ static void launch_nodeblock(const Level& L, const double* nval, const double* p
   long long blocks;
   if (D == 2 && VL == 4) {
     // large 2D levels (velocity rows ~96% of the entries): every warp takes velocity groups, then
-    // pressure rows, over a grid of up to 4 CTAs per SM (measured best there)
+    // pressure rows, over a grid of up to 4 CTAs per SM. Where only 3 fit (80 registers) the last
+    // quarter of the CTAs fills in as others retire; measured faster than a grid of the resident
+    // count, twice it, or one unit per warp (FP64 98 against 107 us, FP32 56 against 62-69 us)
     vpc = 8;
     blocks = std::min<long long>(std::max((long long)L.R * VL, npr), (long long)sms_count() * 4 * 256);
     blocks = std::max<long long>(1, (blocks + 255) / 256);
@@ -274,13 +355,14 @@ static void launch_nodeblock(const Level& L, const double* nval, const double* p
     vpc = (int)std::min<long long>(7, std::max<long long>(1, (8 * need_v + (need_v + need_p) / 2) / (need_v + need_p)));
     blocks = std::max<long long>(1, std::max((need_v + vpc - 1) / vpc, (need_p + (8 - vpc) - 1) / (8 - vpc)));
   }
-  k_spmv_nodeblock<VL, K, D><<<(int)blocks, 256, 0, s>>>(L.rowptr, L.val, nval, pvalT, L.nbase, L.nbr_ptr, L.nbr,
-                                                         L.ncell, L.node_cells, L.cell_nodes, L.job_nodes, L.block,
-                                                         L.R, L.C, L.nv, x, b, y, mode, vpc);
+  k_spmv_nodeblock<TV, VL, K, D><<<(int)blocks, 256, 0, s>>>(nval, pvalT, L.nbase, L.nbr_ptr, L.nbr, L.ncell,
+                                                             L.node_cells, L.cell_nodes, L.job_nodes, L.block, L.R,
+                                                             L.C, L.nv, x, b, y, mode, vpc);
 }
 
-stm_status spmv_nodeblock(const Level& L, const double* nval, const double* pvalT, const double* x, const double* b,
-                          double* y, int mode, cudaStream_t s) {
+template <typename TV>
+static stm_status spmv_nodeblock_t(const Level& L, const TV* nval, const TV* pvalT, const double* x, const double* b,
+                                   double* y, int mode, cudaStream_t s) {
   // short groups (4 lanes in 2D, 8 in 3D) need at least ~1024 resident threads per SM to keep
   // enough loads in flight; smaller levels use 16 lanes per node
   const long long per_sm_threads = 1024;
@@ -288,30 +370,70 @@ stm_status spmv_nodeblock(const Level& L, const double* nval, const double* pval
   if ((long long)L.R * (L.dim == 2 ? 4 : 8) < (long long)sms_count() * per_sm_threads) cls = 100;
   if ((long long)L.R * 16 < (long long)sms_count() * per_sm_threads / 4) cls = 200;
   switch (L.dim * 10 + L.K + cls) {
-    case 21: launch_nodeblock<4, 1, 2>(L, nval, pvalT, x, b, y, mode, s); break;
-    case 22: launch_nodeblock<4, 2, 2>(L, nval, pvalT, x, b, y, mode, s); break;
-    case 23: launch_nodeblock<4, 3, 2>(L, nval, pvalT, x, b, y, mode, s); break;
-    case 31: launch_nodeblock<8, 1, 3>(L, nval, pvalT, x, b, y, mode, s); break;
-    case 32: launch_nodeblock<8, 2, 3>(L, nval, pvalT, x, b, y, mode, s); break;
-    case 33: launch_nodeblock<8, 3, 3>(L, nval, pvalT, x, b, y, mode, s); break;
-    case 121: launch_nodeblock<16, 1, 2>(L, nval, pvalT, x, b, y, mode, s); break;
-    case 122: launch_nodeblock<16, 2, 2>(L, nval, pvalT, x, b, y, mode, s); break;
-    case 123: launch_nodeblock<16, 3, 2>(L, nval, pvalT, x, b, y, mode, s); break;
-    case 131: launch_nodeblock<16, 1, 3>(L, nval, pvalT, x, b, y, mode, s); break;
-    case 132: launch_nodeblock<16, 2, 3>(L, nval, pvalT, x, b, y, mode, s); break;
-    case 133: launch_nodeblock<16, 3, 3>(L, nval, pvalT, x, b, y, mode, s); break;
-    case 221: launch_nodeblock<32, 1, 2>(L, nval, pvalT, x, b, y, mode, s); break;
-    case 222: launch_nodeblock<32, 2, 2>(L, nval, pvalT, x, b, y, mode, s); break;
-    case 223: launch_nodeblock<32, 3, 2>(L, nval, pvalT, x, b, y, mode, s); break;
-    case 231: launch_nodeblock<32, 1, 3>(L, nval, pvalT, x, b, y, mode, s); break;
-    case 232: launch_nodeblock<32, 2, 3>(L, nval, pvalT, x, b, y, mode, s); break;
-    case 233: launch_nodeblock<32, 3, 3>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 21: launch_nodeblock<TV, 4, 1, 2>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 22: launch_nodeblock<TV, 4, 2, 2>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 23: launch_nodeblock<TV, 4, 3, 2>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 31: launch_nodeblock<TV, 8, 1, 3>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 32: launch_nodeblock<TV, 8, 2, 3>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 33: launch_nodeblock<TV, 8, 3, 3>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 121: launch_nodeblock<TV, 16, 1, 2>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 122: launch_nodeblock<TV, 16, 2, 2>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 123: launch_nodeblock<TV, 16, 3, 2>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 131: launch_nodeblock<TV, 16, 1, 3>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 132: launch_nodeblock<TV, 16, 2, 3>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 133: launch_nodeblock<TV, 16, 3, 3>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 221: launch_nodeblock<TV, 32, 1, 2>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 222: launch_nodeblock<TV, 32, 2, 2>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 223: launch_nodeblock<TV, 32, 3, 2>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 231: launch_nodeblock<TV, 32, 1, 3>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 232: launch_nodeblock<TV, 32, 2, 3>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 233: launch_nodeblock<TV, 32, 3, 3>(L, nval, pvalT, x, b, y, mode, s); break;
     default:
       set_error("node-block SpMV: unsupported (dim, k)");
       return STM_ERR_INVALID_ARG;
   }
   note_launch();
   STM_CUDA(cudaGetLastError());
+  return STM_OK;
+}
+
+stm_status spmv_nodeblock(const Level& L, const double* nval, const double* pvalT, const double* x, const double* b,
+                          double* y, int mode, cudaStream_t s) {
+  return spmv_nodeblock_t<double>(L, nval, pvalT, x, b, y, mode, s);
+}
+stm_status spmv_nodeblock(const Level& L, const float* nval, const float* pvalT, const double* x, const double* b,
+                          double* y, int mode, cudaStream_t s) {
+  return spmv_nodeblock_t<float>(L, nval, pvalT, x, b, y, mode, s);
+}
+
+// FP32 copy of an FP64 array (round to nearest)
+__global__ void k_round_f32(const double* __restrict__ src, float* __restrict__ dst, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = __double2float_rn(src[i]);
+}
+
+static stm_status round_f32(const double* src, float* dst, long long n, cudaStream_t s) {
+  if (n <= 0) return STM_OK;
+  const int blocks = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, (long long)sms_count() * 8));
+  k_round_f32<<<blocks, 256, 0, s>>>(src, dst, n);
+  note_launch();
+  STM_CUDA(cudaGetLastError());
+  return STM_OK;
+}
+
+stm_status build_values_f32(Level& L, int transpose, cudaStream_t s) {
+  const double* nv = transpose ? L.nvalJT : L.nval;
+  const double* pv = transpose ? L.pvalJT : L.pvalT;
+  float*& n32 = transpose ? L.nvalJT32 : L.nval32;
+  float*& p32 = transpose ? L.pvalJT32 : L.pval32;
+  if (!nv) {
+    set_error("FP32 defect copies: the FP64 node-block values are not built");
+    return STM_ERR_STATE;
+  }
+  if (!n32) STM_CUDA(cudaMalloc((void**)&n32, sizeof(float) * std::max<long long>(1, L.nval_len)));
+  if (!p32) STM_CUDA(cudaMalloc((void**)&p32, sizeof(float) * std::max<long long>(1, L.pval_len)));
+  STM_TRY(round_f32(nv, n32, L.nval_len, s));
+  if (pv) STM_TRY(round_f32(pv, p32, L.pval_len, s));
   return STM_OK;
 }
 

@@ -277,7 +277,10 @@ __global__ void __launch_bounds__(256) k_vanka_local_t(const S* __restrict__ inv
   }
 }
 
-// Second pass of the additive / overwrite variants (one thread per global DoF).
+// Second pass of the additive / overwrite variants (one thread per global DoF). A DoF has at most
+// 2^d owners (the cells around a vertex), so all owner positions are loaded first and then all Y
+// entries, two dependent loads in all instead of two per owner; the sum still runs in owner order.
+template <int MAXO>
 __global__ void k_vanka_gather(double* __restrict__ d, const double* __restrict__ Y,
                                const int* __restrict__ own_ptr, const int* __restrict__ own_pos,
                                const int* __restrict__ last_owner, const double* __restrict__ wmult,
@@ -286,8 +289,18 @@ __global__ void k_vanka_gather(double* __restrict__ d, const double* __restrict_
     if (overwrite) {
       d[i] += omega * Y[last_owner[i]];
     } else {
+      const int p0 = own_ptr[i], p1 = own_ptr[i + 1];
+      int pos[MAXO];
+#pragma unroll
+      for (int k = 0; k < MAXO; ++k) pos[k] = p0 + k < p1 ? __ldg(own_pos + p0 + k) : -1;
+      double y[MAXO];
+#pragma unroll
+      for (int k = 0; k < MAXO; ++k) y[k] = pos[k] >= 0 ? Y[pos[k]] : 0.0;
       double s = 0.0;
-      for (int p = own_ptr[i]; p < own_ptr[i + 1]; ++p) s += Y[own_pos[p]];
+#pragma unroll
+      for (int k = 0; k < MAXO; ++k)
+        if (pos[k] >= 0) s += y[k];
+      for (int p = p0 + MAXO; p < p1; ++p) s += Y[own_pos[p]];
       d[i] += omega * wmult[i] * s;
     }
   }
@@ -406,7 +419,7 @@ stm_status vanka_step(Hierarchy& H, int g, const double* r, double* d, int trans
       const int nc = L.colour_off[col + 1] - L.colour_off[col];
       const double* t = r;
       if (!(d_is_zero && col == 0)) {
-        stm_status st = jacobian_apply(H, g, d, r, L.t, 1, transpose, s);
+        stm_status st = smoother_defect(H, g, d, r, L.t, transpose, s);
         if (st != STM_OK) return st;
         t = L.t;
       }
@@ -417,7 +430,7 @@ stm_status vanka_step(Hierarchy& H, int g, const double* r, double* d, int trans
   }
   const double* t = r;
   if (!d_is_zero) {
-    stm_status st = jacobian_apply(H, g, d, r, L.t, 1, transpose, s);
+    stm_status st = smoother_defect(H, g, d, r, L.t, transpose, s);
     if (st != STM_OK) return st;
     t = L.t;
   }
@@ -425,8 +438,9 @@ stm_status vanka_step(Hierarchy& H, int g, const double* r, double* d, int trans
   if (st != STM_OK) return st;
   const int blocks = (int)std::min<long long>((L.N + 255) / 256, sm_count() * 16LL);
   ProfScope ps(&H, STM_KCLASS_VANKA_COMBINE, s, 0.0, g);
-  k_vanka_gather<<<blocks, 256, 0, s>>>(d, L.Y, L.own_ptr, L.own_pos, L.last_owner, L.wmult, L.N, omega,
-                                        H.p.smoother == STM_VANKA_PAPER_OVERWRITE);
+  const int ow = H.p.smoother == STM_VANKA_PAPER_OVERWRITE;
+  if (L.dim == 2) k_vanka_gather<4><<<blocks, 256, 0, s>>>(d, L.Y, L.own_ptr, L.own_pos, L.last_owner, L.wmult, L.N, omega, ow);
+  else k_vanka_gather<8><<<blocks, 256, 0, s>>>(d, L.Y, L.own_ptr, L.own_pos, L.last_owner, L.wmult, L.N, omega, ow);
   note_launch();
   STM_CUDA(cudaGetLastError());
   return STM_OK;

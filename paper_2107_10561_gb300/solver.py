@@ -14,7 +14,7 @@ from . import _lib
 
 def make_params(dim, k, n_levels, coarse_cells, length, obstacle_lo=(0, 0, 0), obstacle_hi=(0, 0, 0),
                 tau=0.01, nu=1e-3, gamma1=35.0, gamma2=35.0, inv_precision="f64", smoother="additive",
-                omega=0.7, nu1=2, nu2=2):
+                omega=0.7, nu1=2, nu2=2, defect_precision="f64"):
     p = _lib.StmParams()
     p.dim, p.k, p.n_levels = dim, k, n_levels
     pad = lambda t, v: list(t) + [v] * (3 - len(t))
@@ -26,6 +26,8 @@ def make_params(dim, k, n_levels, coarse_cells, length, obstacle_lo=(0, 0, 0), o
     p.inv_precision = _lib.PRECISION[inv_precision] if isinstance(inv_precision, str) else inv_precision
     p.smoother = _lib.SMOOTHER[smoother] if isinstance(smoother, str) else smoother
     p.omega, p.nu1, p.nu2 = omega, nu1, nu2
+    p.defect_precision = (_lib.PRECISION[defect_precision] if isinstance(defect_precision, str)
+                          else defect_precision)
     return p
 
 
@@ -105,6 +107,12 @@ class Hierarchy:
         n = self.n_dofs(level)
         _lib.check(self.lib.stm_spmv(self.h, level, _ptr(x, n, "x"), _ptr(y, n, "y"), int(transpose), _stream(stream)),
                    "stm_spmv")
+
+    def defect(self, level, r, d, t, transpose=False, stream=None):
+        """t = r - J_g d (or J_g^T d) as the V-cycle computes it (params.defect_precision)."""
+        n = self.n_dofs(level)
+        _lib.check(self.lib.stm_defect(self.h, level, _ptr(r, n, "r"), _ptr(d, n, "d"), _ptr(t, n, "t"),
+                                       int(transpose), _stream(stream)), "stm_defect")
 
     def vanka_sweep(self, level, r, d, transpose=False, stream=None):
         n = self.n_dofs(level)
