@@ -44,6 +44,8 @@ def parse():
                     help="viscosity / damping study: Newton and FGMRES counts for nu x omega_d (V(4,4), tau 0.005)")
     ap.add_argument("--march", type=int, default=0,
                     help="time-march this many slabs (damped Newton per slab) and report the wake functional")
+    ap.add_argument("--mesh-study", action="store_true",
+                    help="FGMRES iterations of V(1,1) and V(4,4) as one coarse grid is refined (2D and 3D dG(1))")
     ap.add_argument("--newton", action="store_true",
                     help="time the damped Newton solve of the nonlinear slab problem instead of one linear solve")
     ap.add_argument("--oracle-child", default=None, help=argparse.SUPPRESS)
@@ -210,8 +212,9 @@ def spmv_roofline(r, wl, sizes, fp64_peak, workload_name):
 def defect_roofline(r, sizes, hbm, peak_source, workload_name):
     """The V-cycle's defect r - J_g d over the FP32 copies of J_g, finest level (HBM bound).
 
-    achieved = (4 nnz + 24 N) algorithmic bytes per launch (FP32 values; x, b, y in FP64) / average
-    event time per launch; peak = the measured copy bandwidth."""
+    achieved = (4 nnz + 20 N) algorithmic bytes per launch (FP32 values and d, FP64 r and t) / average
+    event time per launch of the product kernel; peak = the measured copy bandwidth. The rounding of
+    d to FP32 before it (12 N bytes, a launch of its own) is timed as class round_f32."""
     f = r["finest"]["defect_f32"]
     if f["ms"] <= 0 or f["launches"] == 0:
         return None
@@ -357,7 +360,8 @@ def gpu_leg(args, rank, world, local_rank):
         pv1.record(stream)
         torch.cuda.synchronize()
         r["ms_per_solve_profiled"] = pv0.elapsed_time(pv1) / args.steps
-        r["kernels"] = {k: h.profile_read(k) for k in ("vanka_local", "jacobian_spmv", "defect_f32", "vanka_combine", "transfer",
+        r["kernels"] = {k: h.profile_read(k) for k in ("vanka_local", "jacobian_spmv", "defect_f32", "round_f32",
+                                                       "vanka_combine", "transfer",
                                                        "coarse", "krylov")}
         r["finest"] = {k: h.profile_read(k, wl.n_levels - 1) for k in ("vanka_local", "jacobian_spmv", "defect_f32")}
         r["per_level"] = {k: [h.profile_read(k, g) for g in range(wl.n_levels)]
@@ -663,6 +667,60 @@ def gpu_leg_robustness(args, local_rank):
     print(json.dumps(line))
 
 
+def gpu_leg_mesh(args, local_rank):
+    """Tables 5.1 and 5.5 setting on the synthetic channel: one linear FGMRES solve (seeded right-hand
+    side, seeded linearisation point, rtol as given) with V(1,1) and with V(4,4) cycles while the same
+    coarse grid is refined: 2D dG(1) on 3..6 levels, 3D dG(1) on 2..4 levels. The paper reports the
+    average per Newton step over whole simulations; here each entry is one solve."""
+    import dataclasses
+
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2107_10561_gb300 import Hierarchy
+    from paper_2107_10561_gb300 import build as _build
+
+    torch.cuda.set_device(local_rank)
+    _build.build()
+    prec = args.precisions.split(",")[-1]
+    table = []
+    t_all = time.perf_counter()
+    for base_name, levels in (("c4_2d_k1", (3, 4, 5, 6)), ("c3_3d_k1", (2, 3, 4))):
+        base = workload(base_name)
+        for n_levels in levels:
+            for sweeps in (1, 4):
+                wl = dataclasses.replace(base, n_levels=n_levels, nu1=sweeps, nu2=sweeps)
+                h = Hierarchy(hier_params(wl, prec, "additive"))
+                idx = h.dof_lattice_index()
+                X = torch.from_numpy(np.ascontiguousarray(synth.linearisation_point(wl).reshape(-1)[idx])).cuda()
+                b = torch.from_numpy(np.ascontiguousarray(synth.random_rhs(wl).reshape(-1)[idx])).cuda()
+                h.assemble_jacobian(X)
+                h.factor_cells()
+                x = torch.zeros_like(b)
+                h.gmres_solve(b, x, rtol=args.rtol, restart=wl.restart, raise_on_fail=False)
+                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                x.zero_()
+                torch.cuda.synchronize()
+                ev0.record()
+                info = h.gmres_solve(b, x, rtol=args.rtol, restart=wl.restart, raise_on_fail=False)
+                ev1.record()
+                torch.cuda.synchronize()
+                table.append({"mesh": f"{wl.dim}D {'x'.join(map(str, wl.fine_cells))}", "levels": n_levels,
+                              "dofs": h.n_dofs(), "cycle": f"V({sweeps},{sweeps})", "iters": info["iters"],
+                              "converged": info["status"] == "STM_OK", "ms": ev0.elapsed_time(ev1)})
+                h.close()
+    line = {"metric": "FGMRES iterations per solve for V(1,1) / V(4,4) under refinement (Tables 5.1, 5.5 setting)",
+            "value": time.perf_counter() - t_all, "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": dtype_label(prec),
+            "data": "synthetic",
+            "config": {"workload": "2D channel 16x4 coarse cells (obstacle), dG(1), 3..6 levels; 3D channel "
+                                   "16x4x4 coarse cells (obstacle), dG(1), 2..4 levels; additive Vanka, omega 0.7",
+                       "rtol": args.rtol, "parallelism": "single GPU"},
+            "table": table}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.oracle_child:
@@ -692,6 +750,10 @@ def main():
         print(json.dumps(line))
         return
 
+    if args.mesh_study:
+        if rank == 0:
+            gpu_leg_mesh(args, local_rank)
+        return
     if args.newton:
         if rank == 0:
             gpu_leg_newton(args, local_rank)

@@ -292,7 +292,8 @@ stm_status stm_vanka_apply_noalloc(long long n_cells, int n_local, long long n_d
  *   VANKA_COMBINE second pass of the additive/overwrite smoother; TRANSFER P and P^T products;
  *   COARSE        dense coarse solve; KRYLOV Gram-Schmidt, norms and updates of FGMRES;
  *   DEFECT_F32    the V-cycle's defect r - J_g d over the FP32 copies (defect_precision =
- *                 STM_F32): 4 nnz + 24 N bytes. */
+ *                 STM_F32): 4 nnz + 20 N bytes (values, d in FP32, r, t);
+ *   ROUND_F32     the rounding of d to FP32 that precedes each FP32 defect: 12 N bytes. */
 typedef enum {
   STM_KCLASS_VANKA_LOCAL = 0,
   STM_KCLASS_JACOBIAN_SPMV = 1,
@@ -300,7 +301,8 @@ typedef enum {
   STM_KCLASS_TRANSFER = 3,
   STM_KCLASS_COARSE = 4,
   STM_KCLASS_KRYLOV = 5,
-  STM_KCLASS_DEFECT_F32 = 6
+  STM_KCLASS_DEFECT_F32 = 6,
+  STM_KCLASS_ROUND_F32 = 7
 } stm_kernel_class;
 
 /* Turn event timing of kernel launches on (1) or off (0); turning it on clears the records. */

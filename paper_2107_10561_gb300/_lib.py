@@ -13,7 +13,7 @@ STATUS_NAMES = {0: "STM_OK", 1: "STM_ERR_INVALID_ARG", 2: "STM_ERR_CUDA", 3: "ST
                 7: "STM_ERR_STATE"}
 PRECISION = {"f64": 0, "f32": 1, "bf16": 2}
 SMOOTHER = {"additive": 0, "coloured": 1, "overwrite": 2}
-KCLASS = {"vanka_local": 0, "jacobian_spmv": 1, "vanka_combine": 2, "transfer": 3, "coarse": 4, "krylov": 5, "defect_f32": 6}
+KCLASS = {"vanka_local": 0, "jacobian_spmv": 1, "vanka_combine": 2, "transfer": 3, "coarse": 4, "krylov": 5, "defect_f32": 6, "round_f32": 7}
 
 
 class StmParams(C.Structure):

@@ -751,7 +751,7 @@ void free_hierarchy(Hierarchy& H) {
   for (Level& L : H.L) {
     void* ptrs[] = {L.idx, L.cell_nodes, L.cell_xyz, L.bmask, L.rank, L.cellrank, L.nn, L.ncell, L.rowptr, L.nbr_ptr, L.nbr,
                     L.node_cells, L.job_nodes, L.nbase, L.nval, L.pvalT, L.nvalJT, L.pvalJT, L.nval32, L.pval32,
-                    L.nvalJT32, L.pvalJT32,
+                    L.nvalJT32, L.pvalJT32, L.x32,
                     L.colidx, L.val, L.valT, L.ref, L.inj, L.wnod, L.inv, L.wmult, L.own_ptr,
                     L.own_pos, L.last_owner, L.colour_cells, L.Y, L.P_rowptr, L.P_col, L.P_val,
                     L.Rt_rowptr, L.Rt_col, L.Rt_val, L.tv_ptr, L.tv_node, L.tv_w, L.tc_ptr, L.tc_node,

@@ -14,7 +14,7 @@
 #include "stm.h"
 
 namespace stm {
-constexpr int STM_KCLASS_COUNT = 7;
+constexpr int STM_KCLASS_COUNT = 8;
 
 constexpr int kMaxDim = 3;
 constexpr int kCoarseTChunk = 512;  // rows per partial sum of the transposed coarse solve
@@ -116,6 +116,7 @@ struct Level {
   // FP32 copies of nval/pvalT (and of nvalJT/pvalJT) in the same layout, for the V-cycle's defects
   // r - J_g d with defect_precision = STM_F32; null otherwise
   float *nval32 = nullptr, *pval32 = nullptr, *nvalJT32 = nullptr, *pvalJT32 = nullptr;
+  float* x32 = nullptr;  // [N] the defect's d rounded to FP32
   long long nval_len = 0, pval_len = 0;          // entries of nval and pvalT
   int* ncell = nullptr;           // [R] number of cells containing the node
   long long* rowptr = nullptr;    // [N+1]
@@ -237,9 +238,10 @@ stm_status spmv_nodeblock(const Level& L, const double* nval, const double* pval
 stm_status build_nodeblock(Level& L, cudaStream_t s);
 // node-block and warp-transposed pressure-row copies of any value array on J's pattern (J or J^T)
 stm_status build_nodeblock_from(const Level& L, const double* val, double* nval, double* pvalT, cudaStream_t s);
-// the same product over FP32 copies of the values: FP32 products and sums, FP64 x, b and y
-stm_status spmv_nodeblock(const Level& L, const float* nval, const float* pvalT, const double* x, const double* b,
-                          double* y, int mode, cudaStream_t s);
+// y = b - J_g x (transpose: J_g^T) over the FP32 copies of the values: x rounded to FP32 into L.x32,
+// FP32 products and sums, b and y in FP64
+stm_status defect_f32(Hierarchy& H, int g, int transpose, const double* x, const double* b, double* y,
+                      cudaStream_t s);
 // FP32 copies of J_g's (or J_g^T's) node-block arrays (allocated on first use, same layout)
 stm_status build_values_f32(Level& L, int transpose, cudaStream_t s);
 stm_status jacobian_apply(Hierarchy& H, int g, const double* x, const double* b, double* y,

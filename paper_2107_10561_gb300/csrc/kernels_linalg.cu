@@ -143,16 +143,8 @@ stm_status jacobian_apply(Hierarchy& H, int g, const double* x, const double* b,
 stm_status smoother_defect(Hierarchy& H, int g, const double* x, const double* b, double* y, int transpose,
                            cudaStream_t s) {
   if (H.p.defect_precision != STM_F32) return jacobian_apply(H, g, x, b, y, 1, transpose, s);
-  Level& L = H.L[g];
   if (transpose) STM_TRY(ensure_transpose(H, g, s));
-  const float* nv = transpose ? L.nvalJT32 : L.nval32;
-  const float* pv = transpose ? L.pvalJT32 : L.pval32;
-  if (!nv || !pv) {
-    set_error("FP32 defect copies missing: assemble the Jacobian first");
-    return STM_ERR_STATE;
-  }
-  ProfScope ps(&H, STM_KCLASS_DEFECT_F32, s, 4.0 * (double)L.nnz + 24.0 * (double)L.N, g);
-  return spmv_nodeblock(L, nv, pv, x, b, y, 1, s);
+  return defect_f32(H, g, transpose, x, b, y, s);
 }
 
 // Dense coarse solve: d = Cinv r (row-major) or d = Cinv^T r.

@@ -1,6 +1,6 @@
 // Structured product with the slab Jacobian J_g or its transpose: y = J x, y = b - J x or y += J x,
 // in FP64, or over FP32 copies of the values for the V-cycle's defects (FP32 products and sums, x
-// rounded to FP32 on load, b and y in FP64).
+// rounded to FP32 in a pass of its own, b and y in FP64).
 //
 // Every velocity row (a, l, i) of J couples node i with the same neighbour list nbr(i) in every
 // (time b, component m) block, plus the pressures of the cells around i at time a (Problem 3.1,
@@ -133,14 +133,6 @@ stm_status build_nodeblock_from(const Level& L, const double* val, double* nval,
   return STM_OK;
 }
 
-// x is FP64 in both products; the FP32 one rounds it to nearest (hardware conversion)
-template <typename TV>
-__device__ __forceinline__ TV from_f64(double v);
-template <>
-__device__ __forceinline__ double from_f64<double>(double v) { return v; }
-template <>
-__device__ __forceinline__ float from_f64<float>(double v) { return __double2float_rn(v); }
-
 // Loads the K*d values of one node-block position (FP64: one by one; FP32 with K*d even: as float2,
 // the position starts on an 8-byte boundary since every node block holds a multiple of K*d values).
 template <int KD>
@@ -173,7 +165,7 @@ __global__ void __launch_bounds__(256, ((sizeof(TV) == 4 && VL > 8) || K < 3) ? 
     const TV* __restrict__ nval, const TV* __restrict__ pvalT,
     const long long* __restrict__ nbase, const int* __restrict__ nbr_ptr, const int* __restrict__ nbr,
     const int* __restrict__ ncell, const int* __restrict__ node_cells, const int* __restrict__ cell_nodes,
-    const int* __restrict__ job_nodes, long long block, int R, int C, int nv, const double* __restrict__ x,
+    const int* __restrict__ job_nodes, long long block, int R, int C, int nv, const TV* __restrict__ x,
     const double* __restrict__ b, double* __restrict__ y, int mode, int vpc) {
   constexpr int GPW = 32 / VL;
   constexpr int KD = K * D;
@@ -246,7 +238,7 @@ __global__ void __launch_bounds__(256, ((sizeof(TV) == 4 && VL > 8) || K < 3) ? 
           for (int k = 0; k < U; ++k)
             if (k == 0 || p + k * VL < npv) {
               const int bb = bk[k] / D, m = bk[k] - bb * D;
-              xk[k] = from_f64<TV>(__ldg(x + bb * block + (long long)m * R + nbr[p0 + jk[k]]));
+              xk[k] = __ldg(x + bb * block + (long long)m * R + nbr[p0 + jk[k]]);
             }
 #pragma unroll
           for (int k = 0; k < U; ++k)
@@ -265,7 +257,7 @@ __global__ void __launch_bounds__(256, ((sizeof(TV) == 4 && VL > 8) || K < 3) ? 
         const TV* v = blk + (long long)(npv + tq) * KD;
 #pragma unroll
         for (int a = 0; a < K; ++a) {
-          const TV xp = from_f64<TV>(__ldg(x + a * block + pc));
+          const TV xp = __ldg(x + a * block + pc);
 #pragma unroll
           for (int l = 0; l < D; ++l) acc[a * D + l] += __ldcs(v + a * D + l) * xp;
         }
@@ -315,13 +307,13 @@ __global__ void __launch_bounds__(256, ((sizeof(TV) == 4 && VL > 8) || K < 3) ? 
       const long long row = a * block + (long long)D * R + cq;
       const TV* vr = pvalT + ((pr >> 5) * (D * NV)) * 32 + (pr & 31);
       const int* cn = cell_nodes + c * NV;
-      const double* xa = x + a * block;
+      const TV* xa = x + a * block;
       TV s = TV(0);
 #pragma unroll
       for (int m = 0; m < D; ++m) {
 #pragma unroll 9
         for (int jj = 0; jj < NV; ++jj)
-          s += __ldcs(vr + (m * NV + jj) * 32) * from_f64<TV>(__ldg(xa + (long long)m * R + __ldg(cn + jj)));
+          s += __ldcs(vr + (m * NV + jj) * 32) * __ldg(xa + (long long)m * R + __ldg(cn + jj));
       }
       const double sum = (double)s;
       if (mode == 0) y[row] = sum;
@@ -334,7 +326,7 @@ __global__ void __launch_bounds__(256, ((sizeof(TV) == 4 && VL > 8) || K < 3) ? 
 static int sms_count();
 
 template <typename TV, int VL, int K, int D>
-static void launch_nodeblock(const Level& L, const TV* nval, const TV* pvalT, const double* x, const double* b,
+static void launch_nodeblock(const Level& L, const TV* nval, const TV* pvalT, const TV* x, const double* b,
                              double* y, int mode, cudaStream_t s) {
   constexpr int GPW = 32 / VL;
   const long long npr = (long long)K * L.C * (D + 1);
@@ -361,7 +353,7 @@ static void launch_nodeblock(const Level& L, const TV* nval, const TV* pvalT, co
 }
 
 template <typename TV>
-static stm_status spmv_nodeblock_t(const Level& L, const TV* nval, const TV* pvalT, const double* x, const double* b,
+static stm_status spmv_nodeblock_t(const Level& L, const TV* nval, const TV* pvalT, const TV* x, const double* b,
                                    double* y, int mode, cudaStream_t s) {
   // short groups (4 lanes in 2D, 8 in 3D) need at least ~1024 resident threads per SM to keep
   // enough loads in flight; smaller levels use 16 lanes per node
@@ -401,10 +393,6 @@ stm_status spmv_nodeblock(const Level& L, const double* nval, const double* pval
                           double* y, int mode, cudaStream_t s) {
   return spmv_nodeblock_t<double>(L, nval, pvalT, x, b, y, mode, s);
 }
-stm_status spmv_nodeblock(const Level& L, const float* nval, const float* pvalT, const double* x, const double* b,
-                          double* y, int mode, cudaStream_t s) {
-  return spmv_nodeblock_t<float>(L, nval, pvalT, x, b, y, mode, s);
-}
 
 // FP32 copy of an FP64 array (round to nearest)
 __global__ void k_round_f32(const double* __restrict__ src, float* __restrict__ dst, long long n) {
@@ -432,9 +420,29 @@ stm_status build_values_f32(Level& L, int transpose, cudaStream_t s) {
   }
   if (!n32) STM_CUDA(cudaMalloc((void**)&n32, sizeof(float) * std::max<long long>(1, L.nval_len)));
   if (!p32) STM_CUDA(cudaMalloc((void**)&p32, sizeof(float) * std::max<long long>(1, L.pval_len)));
+  if (!L.x32) STM_CUDA(cudaMalloc((void**)&L.x32, sizeof(float) * std::max<long long>(1, L.N)));
   STM_TRY(round_f32(nv, n32, L.nval_len, s));
   if (pv) STM_TRY(round_f32(pv, p32, L.pval_len, s));
   return STM_OK;
+}
+
+// y = b - J x (or J^T x) over the FP32 copies: x is rounded to FP32 once (one pass over N), so the
+// product gathers 4-byte entries and converts nothing
+stm_status defect_f32(Hierarchy& H, int g, int transpose, const double* x, const double* b, double* y,
+                      cudaStream_t s) {
+  Level& L = H.L[g];
+  const float* nv = transpose ? L.nvalJT32 : L.nval32;
+  const float* pv = transpose ? L.pvalJT32 : L.pval32;
+  if (!nv || !pv || !L.x32) {
+    set_error("FP32 defect copies missing: assemble the Jacobian first");
+    return STM_ERR_STATE;
+  }
+  {
+    ProfScope ps(&H, STM_KCLASS_ROUND_F32, s, 12.0 * (double)L.N, g);
+    STM_TRY(round_f32(x, L.x32, L.N, s));
+  }
+  ProfScope ps(&H, STM_KCLASS_DEFECT_F32, s, 4.0 * (double)L.nnz + 20.0 * (double)L.N, g);
+  return spmv_nodeblock_t<float>(L, nv, pv, L.x32, b, y, 1, s);
 }
 
 static int sms_count() {
