@@ -232,16 +232,19 @@ stm_status csr_apply(const long long* rowptr, const int* col, const double* val,
                      const double* x, const double* b, double* y, int mode, cudaStream_t s);
 // Matrix-free transfers between level g-1 and level g (kernels_transfer.cu)
 stm_status transfer_restrict(const Level& F, const Level& Cl, const double* fine, double* coarse, cudaStream_t s);
-stm_status transfer_prolong_add(const Level& F, const Level& Cl, const double* coarse, double* fine, cudaStream_t s);
+// fine += P coarse; with fine32 non-null the updated entries are also stored rounded to FP32 there
+stm_status transfer_prolong_add(const Level& F, const Level& Cl, const double* coarse, double* fine, cudaStream_t s,
+                                float* fine32 = nullptr);
 stm_status spmv_nodeblock(const Level& L, const double* nval, const double* pvalT, const double* x, const double* b,
                           double* y, int mode, cudaStream_t s);
 stm_status build_nodeblock(Level& L, cudaStream_t s);
 // node-block and warp-transposed pressure-row copies of any value array on J's pattern (J or J^T)
 stm_status build_nodeblock_from(const Level& L, const double* val, double* nval, double* pvalT, cudaStream_t s);
-// y = b - J_g x (transpose: J_g^T) over the FP32 copies of the values: x rounded to FP32 into L.x32,
-// FP32 products and sums, b and y in FP64
+// y = b - J_g x (transpose: J_g^T) over the FP32 copies of the values: x rounded to FP32 into L.x32
+// (skipped when x32_current: the kernel that last wrote x stored it there rounded), FP32 products
+// and sums, b and y in FP64
 stm_status defect_f32(Hierarchy& H, int g, int transpose, const double* x, const double* b, double* y,
-                      cudaStream_t s);
+                      cudaStream_t s, bool x32_current = false);
 // FP32 copies of J_g's (or J_g^T's) node-block arrays (allocated on first use, same layout)
 stm_status build_values_f32(Level& L, int transpose, cudaStream_t s);
 stm_status jacobian_apply(Hierarchy& H, int g, const double* x, const double* b, double* y,
@@ -249,9 +252,11 @@ stm_status jacobian_apply(Hierarchy& H, int g, const double* x, const double* b,
 // the V-cycle's defect y = b - J_g x (or J_g^T): over the FP32 copies with defect_precision =
 // STM_F32, else jacobian_apply in FP64
 stm_status smoother_defect(Hierarchy& H, int g, const double* x, const double* b, double* y, int transpose,
-                           cudaStream_t s);
+                           cudaStream_t s, bool x32_current = false);
+// one smoothing step; d32_current: L.x32 holds d rounded to FP32 (the V-cycle's own sequence). With
+// FP32 defects the additive/overwrite combine stores the new d rounded to FP32 in L.x32 as well.
 stm_status vanka_step(Hierarchy& H, int g, const double* r, double* d, int transpose,
-                      bool d_is_zero, cudaStream_t s);
+                      bool d_is_zero, cudaStream_t s, bool d32_current = false);
 stm_status coarse_apply(Hierarchy& H, const double* r, double* d, int transpose, cudaStream_t s);
 stm_status assemble_cellvec(Hierarchy& H, int mode, double U, double nu, const int* wake_lo, const int* wake_hi,
                             double* out, cudaStream_t s, const double* vprev = nullptr);

@@ -141,10 +141,10 @@ stm_status jacobian_apply(Hierarchy& H, int g, const double* x, const double* b,
 // 1e-7 of |J_g||d|) below that of FP32 or BF16 cell inverses. The Arnoldi products and the true
 // residual stay FP64.
 stm_status smoother_defect(Hierarchy& H, int g, const double* x, const double* b, double* y, int transpose,
-                           cudaStream_t s) {
+                           cudaStream_t s, bool x32_current) {
   if (H.p.defect_precision != STM_F32) return jacobian_apply(H, g, x, b, y, 1, transpose, s);
   if (transpose) STM_TRY(ensure_transpose(H, g, s));
-  return defect_f32(H, g, transpose, x, b, y, s);
+  return defect_f32(H, g, transpose, x, b, y, s, x32_current);
 }
 
 // Dense coarse solve: d = Cinv r (row-major) or d = Cinv^T r.
@@ -201,6 +201,11 @@ stm_status coarse_apply(Hierarchy& H, const double* r, double* d, int transpose,
 stm_status vcycle(Hierarchy& H, const double* r_fine, double* d_fine, int transpose, cudaStream_t s) {
   const int G = (int)H.L.size();
   const int nu1 = H.p.nu1, nu2 = H.p.nu2;
+  // with FP32 defects, every d a defect reads here was last written by the combine of the additive /
+  // overwrite smoother or by the prolongation, which store it rounded to FP32 as well (the coloured
+  // smoother's local solves write d directly, so its defects round d themselves)
+  const bool f32 = H.p.defect_precision == STM_F32;
+  const bool mirrored = f32 && H.p.smoother != STM_VANKA_COLOURED;
   // descend
   const double* r = r_fine;
   for (int g = G - 1; g >= 1; --g) {
@@ -208,11 +213,12 @@ stm_status vcycle(Hierarchy& H, const double* r_fine, double* d_fine, int transp
     double* d = (g == G - 1) ? d_fine : L.d;
     STM_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * L.N, s));
     for (int it = 0; it < nu1; ++it) {
-      stm_status st = vanka_step(H, g, r, d, transpose, it == 0, s);
+      stm_status st = vanka_step(H, g, r, d, transpose, it == 0, s, mirrored && it > 0);
       if (st != STM_OK) return st;
     }
     // t = r - J d, restrict to the next coarser level
-    stm_status st = (nu1 > 0) ? smoother_defect(H, g, d, r, L.t, transpose, s) : vec_copy(L.t, r, L.N, s);
+    stm_status st = (nu1 > 0) ? smoother_defect(H, g, d, r, L.t, transpose, s, mirrored)
+                              : vec_copy(L.t, r, L.N, s);
     if (st != STM_OK) return st;
     Level& Lc = H.L[g - 1];
     {
@@ -237,11 +243,11 @@ stm_status vcycle(Hierarchy& H, const double* r_fine, double* d_fine, int transp
     stm_status st;
     {
       ProfScope ps(&H, STM_KCLASS_TRANSFER, s, 0.0, g);
-      st = transfer_prolong_add(L, H.L[g - 1], H.L[g - 1].d, d, s);
+      st = transfer_prolong_add(L, H.L[g - 1], H.L[g - 1].d, d, s, f32 ? L.x32 : nullptr);
     }
     if (st != STM_OK) return st;
     for (int it = 0; it < nu2; ++it) {
-      st = vanka_step(H, g, rg, d, transpose, false, s);
+      st = vanka_step(H, g, rg, d, transpose, false, s, mirrored);
       if (st != STM_OK) return st;
     }
   }

@@ -426,10 +426,10 @@ stm_status build_values_f32(Level& L, int transpose, cudaStream_t s) {
   return STM_OK;
 }
 
-// y = b - J x (or J^T x) over the FP32 copies: x is rounded to FP32 once (one pass over N), so the
-// product gathers 4-byte entries and converts nothing
+// y = b - J x (or J^T x) over the FP32 copies: x is rounded to FP32 once (one pass over N, or by the
+// kernel that wrote x), so the product gathers 4-byte entries and converts nothing
 stm_status defect_f32(Hierarchy& H, int g, int transpose, const double* x, const double* b, double* y,
-                      cudaStream_t s) {
+                      cudaStream_t s, bool x32_current) {
   Level& L = H.L[g];
   const float* nv = transpose ? L.nvalJT32 : L.nval32;
   const float* pv = transpose ? L.pvalJT32 : L.pval32;
@@ -437,7 +437,7 @@ stm_status defect_f32(Hierarchy& H, int g, int transpose, const double* x, const
     set_error("FP32 defect copies missing: assemble the Jacobian first");
     return STM_ERR_STATE;
   }
-  {
+  if (!x32_current) {
     ProfScope ps(&H, STM_KCLASS_ROUND_F32, s, 12.0 * (double)L.N, g);
     STM_TRY(round_f32(x, L.x32, L.N, s));
   }

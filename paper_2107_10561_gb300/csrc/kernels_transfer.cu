@@ -36,7 +36,7 @@ struct TransferGeom {
 template <int K, int D, int G>
 __global__ void k_prolong(const int* __restrict__ vptr, const int* __restrict__ vnode, const double* __restrict__ vw,
                           const int* __restrict__ parent, const unsigned char* __restrict__ bits, TransferGeom g,
-                          const double* __restrict__ xc, double* __restrict__ yf) {
+                          const double* __restrict__ xc, double* __restrict__ yf, float* __restrict__ yf32) {
   constexpr int NP = D + 1;
   const double s3 = 1.7320508075688772;  // sqrt(3), P1 Legendre normalisation
   const long long vthreads = ((long long)g.fR * G + 31) / 32 * 32;
@@ -65,7 +65,12 @@ __global__ void k_prolong(const int* __restrict__ vptr, const int* __restrict__ 
       if (nd < g.fR)
 #pragma unroll
         for (int r = 0; r < K * D; ++r)
-          if (r % G == gl) yf[(r / D) * g.fblock + (long long)(r % D) * g.fR + nd] += acc[r];
+          if (r % G == gl) {
+            const long long e = (r / D) * g.fblock + (long long)(r % D) * g.fR + nd;
+            const double v = yf[e] + acc[r];
+            yf[e] = v;
+            if (yf32) yf32[e] = __double2float_rn(v);
+          }
     } else {
       const int cf = (int)(it - vthreads);
       const int pc = parent[cf];
@@ -73,13 +78,17 @@ __global__ void k_prolong(const int* __restrict__ vptr, const int* __restrict__ 
 #pragma unroll
       for (int a = 0; a < K; ++a) {
         const double* c = xc + a * g.cblock + (long long)D * g.cR + (long long)pc * NP;
-        double* f = yf + a * g.fblock + (long long)D * g.fR + (long long)cf * NP;
+        const long long fo = a * g.fblock + (long long)D * g.fR + (long long)cf * NP;
+        double* f = yf + fo;
         double c0 = c[0];
 #pragma unroll
         for (int m = 0; m < D; ++m) c0 += s3 * ((double)((b >> m) & 1) - 0.5) * c[1 + m];
         f[0] += c0;
 #pragma unroll
         for (int m = 0; m < D; ++m) f[1 + m] += 0.5 * c[1 + m];
+        if (yf32)
+#pragma unroll
+          for (int q = 0; q < NP; ++q) yf32[fo + q] = __double2float_rn(f[q]);
       }
     }
   }
@@ -155,16 +164,18 @@ static TransferGeom geom(const Level& F, const Level& Cl) {
 constexpr long long many_nodes(int d) { return d == 2 ? 16384 : 65536; }
 
 template <int K, int D, int G>
-static void launch_prolong_g(const Level& F, const TransferGeom& g, const double* xc, double* yf, cudaStream_t s) {
+static void launch_prolong_g(const Level& F, const TransferGeom& g, const double* xc, double* yf, float* yf32,
+                             cudaStream_t s) {
   const long long items = ((long long)g.fR * G + 31) / 32 * 32 + g.fC;
   const int blocks = (int)std::max<long long>(1, std::min<long long>((items + 255) / 256, sm_count_tr() * 8LL));
-  k_prolong<K, D, G><<<blocks, 256, 0, s>>>(F.tv_ptr, F.tv_node, F.tv_w, F.cparent, F.cbits, g, xc, yf);
+  k_prolong<K, D, G><<<blocks, 256, 0, s>>>(F.tv_ptr, F.tv_node, F.tv_w, F.cparent, F.cbits, g, xc, yf, yf32);
 }
 
 template <int K, int D>
-static void launch_prolong(const Level& F, const TransferGeom& g, const double* xc, double* yf, cudaStream_t s) {
-  if (g.fR >= many_nodes(D)) launch_prolong_g<K, D, 1>(F, g, xc, yf, s);
-  else launch_prolong_g<K, D, D == 2 ? 4 : 8>(F, g, xc, yf, s);
+static void launch_prolong(const Level& F, const TransferGeom& g, const double* xc, double* yf, float* yf32,
+                           cudaStream_t s) {
+  if (g.fR >= many_nodes(D)) launch_prolong_g<K, D, 1>(F, g, xc, yf, yf32, s);
+  else launch_prolong_g<K, D, D == 2 ? 4 : 8>(F, g, xc, yf, yf32, s);
 }
 
 template <int K, int D, int G>
@@ -180,15 +191,16 @@ static void launch_restrict(const Level& F, const TransferGeom& g, const double*
   else launch_restrict_g<K, D, D == 2 ? 8 : 16>(F, g, tf, rc, s);
 }
 
-stm_status transfer_prolong_add(const Level& F, const Level& Cl, const double* coarse, double* fine, cudaStream_t s) {
+stm_status transfer_prolong_add(const Level& F, const Level& Cl, const double* coarse, double* fine, cudaStream_t s,
+                                float* fine32) {
   const TransferGeom g = geom(F, Cl);
   switch (F.dim * 10 + F.K) {
-    case 21: launch_prolong<1, 2>(F, g, coarse, fine, s); break;
-    case 22: launch_prolong<2, 2>(F, g, coarse, fine, s); break;
-    case 23: launch_prolong<3, 2>(F, g, coarse, fine, s); break;
-    case 31: launch_prolong<1, 3>(F, g, coarse, fine, s); break;
-    case 32: launch_prolong<2, 3>(F, g, coarse, fine, s); break;
-    case 33: launch_prolong<3, 3>(F, g, coarse, fine, s); break;
+    case 21: launch_prolong<1, 2>(F, g, coarse, fine, fine32, s); break;
+    case 22: launch_prolong<2, 2>(F, g, coarse, fine, fine32, s); break;
+    case 23: launch_prolong<3, 2>(F, g, coarse, fine, fine32, s); break;
+    case 31: launch_prolong<1, 3>(F, g, coarse, fine, fine32, s); break;
+    case 32: launch_prolong<2, 3>(F, g, coarse, fine, fine32, s); break;
+    case 33: launch_prolong<3, 3>(F, g, coarse, fine, fine32, s); break;
     default:
       set_error("prolongation: unsupported (dim, k)");
       return STM_ERR_INVALID_ARG;

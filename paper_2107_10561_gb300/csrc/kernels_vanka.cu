@@ -280,14 +280,17 @@ __global__ void __launch_bounds__(256) k_vanka_local_t(const S* __restrict__ inv
 // Second pass of the additive / overwrite variants (one thread per global DoF). A DoF has at most
 // 2^d owners (the cells around a vertex), so all owner positions are loaded first and then all Y
 // entries, two dependent loads in all instead of two per owner; the sum still runs in owner order.
+// With d32 non-null the new d is also stored rounded to FP32 there (the next FP32 defect reads it).
 template <int MAXO>
-__global__ void k_vanka_gather(double* __restrict__ d, const double* __restrict__ Y,
+__global__ void k_vanka_gather(double* __restrict__ d, float* __restrict__ d32, const double* __restrict__ Y,
                                const int* __restrict__ own_ptr, const int* __restrict__ own_pos,
                                const int* __restrict__ last_owner, const double* __restrict__ wmult,
                                long long N, double omega, int overwrite) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
     if (overwrite) {
-      d[i] += omega * Y[last_owner[i]];
+      const double nd = d[i] + omega * Y[last_owner[i]];
+      d[i] = nd;
+      if (d32) d32[i] = __double2float_rn(nd);
     } else {
       const int p0 = own_ptr[i], p1 = own_ptr[i + 1];
       int pos[MAXO];
@@ -301,7 +304,9 @@ __global__ void k_vanka_gather(double* __restrict__ d, const double* __restrict_
       for (int k = 0; k < MAXO; ++k)
         if (pos[k] >= 0) s += y[k];
       for (int p = p0 + MAXO; p < p1; ++p) s += Y[own_pos[p]];
-      d[i] += omega * wmult[i] * s;
+      const double nd = d[i] + omega * wmult[i] * s;
+      d[i] = nd;
+      if (d32) d32[i] = __double2float_rn(nd);
     }
   }
 }
@@ -411,7 +416,7 @@ static stm_status launch_local(Hierarchy& H, Level& L, int level, const double* 
 }
 
 stm_status vanka_step(Hierarchy& H, int g, const double* r, double* d, int transpose, bool d_is_zero,
-                      cudaStream_t s) {
+                      cudaStream_t s, bool d32_current) {
   Level& L = H.L[g];
   const double omega = H.p.omega;
   if (H.p.smoother == STM_VANKA_COLOURED) {
@@ -430,7 +435,7 @@ stm_status vanka_step(Hierarchy& H, int g, const double* r, double* d, int trans
   }
   const double* t = r;
   if (!d_is_zero) {
-    stm_status st = smoother_defect(H, g, d, r, L.t, transpose, s);
+    stm_status st = smoother_defect(H, g, d, r, L.t, transpose, s, d32_current);
     if (st != STM_OK) return st;
     t = L.t;
   }
@@ -439,8 +444,11 @@ stm_status vanka_step(Hierarchy& H, int g, const double* r, double* d, int trans
   const int blocks = (int)std::min<long long>((L.N + 255) / 256, sm_count() * 16LL);
   ProfScope ps(&H, STM_KCLASS_VANKA_COMBINE, s, 0.0, g);
   const int ow = H.p.smoother == STM_VANKA_PAPER_OVERWRITE;
-  if (L.dim == 2) k_vanka_gather<4><<<blocks, 256, 0, s>>>(d, L.Y, L.own_ptr, L.own_pos, L.last_owner, L.wmult, L.N, omega, ow);
-  else k_vanka_gather<8><<<blocks, 256, 0, s>>>(d, L.Y, L.own_ptr, L.own_pos, L.last_owner, L.wmult, L.N, omega, ow);
+  float* d32 = H.p.defect_precision == STM_F32 ? L.x32 : nullptr;
+  if (L.dim == 2)
+    k_vanka_gather<4><<<blocks, 256, 0, s>>>(d, d32, L.Y, L.own_ptr, L.own_pos, L.last_owner, L.wmult, L.N, omega, ow);
+  else
+    k_vanka_gather<8><<<blocks, 256, 0, s>>>(d, d32, L.Y, L.own_ptr, L.own_pos, L.last_owner, L.wmult, L.N, omega, ow);
   note_launch();
   STM_CUDA(cudaGetLastError());
   return STM_OK;

@@ -247,3 +247,42 @@ def test_bf16_defects_rejected():
     with pytest.raises(_lib.StmError) as e:
         Hierarchy(gpu_params(CASES["2d_k1_obs"], "bf16", defect_precision="bf16"))
     assert e.value.status == _lib.STM_ERR_INVALID_ARG
+
+
+def _composed_vcycle(h, wl, r, transpose):
+    """Algorithm 1 spelled out through the public entry points: sweeps, defect, restriction, coarse
+    solve, prolongation. Inside stm_vcycle the FP32 defects read d as rounded by the kernel that last
+    wrote it; here every defect rounds d itself, so equal results show those copies are current."""
+    G = wl.n_levels
+    zeros = lambda g: torch.zeros(h.n_dofs(g), dtype=torch.float64, device="cuda")
+    rs, ds = {G - 1: r}, {}
+    for g in range(G - 1, 0, -1):
+        d = zeros(g)
+        for _ in range(wl.nu1):
+            h.vanka_sweep(g, rs[g], d, transpose=transpose)
+        t = zeros(g)
+        h.defect(g, rs[g], d, t, transpose=transpose)
+        rs[g - 1] = zeros(g - 1)
+        h.restrict(g, t, rs[g - 1])
+        ds[g] = d
+    ds[0] = zeros(0)
+    h.coarse_solve(rs[0], ds[0], transpose=transpose)
+    for g in range(1, G):
+        h.prolongate_add(g, ds[g - 1], ds[g])
+        for _ in range(wl.nu2):
+            h.vanka_sweep(g, rs[g], ds[g], transpose=transpose)
+    return ds[G - 1]
+
+
+@pytest.mark.parametrize("defect", ["f32", "f64"])
+@pytest.mark.parametrize("smoother", ["additive", "overwrite", "coloured"])
+@pytest.mark.parametrize("transpose", [False, True])
+def test_vcycle_equals_its_public_steps(defect, smoother, transpose):
+    name = "2d_k2_obs_3lev"
+    wl = CASES[name]
+    h = _hier(name, "bf16", smoother, defect=defect)
+    r = dev(np.random.default_rng(73).standard_normal(h.n_dofs(h.finest)))
+    d = torch.zeros_like(r)
+    h.vcycle(r, d, transpose=transpose)
+    assert torch.equal(d, _composed_vcycle(h, wl, r, transpose))
+    h.close()
