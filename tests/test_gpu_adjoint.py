@@ -1,4 +1,4 @@
-"""Adjoint / gradient path on the GPU against the oracle (config 4 and small 2D/3D cases).
+"""Adjoint / gradient path on the GPU against the oracle (the 2D dG(1) channel c4_2d_k1 and small 2D/3D cases).
 
 Right-hand sides, functional weights and (dJ/dnu) x must match the oracle to rounding (1e-12).
 Autograd gradients (one forward and one adjoint FGMRES solve, rtol 1e-13) must match the oracle's
@@ -63,7 +63,7 @@ def test_rhs_functional_and_dnu_parity(name):
     h.close()
 
 
-def test_autograd_gradients_config4():
+def test_autograd_gradients_c4_2d_k1():
     from oracle import adjoint
     from paper_2107_10561_gb300.adjoint import GMGSolveFunctional, SlabFunctional
     wl = synth.WORKLOADS["c4_2d_k1"]

@@ -1,9 +1,9 @@
 """Parity at the benchmark's full sizes, in the launch configuration bench.py times.
 
-Config 2 (536,448 DoFs, 5 levels): the complete oracle is affordable, so the whole FGMRES solve is
+The 2D dG(2) channel c2_2d_k2 (536,448 DoFs, 5 levels): the complete oracle is affordable, so the whole FGMRES solve is
 compared (both to rtol 1e-10; iterations +-1, solutions within 1e-8 with FP64 inverses and 1e-7
 with BF16 inverses).
-Config 3 (962,208 DoFs, 3D): sampled outputs the oracle computes one by one: rows of J (from the
+The 3D dG(1) channel c3_3d_k1 (962,208 DoFs, 3 levels): sampled outputs the oracle computes one by one: rows of J (from the
 element matrices of the cells around a DoF), cell inverses (J_T from its 3x3x3 cell neighbourhood),
 and one smoothing step at sampled DoFs; plus properties that hold at any size (true residual of
 the converged solve, exact prolongation of a coarse polynomial).
@@ -19,7 +19,7 @@ pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 
 @pytest.mark.timeout(900)
-def test_config2_full_solve_against_oracle():
+def test_c2_2d_k2_full_solve_against_oracle():
     """Both solves to rtol 1e-10: the iterates then agree with each other to ~cond * 1e-10."""
     from oracle import solvers
     wl = synth.WORKLOADS["c2_2d_k2"]
@@ -39,7 +39,7 @@ def test_config2_full_solve_against_oracle():
 
 
 # ---------------------------------------------------------------------------------------------
-# config 3: sampled checks
+# c3_3d_k1: sampled checks
 # ---------------------------------------------------------------------------------------------
 def _fine_level(wl):
     from oracle import fem
@@ -115,7 +115,7 @@ def c3():
 
 
 @pytest.mark.timeout(600)
-def test_config3_sampled_jacobian_rows(c3):
+def test_c3_3d_k1_sampled_jacobian_rows(c3):
     wl, lev, X_lin, h, la = c3
     J = h.copy_jacobian(h.finest)
     rng = np.random.default_rng(71)
@@ -132,7 +132,7 @@ def test_config3_sampled_jacobian_rows(c3):
 
 
 @pytest.mark.timeout(600)
-def test_config3_sampled_cell_inverses_and_sweep(c3):
+def test_c3_3d_k1_sampled_cell_inverses_and_sweep(c3):
     wl, lev, X_lin, h, la = c3
     inv_all = h.copy_cell_inverses(h.finest)
     rng = np.random.default_rng(72)
@@ -164,7 +164,7 @@ def test_config3_sampled_cell_inverses_and_sweep(c3):
 
 
 @pytest.mark.timeout(600)
-def test_config3_converged_residual_and_prolongation(c3):
+def test_c3_3d_k1_converged_residual_and_prolongation(c3):
     wl, lev, X_lin, h, la = c3
     b = torch.from_numpy(lev.dofs_from_lattice(synth.random_rhs(wl))).cuda()
     x = torch.zeros_like(b)

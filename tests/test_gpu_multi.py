@@ -45,7 +45,7 @@ def test_multi_sweep_equals_single_sweeps(name, prec, nrhs):
     h.close()
 
 
-def _config5_like_rhs(h, wl, nrhs):
+def _inflow_sweep_rhs(h, wl, nrhs):
     """Columns b(U_j, nu) + c(w, w), U_j = linspace(0.2, 0.45, nrhs) (the multi-RHS workload)."""
     n = h.n_dofs()
     B = torch.empty((nrhs, n), dtype=torch.float64, device="cuda")
@@ -61,7 +61,7 @@ def test_multi_gmres_matches_single_solves(prec):
     wl = CASES["3d_k1"]
     h = gpu_hierarchy(wl, prec)
     nrhs = 32
-    B = _config5_like_rhs(h, wl, nrhs)
+    B = _inflow_sweep_rhs(h, wl, nrhs)
     X = torch.zeros_like(B)
     infos = h.gmres_solve_multi(B, X, rtol=1e-10)
     assert all(i["converged"] and i["rel_res_true"] <= 2e-10 for i in infos), infos[:3]

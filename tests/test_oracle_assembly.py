@@ -152,7 +152,7 @@ def test_element_sum_reproduces_global_matrix_structure():
             assert set(cols) <= allowed
 
 
-def test_config_sizes():
+def test_workload_sizes():
     """DoF formula N = (k+1)(d R + n_p C) on the synthetic channel levels."""
     import synth
     expect = {
