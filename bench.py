@@ -240,8 +240,8 @@ def max_over_ranks(value, dist, device):
 
 def split_precision(tok):
     """'bf16+f32d' -> ('bf16', 'f32'): cell-inverse storage and V-cycle defect precision."""
-    inv, _, d = tok.partition("+")
-    if inv not in ("f64", "f32", "bf16") or d not in ("", "f32d"):
+    inv, sep, d = tok.partition("+")
+    if inv not in ("f64", "f32", "bf16") or (sep and d != "f32d"):
         raise ValueError(f"precision {tok!r}: expected f64|f32|bf16, optionally +f32d")
     return inv, ("f32" if d else "f64")
 
