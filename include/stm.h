@@ -125,8 +125,8 @@ stm_status stm_defect(stm_hierarchy* h, int level, const double* r_dev, const do
                       int transpose, void* stream);
 
 /* One smoothing step d <- S(d, r) on level g >= 1 with params.smoother and params.omega
- * (Eq. LocVanka with damping; residual r - J_g d recomputed inside). transpose = 1 smooths for
- * J_g^T with the transposed cell inverses. */
+ * (Eq. LocVanka with damping; residual r - J_g d recomputed inside, as stm_defect computes it, in
+ * params.defect_precision). transpose = 1 smooths for J_g^T with the transposed cell inverses. */
 stm_status stm_vanka_sweep(stm_hierarchy* h, int level, const double* r_dev, double* d_dev,
                            int transpose, void* stream);
 
@@ -141,7 +141,9 @@ stm_status stm_prolongate_add(stm_hierarchy* h, int level, const double* coarse_
 stm_status stm_coarse_solve(stm_hierarchy* h, const double* r_dev, double* d_dev, int transpose,
                             void* stream);
 
-/* One V(nu1,nu2)-cycle (Algorithm 1) on the finest level with zero initial guess: d = M^{-1} r. */
+/* One V(nu1,nu2)-cycle (Algorithm 1) on the finest level with zero initial guess: d = M^{-1} r.
+ * Equal, bit for bit, to its steps composed through stm_vanka_sweep, stm_defect, stm_restrict,
+ * stm_coarse_solve and stm_prolongate_add. */
 stm_status stm_vcycle(stm_hierarchy* h, const double* r_dev, double* d_dev, int transpose,
                       void* stream);
 
