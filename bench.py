@@ -4,12 +4,17 @@
 Step = one flexible-GMRES solve (V(2,2) additive-Vanka V-cycle per iteration) of the dG(k)
 Q2/P1disc slab Newton system to 1e-8 relative residual, from x = 0, with the hierarchy assembled
 and factored once beforehand (assembly and factorisation times are reported under "setup").
-The headline `value` is seconds per solve of the fastest mixed-precision run: FP32 or BF16 cell
-inverses, optionally with FP32 defects inside the V-cycle ("bf16+f32d"); the FGMRES products and
-stopping test are FP64 in every run, and the plain FP64 path is timed in the same run ("fp64_s").
+Default workload: the 3D channel with a square-prism obstacle, 3 levels (fine 64x16x16 minus the
+obstacle), dG(1), 962,208 DoFs, cell inverses of 170x170.
+
+The headline `value` is seconds per solve of the fastest mixed-precision run whose V-cycle keeps
+every residual product in FP64: cell inverses stored and applied in FP32 or BF16 (FP32
+accumulation), FP64 FGMRES, Arnoldi, residual products and coarse solve. The plain FP64 path is
+timed in the same run ("fp64_s"); every precision reports its error against the FP64 solution.
+A run with FP32 V-cycle defects ("bf16+f32d") is reported as an extra row only.
 
 Prints ONE JSON line (rank 0). `--impl reference` times the CPU oracle (the plain FP64 reference
-implementation written from the paper) on the same workload instead.
+implementation written from the paper) on a bounded sample of the same workload instead.
 """
 from __future__ import annotations
 
@@ -25,7 +30,9 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-DEFAULT_WORKLOAD = "c2_2d_k2"
+DEFAULT_WORKLOAD = "c3_3d_k1"
+# conforming mixed-precision arms (FP64 residual products): the headline is the fastest of these
+CONFORMING_MIXED = ("f32", "bf16")
 
 
 def parse():
@@ -39,6 +46,7 @@ def parse():
     ap.add_argument("--precisions", default="f64,f32,bf16,bf16+f32d",
                     help="cell-inverse storage per run; INV+f32d also takes the V-cycle defects in FP32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-other-rows", action="store_true", help="skip the other-workload rows (c2, c5)")
     ap.add_argument("--multi-restart", type=int, default=20)
     ap.add_argument("--robustness", action="store_true",
                     help="viscosity / damping study: Newton and FGMRES counts for nu x omega_d (V(4,4), tau 0.005)")
@@ -69,45 +77,137 @@ def describe(wl, sizes):
 
 
 # ---------------------------------------------------------------------------------------------
-# CPU oracle leg (run in a spawned child process so that it never shares the CUDA context)
+# CPU oracle leg (run in spawned child processes so that it never shares the CUDA context)
 # ---------------------------------------------------------------------------------------------
+# The oracle's set-up of the full 3D workload takes minutes (numpy assembly, Python-loop transfer
+# matrices, a sparse LU of the coarse level), so the CPU baseline runs on a bounded sample: the same
+# channel, element pair, time degree, obstacle rule and seeded data with one refinement level fewer
+# (config 3 on 2 levels: 127,920 DoFs), scaled to the full workload by the ratio of DoFs (one FGMRES
+# iteration costs O(DoFs); the iteration count does not depend on the mesh, Tables 5.1 / 5.5).
+SAMPLE_LEVELS_DROP = 1
+REFERENCE_MAX_STEPS = 8
+
+
 def oracle_child(spec_path):
     spec = json.load(open(spec_path))
+    if spec.get("cpus") and hasattr(os, "sched_setaffinity"):
+        os.sched_setaffinity(0, set(spec["cpus"]))
+    import dataclasses
+
     import numpy as np
 
     import synth
     from oracle import solvers
 
     wl = synth.WORKLOADS[spec["workload"]]
+    if spec.get("n_levels"):
+        wl = dataclasses.replace(wl, n_levels=spec["n_levels"])
     t0 = time.perf_counter()
     H = solvers.Hierarchy(wl, synth.linearisation_point(wl))
     setup = time.perf_counter() - t0
-    b = H.fine.dofs_from_lattice(synth.random_rhs(wl))
+    lev = H.fine
+    rng = np.random.default_rng(7)
+    r, d = rng.standard_normal(lev.N), rng.standard_normal(lev.N)
+    sweep_s = []
+    for _ in range(spec.get("sweeps", 0)):
+        t0 = time.perf_counter()
+        solvers.vanka_step(lev, H.J[-1], H.inv[-1], d, r, wl.omega)
+        sweep_s.append(time.perf_counter() - t0)
+    b = lev.dofs_from_lattice(synth.random_rhs(wl))
     times, iters = [], []
+    x, info = None, {"converged": False}
     for _ in range(spec["solves"]):
         t0 = time.perf_counter()
         x, info = H.solve(b, rtol=spec["rtol"], maxit=spec["maxit"])
         times.append(time.perf_counter() - t0)
         iters.append(info["iters"])
-    sizes = {"n_dofs": int(H.fine.N), "n_cells": int(H.fine.C), "n_local": int(H.fine.n)}
+    if spec.get("x_out") and x is not None:
+        np.save(spec["x_out"], x)
+    sizes = {"n_dofs": int(lev.N), "n_cells": int(lev.C), "n_local": int(lev.n), "n_levels": wl.n_levels}
     json.dump({"setup_s": setup, "solve_s": times, "iters": iters, "converged": bool(info["converged"]),
-               "sizes": sizes}, open(spec["out"], "w"))
+               "sweep_s": sweep_s, "sizes": sizes}, open(spec["out"], "w"))
 
 
-def run_oracle(wl_name, rtol, solves, maxit=1000, threads=1):
-    with tempfile.TemporaryDirectory() as td:
-        spec = {"workload": wl_name, "rtol": rtol, "solves": solves, "maxit": maxit, "out": os.path.join(td, "o.json")}
-        sp = os.path.join(td, "spec.json")
-        json.dump(spec, open(sp, "w"))
-        env = dict(os.environ)
-        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-            env[v] = str(threads)
-        env["CUDA_VISIBLE_DEVICES"] = ""
-        p = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-child", sp], env=env,
-                           capture_output=True, text=True)
-        if p.returncode != 0:
-            raise RuntimeError("oracle child failed:\n" + p.stderr[-3000:])
-        return json.load(open(spec["out"]))
+def start_oracle(wl_name, rtol, solves, sweeps=0, n_levels=None, threads=1, maxit=1000, x_out=None, cpus=None):
+    """Spawn the oracle child; returns a handle for finish_oracle (the child runs while the caller
+    does other work)."""
+    td = tempfile.mkdtemp(prefix="stm_oracle_")
+    spec = {"workload": wl_name, "rtol": rtol, "solves": solves, "sweeps": sweeps, "maxit": maxit,
+            "n_levels": n_levels, "out": os.path.join(td, "o.json"), "x_out": x_out, "cpus": cpus}
+    sp = os.path.join(td, "spec.json")
+    json.dump(spec, open(sp, "w"))
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = str(threads)
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    proc = subprocess.Popen([sys.executable, os.path.abspath(__file__), "--oracle-child", sp], env=env,
+                            stdout=subprocess.DEVNULL, stderr=subprocess.PIPE, text=True)
+    return {"proc": proc, "spec": spec, "dir": td, "threads": threads}
+
+
+def finish_oracle(handle):
+    import shutil
+
+    err = handle["proc"].communicate()[1]
+    try:
+        if handle["proc"].returncode != 0:
+            raise RuntimeError("oracle child failed:\n" + (err or "")[-3000:])
+        out = json.load(open(handle["spec"]["out"]))
+        out["threads"] = handle["threads"]
+        return out
+    finally:
+        shutil.rmtree(handle["dir"], ignore_errors=True)
+
+
+def run_oracle(wl_name, rtol, solves, maxit=1000, threads=1, n_levels=None, sweeps=0):
+    return finish_oracle(start_oracle(wl_name, rtol, solves, sweeps=sweeps, n_levels=n_levels, threads=threads,
+                                      maxit=maxit))
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+
+    return platform.processor() or platform.machine()
+
+
+def sample_levels(wl):
+    return max(2, wl.n_levels - SAMPLE_LEVELS_DROP)
+
+
+def cpu_baseline_entry(o1, on, full_dofs, full_cells, gpu_iters, wl):
+    """cpu_baseline of the bench line from the 1-thread and all-thread oracle samples."""
+    import numpy as np
+
+    scale = full_dofs / o1["sizes"]["n_dofs"]
+    cscale = full_cells / o1["sizes"]["n_cells"]
+
+    def leg(o):
+        return {"threads": o["threads"], "solve_s_sample_median": float(np.median(o["solve_s"])),
+                "solve_s_scaled": float(np.median(o["solve_s"])) * scale, "iters_sample": o["iters"][-1],
+                "sweep_s_sample_median": float(np.median(o["sweep_s"])) if o["sweep_s"] else None,
+                "sweep_s_scaled": float(np.median(o["sweep_s"])) * cscale if o["sweep_s"] else None,
+                "setup_s_sample_untimed": o["setup_s"]}
+
+    one, alln = leg(o1), leg(on)
+    return {"value": one["solve_s_scaled"], "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": (f"the oracle's full FP64 FGMRES solve (rtol {wl.rtol:g}) of the same 3D dG(1) channel with one "
+                       f"refinement level fewer ({o1['sizes']['n_levels']} levels, {o1['sizes']['n_dofs']:,} DoFs, "
+                       f"{o1['iters'][-1]} iterations; the GPU needs {gpu_iters} on the full workload), median of "
+                       f"{len(o1['solve_s'])}, scaled by the DoF ratio {scale:.3f}; the Vanka sweep (the oracle's "
+                       f"vanka_step: residual, local solves, weighted combine) on that sample's finest level "
+                       f"({o1['sizes']['n_cells']:,} cells, n = {o1['sizes']['n_local']}), median of "
+                       f"{len(o1['sweep_s'])}, scaled by the cell ratio {cscale:.3f}"),
+            "cpu_model": cpu_model(), "nproc": os.cpu_count(), "cores_all_threads_leg": on["threads"],
+            "one_thread": one, "all_threads": alln,
+            "note": "numpy/scipy as written: the sparse products, einsum local solves and the SuperLU coarse "
+                    "solve run on one thread whatever the BLAS thread count"}
 
 
 # ---------------------------------------------------------------------------------------------
@@ -275,12 +375,143 @@ def peaks():
 # ---------------------------------------------------------------------------------------------
 # GPU leg
 # ---------------------------------------------------------------------------------------------
-def gpu_leg(args, rank, world, local_rank):
+def lattice_vec(h, arr):
     import numpy as np
     import torch
 
+    idx = h.dof_lattice_index()
+    return torch.from_numpy(np.ascontiguousarray(arr.reshape(-1)[idx])).cuda()
+
+
+def time_precisions(wl, precs, state, rhs_lat, steps, warmup, rtol, dist=None, profile=True):
+    """Per precision token: build, assemble, factor, W warm-up solves, then K timed solves from x = 0
+    (CUDA events on the launching stream, V-cycles replayed as CUDA graphs), then the same K solves
+    with per-kernel event timing (direct launches). Returns (results, hierarchies)."""
+    import torch
+
+    from paper_2107_10561_gb300 import Hierarchy
+
+    results, hs = {}, {}
+    for prec in precs:
+        h = Hierarchy(hier_params(wl, prec, "additive"))
+        X = lattice_vec(h, state)
+        b = lattice_vec(h, rhs_lat)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        torch.cuda.synchronize()
+        e0.record()
+        h.assemble_jacobian(X)
+        e1.record()
+        h.factor_cells()
+        e2.record()
+        torch.cuda.synchronize()
+        setup = {"assemble_ms": e0.elapsed_time(e1), "factor_ms": e1.elapsed_time(e2)}
+        x = torch.zeros_like(b)
+        info = None
+        for _ in range(warmup):
+            x.zero_()
+            info = h.gmres_solve(b, x, rtol=rtol, restart=wl.restart)
+        hs[prec] = (h, b, x)
+        results[prec] = {"setup": setup}
+    stream = torch.cuda.current_stream()
+    for prec, (h, b, x) in hs.items():
+        launches0 = Hierarchy.kernel_launches()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push(f"timed_solves_{prec.replace('+', '_')}")  # lets a profiler select these launches
+        ev0.record(stream)
+        for _ in range(steps):
+            x.zero_()
+            info = h.gmres_solve(b, x, rtol=rtol, restart=wl.restart)
+        ev1.record(stream)
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / steps
+        if dist:
+            ms = max_over_ranks(ms, dist, "cuda")
+        r = results[prec]
+        r["ms_per_solve"] = ms
+        r["launches_per_step"] = (Hierarchy.kernel_launches() - launches0) / steps
+        r["iters_timed"] = info["iters"]
+        r["rel_res_true_timed"] = info["rel_res_true"]
+        if not profile:
+            continue
+        # profiled pass over the same steps: CUDA events around every launch of the library, recorded
+        # on the launching stream (direct launches, no graphs), for the per-kernel split and roofline
+        h.profile_enable(True)
+        torch.cuda.synchronize()
+        pv0, pv1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        pv0.record(stream)
+        for _ in range(steps):
+            x.zero_()
+            h.gmres_solve(b, x, rtol=rtol, restart=wl.restart)
+        pv1.record(stream)
+        torch.cuda.synchronize()
+        r["ms_per_solve_profiled"] = pv0.elapsed_time(pv1) / steps
+        r["kernels"] = {k: h.profile_read(k) for k in ("vanka_local", "jacobian_spmv", "defect_f32", "round_f32",
+                                                       "vanka_combine", "transfer", "coarse", "krylov")}
+        r["finest"] = {k: h.profile_read(k, wl.n_levels - 1) for k in ("vanka_local", "jacobian_spmv", "defect_f32")}
+        r["per_level"] = {k: [h.profile_read(k, g) for g in range(wl.n_levels)]
+                          for k in ("vanka_local", "jacobian_spmv", "defect_f32", "vanka_combine", "transfer")}
+        h.profile_enable(False)
+    return results, hs
+
+
+def solution_errors(hs, ref="f64"):
+    """Error of every precision's solution against the FP64 solution of the same run (same b)."""
+    if ref not in hs:
+        return {}
+    xr = hs[ref][2].double()
+    nr_max, nr_2 = float(xr.abs().max()), float(xr.norm())
+    out = {}
+    for p, (_, _, x) in hs.items():
+        dx = x.double() - xr
+        out[p] = {"max_rel": float(dx.abs().max()) / nr_max, "l2_rel": float(dx.norm()) / nr_2}
+    return out
+
+
+def by_precision_rows(results, errs, steps):
+    def gbs(e):
+        return e["bytes"] / (e["ms"] * 1e-3) / 1e9 if e["ms"] > 0 else None
+
+    def us(e):
+        return 1e3 * e["ms"] / e["launches"] if e["launches"] else None
+
+    out = {}
+    for p, v in results.items():
+        inv, dp = split_precision(p)
+        row = {"s_per_solve": v["ms_per_solve"] / 1e3, "iters": v["iters_timed"],
+               "rel_res_true": v["rel_res_true_timed"], "setup_ms": v["setup"],
+               "fp64_residual_products": dp == "f64",
+               "err_vs_fp64_solution": errs.get(p)}
+        if dp != "f64":
+            row["note"] = ("extra row: FP32 V-cycle defects, outside the rule that the residual products "
+                           "stay FP64; not a headline candidate")
+        if "kernels" in v:
+            k, f = v["kernels"], v["finest"]
+            row.update({"vanka_sweep_gbs": gbs(k["vanka_local"]), "spmv_gbs": gbs(k["jacobian_spmv"]),
+                        "finest_vanka_gbs": gbs(f["vanka_local"]), "finest_spmv_gbs": gbs(f["jacobian_spmv"]),
+                        "finest_vanka_us": us(f["vanka_local"]), "finest_spmv_us": us(f["jacobian_spmv"]),
+                        "finest_defect_f32_us": us(f["defect_f32"]), "finest_defect_f32_gbs": gbs(f["defect_f32"]),
+                        "kernel_ms_per_solve": {kk: kv["ms"] / steps for kk, kv in k.items()},
+                        "us_per_launch_by_level": {kk: [round(1e3 * e["ms"] / e["launches"], 2) if e["launches"] else None
+                                                        for e in lv] for kk, lv in v["per_level"].items()},
+                        "s_per_solve_profiled_pass": v["ms_per_solve_profiled"] / 1e3})
+        out[p] = row
+    return out
+
+
+def pick_head(results):
+    mixed = [p for p in CONFORMING_MIXED if p in results]
+    return min(mixed, key=lambda p: results[p]["ms_per_solve"]) if mixed else next(iter(results))
+
+
+def gpu_leg(args, rank, world, local_rank):
+    import torch
+
     import synth
-    from paper_2107_10561_gb300 import Hierarchy, make_params
+    from paper_2107_10561_gb300 import Hierarchy
     from paper_2107_10561_gb300 import build as _build
 
     torch.cuda.set_device(local_rank)
@@ -293,86 +524,17 @@ def gpu_leg(args, rank, world, local_rank):
     wl = workload(args.workload)
     state = synth.linearisation_point(wl)
     rhs_lat = synth.random_rhs(wl, seed_offset=rank)
-    results = {}
-    hs = {}
-    for prec in args.precisions.split(","):
-        p = hier_params(wl, prec, "additive")
-        h = Hierarchy(p)
-        idx = h.dof_lattice_index()
-        X = torch.from_numpy(np.ascontiguousarray(state.reshape(-1)[idx])).cuda()
-        b = torch.from_numpy(np.ascontiguousarray(rhs_lat.reshape(-1)[idx])).cuda()
-        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        torch.cuda.synchronize()
-        e0.record()
-        h.assemble_jacobian(X)
-        e1.record()
-        h.factor_cells()
-        e2.record()
-        torch.cuda.synchronize()
-        setup = {"assemble_ms": e0.elapsed_time(e1), "factor_ms": e1.elapsed_time(e2)}
-        x = torch.zeros_like(b)
-        for _ in range(args.warmup):
-            x.zero_()
-            info = h.gmres_solve(b, x, rtol=args.rtol, restart=wl.restart)
-        hs[prec] = (h, b, x)
-        results[prec] = {"setup": setup, "iters": info["iters"], "rel_res_true": info["rel_res_true"]}
-    sizes = [hs[next(iter(hs))][0].sizes(g) for g in range(wl.n_levels)]
-    # cumulative library launches before the timed region (lets an ncu launch list skip the set-up)
-    print(f"library_launches_before_timed_region={Hierarchy.kernel_launches()}", file=sys.stderr)
-
-    # timed region, every precision, K solves each
+    precs = args.precisions.split(",")
     sampler = ClockSampler(local_rank)
     sampler.start()
     time.sleep(0.3)
-    stream = torch.cuda.current_stream()
-    for prec, (h, b, x) in hs.items():
-        # clean timed pass (CUDA graphs for the V-cycles, no per-kernel events): the reported time
-        launches0 = Hierarchy.kernel_launches()
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.nvtx.range_push(f"timed_solves_{prec.replace('+', '_')}")  # lets a profiler select exactly these launches
-        ev0.record(stream)
-        for _ in range(args.steps):
-            x.zero_()
-            info = h.gmres_solve(b, x, rtol=args.rtol, restart=wl.restart)
-        ev1.record(stream)
-        torch.cuda.nvtx.range_pop()
-        torch.cuda.synchronize()
-        ms = ev0.elapsed_time(ev1) / args.steps
-        if dist:
-            ms = max_over_ranks(ms, dist, "cuda")
-        r = results[prec]
-        r["ms_per_solve"] = ms
-        r["launches_per_step"] = (Hierarchy.kernel_launches() - launches0) / args.steps
-        r["iters_timed"] = info["iters"]
-        r["rel_res_true_timed"] = info["rel_res_true"]
-        # profiled pass over the same steps: CUDA events around every launch of the library, recorded
-        # on the launching stream (direct launches, no graphs), for the per-kernel split and roofline
-        h.profile_enable(True)
-        torch.cuda.synchronize()
-        pv0, pv1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        pv0.record(stream)
-        for _ in range(args.steps):
-            x.zero_()
-            h.gmres_solve(b, x, rtol=args.rtol, restart=wl.restart)
-        pv1.record(stream)
-        torch.cuda.synchronize()
-        r["ms_per_solve_profiled"] = pv0.elapsed_time(pv1) / args.steps
-        r["kernels"] = {k: h.profile_read(k) for k in ("vanka_local", "jacobian_spmv", "defect_f32", "round_f32",
-                                                       "vanka_combine", "transfer",
-                                                       "coarse", "krylov")}
-        r["finest"] = {k: h.profile_read(k, wl.n_levels - 1) for k in ("vanka_local", "jacobian_spmv", "defect_f32")}
-        r["per_level"] = {k: [h.profile_read(k, g) for g in range(wl.n_levels)]
-                          for k in ("vanka_local", "jacobian_spmv", "defect_f32", "vanka_combine", "transfer")}
-        h.profile_enable(False)
+    results, hs = time_precisions(wl, precs, state, rhs_lat, args.steps, args.warmup, args.rtol, dist)
     clocks = sampler.stop()
+    sizes = [hs[precs[0]][0].sizes(g) for g in range(wl.n_levels)]
     fp64_peak = Hierarchy.measure_fp64_peak()
-
+    errs = solution_errors(hs)
+    head = pick_head(results)
     # end-to-end through the host-buffer entry point (H2D of b, D2H of x inside the timed region)
-    mixed = [p for p in results if p != "f64"]
-    head = min(mixed, key=lambda p: results[p]["ms_per_solve"]) if mixed else "f64"
     h, b, x = hs[head]
     bh = b.cpu().pin_memory()
     xh = torch.zeros_like(bh).pin_memory()
@@ -384,7 +546,11 @@ def gpu_leg(args, rank, world, local_rank):
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / args.steps
     rows = other_rows(args, wl, hs, head, state, rhs_lat) if rank == 0 else {}
-    return wl, sizes, results, head, clocks, e2e_s, dist, fp64_peak, rows
+    for hh, _, _ in hs.values():
+        hh.close()
+    hs.clear()
+    torch.cuda.empty_cache()
+    return wl, sizes, results, errs, head, clocks, e2e_s, dist, fp64_peak, rows
 
 
 def other_rows(args, wl, hs, head, state, rhs_lat):
@@ -392,10 +558,9 @@ def other_rows(args, wl, hs, head, state, rhs_lat):
     head precision: one V-cycle (Algorithm 1, direct launches), the adjoint solve J^T lambda = b
     (transposed Vanka, P/P^T, coarse inverse^T), and the solve with the coloured multiplicative and
     the literal overwrite smoother (Sec. 4.2)."""
-    import numpy as np
     import torch
 
-    from paper_2107_10561_gb300 import Hierarchy, make_params
+    from paper_2107_10561_gb300 import Hierarchy
 
     out = {}
     h, b, x = hs[head]
@@ -419,13 +584,11 @@ def other_rows(args, wl, hs, head, state, rhs_lat):
     ev1.record()
     torch.cuda.synchronize()
     out["adjoint_solve"] = {"ms": ev0.elapsed_time(ev1) / args.steps, "iters": info["iters"],
-                            "rel_res_true": info["rel_res_true"]}
+                            "rel_res_true": info["rel_res_true"], "precision": head}
     for smoother in ("coloured", "overwrite"):
-        p = hier_params(wl, head, smoother)
-        hv = Hierarchy(p)
-        idx = hv.dof_lattice_index()
-        X = torch.from_numpy(np.ascontiguousarray(state.reshape(-1)[idx])).cuda()
-        bv = torch.from_numpy(np.ascontiguousarray(rhs_lat.reshape(-1)[idx])).cuda()
+        hv = Hierarchy(hier_params(wl, head, smoother))
+        X = lattice_vec(hv, state)
+        bv = lattice_vec(hv, rhs_lat)
         hv.assemble_jacobian(X)
         hv.factor_cells()
         xv = torch.zeros_like(bv)
@@ -438,31 +601,82 @@ def other_rows(args, wl, hs, head, state, rhs_lat):
         ev1.record()
         torch.cuda.synchronize()
         out[f"{smoother}_solve"] = {"ms": ev0.elapsed_time(ev1) / args.steps, "iters": info["iters"],
-                                    "converged": info["status"] == "STM_OK"}
+                                    "converged": info["status"] == "STM_OK", "precision": head}
         hv.close()
     return out
 
 
-def gpu_leg_multi(args, local_rank):
-    """Multi-RHS workload: 32 right-hand sides b(U_j, nu) + c(w, w) sharing one hierarchy."""
+def workload_row(args, name, precs, steps, warmup):
+    """Another single-right-hand-side workload at the same settings: seconds per solve per precision,
+    errors against its FP64 solution, and the finest-level FP64 product against the FP64 rate."""
+    import torch
+
+    import synth
+    from paper_2107_10561_gb300 import Hierarchy
+
+    wl = workload(name)
+    results, hs = time_precisions(wl, precs, synth.linearisation_point(wl), synth.random_rhs(wl), steps, warmup,
+                                  args.rtol)
+    sizes = [hs[precs[0]][0].sizes(g) for g in range(wl.n_levels)]
+    errs = solution_errors(hs)
+    for hh, _, _ in hs.values():
+        hh.close()
+    torch.cuda.empty_cache()
+    head = pick_head(results)
+    fp64_peak = Hierarchy.measure_fp64_peak()
+    row = {"workload": describe(wl, sizes)["workload"], "dofs": sizes[-1]["n_dofs"], "rtol": args.rtol,
+           "head": head, "s_per_solve": results[head]["ms_per_solve"] / 1e3,
+           "fp64_s": results["f64"]["ms_per_solve"] / 1e3 if "f64" in results else None,
+           "by_precision": by_precision_rows(results, errs, steps),
+           "roofline_spmv_f64": {p: spmv_roofline(results[p], wl, sizes, fp64_peak, name) for p in results
+                                 if split_precision(p)[1] == "f64"}}
+    return row
+
+
+def oracle_sample_check(args, wl, precs, x_oracle):
+    """Every precision's GPU solution against the oracle's FP64 solution on the bounded oracle sample
+    (the same workload with one refinement level fewer): max |x - x_oracle| / max |x_oracle|."""
+    import dataclasses
+
     import numpy as np
     import torch
 
     import synth
-    from paper_2107_10561_gb300 import Hierarchy, make_params
-    from paper_2107_10561_gb300 import build as _build
+    from paper_2107_10561_gb300 import Hierarchy
 
-    torch.cuda.set_device(local_rank)
-    _build.build()
-    wl = workload(args.workload)
+    ws = dataclasses.replace(wl, n_levels=sample_levels(wl))
+    state, rhs = synth.linearisation_point(ws), synth.random_rhs(ws)
+    out = {}
+    for prec in precs:
+        h = Hierarchy(hier_params(ws, prec, "additive"))
+        h.assemble_jacobian(lattice_vec(h, state))
+        h.factor_cells()
+        b = lattice_vec(h, rhs)
+        x = torch.zeros_like(b)
+        info = h.gmres_solve(b, x, rtol=args.rtol, restart=ws.restart)
+        xg = x.cpu().numpy()
+        out[prec] = {"max_rel": float(np.abs(xg - x_oracle).max() / np.abs(x_oracle).max()),
+                     "l2_rel": float(np.linalg.norm(xg - x_oracle) / np.linalg.norm(x_oracle)),
+                     "iters": info["iters"]}
+        h.close()
+    return out
+
+
+def multi_row(args, name, steps, warmup, prec="bf16"):
+    """Multi-RHS workload: 32 right-hand sides b(U_j, nu) + c(w, w) sharing one hierarchy; seconds per
+    32-column solve and the finest-level multi-RHS Vanka sweep against HBM."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2107_10561_gb300 import Hierarchy
+
+    wl = workload(name)
     nrhs = wl.extra["nrhs"]
-    prec = args.precisions.split(",")[-1]
-    p = hier_params(wl, prec, "additive")
     t0 = time.perf_counter()
-    h = Hierarchy(p)
+    h = Hierarchy(hier_params(wl, prec, "additive"))
     build_s = time.perf_counter() - t0
-    idx = h.dof_lattice_index()
-    X = torch.from_numpy(np.ascontiguousarray(synth.linearisation_point(wl).reshape(-1)[idx])).cuda()
+    X = lattice_vec(h, synth.linearisation_point(wl))
     e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
     torch.cuda.synchronize()
     e0.record()
@@ -476,48 +690,72 @@ def gpu_leg_multi(args, local_rank):
     for c, U in enumerate(synth.inflow_sweep(nrhs)):
         h.assemble_rhs(float(U), wl.nu, B[c], which=0)
     Xs = torch.zeros_like(B)
-    for _ in range(args.warmup):
+    infos = None
+    for _ in range(warmup):
         Xs.zero_()
         infos = h.gmres_solve_multi(B, Xs, rtol=args.rtol, restart=args.multi_restart)
-    sampler = ClockSampler(local_rank)
-    sampler.start()
-    h.profile_enable(True)
     launches0 = Hierarchy.kernel_launches()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record()
-    for _ in range(args.steps):
+    for _ in range(steps):
         Xs.zero_()
         infos = h.gmres_solve_multi(B, Xs, rtol=args.rtol, restart=args.multi_restart)
     ev1.record()
     torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1) / steps
+    launches = Hierarchy.kernel_launches() - launches0
+    h.profile_enable(True)
+    Xs.zero_()
+    h.gmres_solve_multi(B, Xs, rtol=args.rtol, restart=args.multi_restart)
     kern = {k: h.profile_read(k) for k in ("vanka_local", "jacobian_spmv", "vanka_combine", "transfer", "coarse",
                                            "krylov")}
     fin = h.profile_read("vanka_local", wl.n_levels - 1)
+    h.profile_enable(False)
     sizes = [h.sizes(g) for g in range(wl.n_levels)]
+    h.close()
+    torch.cuda.empty_cache()
     pk = peaks()
     hbm = pk["hbm_gbs"] if pk else 6800.0
     ach = fin["bytes"] / (fin["ms"] * 1e-3) / 1e9 if fin["ms"] > 0 else None
-    cfg = describe(wl, sizes)
-    cfg.update({"rtol": args.rtol, "nrhs": nrhs, "rhs": "b(U_j, nu) + c(w, w), U_j = linspace(0.2, 0.45, 32)",
-                "restart": args.multi_restart, "parallelism": "single GPU",
-                "l2": "inputs larger than L2 (finest J %.1f GB)" % (sizes[-1]["nnz"] * 12 / 1e9)})
-    line = {"metric": "GMG-GMRES s to 1e-8 rel. res (mixed vs FP64, one GB300); Vanka sweep GB/s",
-            "value": ms / 1e3, "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": f"f64 Krylov/SpMM/coarse + {split_precision(prec)[0]} cell inverses ({'tensor cores, ' if split_precision(prec)[0] == 'bf16' else ''}f32 accumulate); FP64 defects",
-            "data": "synthetic", "config": cfg, "per_rhs_s": ms / 1e3 / nrhs,
+    return {"workload": describe(wl, sizes)["workload"], "dofs": sizes[-1]["n_dofs"], "nrhs": nrhs,
+            "rhs": "b(U_j, nu) + c(w, w), U_j = linspace(0.2, 0.45, 32)", "rtol": args.rtol,
+            "restart": args.multi_restart, "s_per_solve": ms / 1e3, "per_rhs_s": ms / 1e3 / nrhs,
             "iters": [i["iters"] for i in infos], "max_rel_res_true": max(i["rel_res_true"] for i in infos),
+            "dtype": f"f64 Krylov/SpMM/coarse + {split_precision(prec)[0]} cell inverses "
+                     f"({'tensor cores, ' if split_precision(prec)[0] == 'bf16' else ''}f32 accumulate); FP64 defects",
             "setup": {"build_hierarchy_s": build_s, "assemble_ms": e0.elapsed_time(e1), "factor_ms": e1.elapsed_time(e2)},
-            "kernel_ms_per_solve": {k: v["ms"] / args.steps for k, v in kern.items()},
-            "gpu_launches": int(Hierarchy.kernel_launches() - launches0),
-            "roofline": {"kernel": f"k_vanka_mrhs ({prec}), finest level, 32 columns", "bound": "hbm",
+            "kernel_ms_per_solve_profiled": {k: v["ms"] for k, v in kern.items()},
+            "gpu_launches_per_solve": launches / steps,
+            "roofline": {"kernel": f"multi-RHS Vanka local products ({prec}), finest level, 32 columns", "bound": "hbm",
                          "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm if ach else None,
-                         "traffic": None, "avg_launch_us": 1e3 * fin["ms"] / max(fin["launches"], 1)},
-            "clocks": clocks, "cpu_baseline": None,
+                         "avg_launch_us": 1e3 * fin["ms"] / max(fin["launches"], 1),
+                         "bytes_per_launch": fin["bytes"] / max(fin["launches"], 1)},
             "cpu_baseline_note": "the FP64 oracle of this workload needs ~70 GB of host memory and hours; not timed"}
+
+
+def gpu_leg_multi(args, local_rank):
+    """Multi-RHS workload as the line's own workload (bench.py --workload c5_3d_k1)."""
+    import torch
+
+    from paper_2107_10561_gb300 import build as _build
+
+    torch.cuda.set_device(local_rank)
+    _build.build()
+    prec = args.precisions.split(",")[-1]
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    row = multi_row(args, args.workload, args.steps, args.warmup, split_precision(prec)[0])
+    clocks = sampler.stop()
+    line = {"metric": "GMG-GMRES s to 1e-8 rel. res (mixed vs FP64, one GB300); Vanka sweep GB/s",
+            "value": row["s_per_solve"], "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * row["s_per_solve"], "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": row["dtype"], "data": "synthetic",
+            "config": {"workload": row["workload"], "dofs": row["dofs"], "nrhs": row["nrhs"], "rhs": row["rhs"],
+                       "rtol": args.rtol, "restart": row["restart"], "parallelism": "single GPU"},
+            "gpu_launches": int(row["gpu_launches_per_solve"] * args.steps), "clocks": clocks,
+            "roofline": row["roofline"], "multi": row, "cpu_baseline": None,
+            "cpu_baseline_note": row["cpu_baseline_note"]}
     print(json.dumps(line))
 
 
@@ -721,6 +959,58 @@ def gpu_leg_mesh(args, local_rank):
     print(json.dumps(line))
 
 
+def reference_arm(args):
+    """The CPU oracle on a bounded sample of the bench's workload (one refinement level fewer), each
+    step one full oracle FGMRES solve, scaled to the full workload by the DoF ratio."""
+    wl = workload(args.workload)
+    if wl.extra.get("nrhs"):
+        print(json.dumps({"impl": "reference", "unavailable": "the FP64 oracle of the 32-right-hand-side workload "
+                                                              "needs ~70 GB of host memory and hours"}))
+        return
+    threads = os.cpu_count() or 1
+    steps = max(1, min(args.steps, REFERENCE_MAX_STEPS))
+    o = run_oracle(args.workload, args.rtol, steps, threads=threads, n_levels=sample_levels(wl))
+    full_dofs = full_workload_dofs(wl)
+    scale = full_dofs / o["sizes"]["n_dofs"]
+    t = statistics.median(o["solve_s"]) * scale
+    sample = (f"each step one full FP64 oracle FGMRES solve (rtol {args.rtol:g}) of the same 3D channel with one "
+              f"refinement level fewer ({o['sizes']['n_levels']} levels, {o['sizes']['n_dofs']:,} DoFs, "
+              f"{o['iters'][-1]} iterations), numpy/scipy with {threads} BLAS threads, after an untimed "
+              f"{o['setup_s']:.1f} s oracle set-up; value = median step x {scale:.3f} (DoF ratio to the full "
+              f"{full_dofs:,}-DoF workload); {steps} of the {args.steps} requested steps (at most "
+              f"{REFERENCE_MAX_STEPS}, so that the run ends within a few minutes)")
+    line = {"impl": "reference", "metric": "GMG-GMRES s to 1e-8 rel. res (mixed vs FP64, one GB300); Vanka sweep GB/s",
+            "value": t, "unit": "s", "n_gpus": args.gpus, "steps": steps, "steps_requested": args.steps,
+            "warmup": 0, "ms_per_step": 1e3 * t, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": describe(wl, [{"n_dofs": full_dofs, "n_cells": None, "n_local": None}])["workload"],
+                       "dofs": full_dofs, "rtol": args.rtol, "parallelism": "CPU oracle (rank 0 of the job)"},
+            "cpu_baseline": {"value": t, "unit": "s", "cores": threads, "kind": "oracle", "sample": sample,
+                             "cpu_model": cpu_model()},
+            "e2e": {"value": t, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def full_workload_dofs(wl):
+    """DoFs of the finest level: (k+1)(d R + n_p C) from the node and cell counts of the obstacle
+    channel (the same count the library reports)."""
+    import numpy as np
+
+    cells = wl.fine_cells
+    f = 2 ** (wl.n_levels - 1)
+    lo = [x * f for x in wl.obstacle_lo]
+    hi = [x * f for x in wl.obstacle_hi]
+    active = np.ones(cells[::-1], dtype=bool)  # (z,) y, x
+    if any(h > l for l, h in zip(lo, hi)):
+        sl = tuple(slice(l, h) for l, h in zip(lo[::-1], hi[::-1]))
+        active[sl] = False
+    nodes = np.zeros(tuple(2 * c + 1 for c in cells[::-1]), dtype=bool)
+    for idx in zip(*np.nonzero(active)):
+        nodes[tuple(slice(2 * i, 2 * i + 3) for i in idx)] = True
+    C, R = int(active.sum()), int(nodes.sum())
+    return (wl.k + 1) * (wl.dim * R + (wl.dim + 1) * C)
+
+
 def main():
     args = parse()
     if args.oracle_child:
@@ -730,24 +1020,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
-        if rank != 0:
-            return
-        wl = workload(args.workload)
-        samples = max(1, args.steps)
-        o = run_oracle(args.workload, args.rtol, samples)
-        t = statistics.mean(o["solve_s"])
-        line = {"impl": "reference", "metric": "GMG-GMRES s to 1e-8 rel. res (mixed vs FP64, one GB300); Vanka sweep GB/s",
-                "value": t, "unit": "s", "n_gpus": args.gpus, "steps": samples, "warmup": 0,
-                "ms_per_step": 1e3 * t, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64", "data": "synthetic",
-                "config": dict(describe(wl, [o["sizes"]]), rtol=args.rtol,
-                               parallelism="CPU oracle, one thread (rank 0 of the job)"),
-                "cpu_baseline": {"value": t, "unit": "s", "cores": 1, "kind": "oracle",
-                                 "sample": f"{samples} full FP64 oracle FGMRES solve(s) of the same workload ({o['iters'][-1]} "
-                                           f"iterations each, single-threaded numpy/scipy) after "
-                                           f"an untimed {o['setup_s']:.1f} s oracle setup"},
-                "e2e": {"value": t, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-        print(json.dumps(line))
+        if rank == 0:
+            reference_arm(args)
         return
 
     if args.mesh_study:
@@ -770,13 +1044,20 @@ def main():
         if rank == 0:
             gpu_leg_multi(args, local_rank)
         return
-    wl, sizes, results, head, clocks, e2e_s, dist, fp64_peak, rows = gpu_leg(args, rank, world, local_rank)
+    wl, sizes, results, errs, head, clocks, e2e_s, dist, fp64_peak, rows = gpu_leg(args, rank, world, local_rank)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
+    precs = list(results)
+    if not args.no_other_rows and world == 1:
+        if args.workload != "c2_2d_k2":
+            rows["c2_2d_k2"] = workload_row(args, "c2_2d_k2", [p for p in ("f64", "bf16", "bf16+f32d") if p in precs]
+                                            or ["f64"], args.steps, args.warmup)
+        rows["c5_3d_k1"] = multi_row(args, "c5_3d_k1", 1, 1)
     pk = peaks()
     hbm = pk["hbm_gbs"] if pk else 6800.0
+    peak_src = "MEASURED_PEAKS.json hbm_gbs (of measured)" if pk else "fallback 6800 GB/s"
     r = results[head]
     vl = r["finest"]["vanka_local"]
     achieved = vl["bytes"] / (vl["ms"] * 1e-3) / 1e9 if vl["ms"] > 0 else None
@@ -785,45 +1066,27 @@ def main():
     cfg = describe(wl, sizes)
     cfg["rtol"] = args.rtol
     inv_bytes = {"f64": 8, "f32": 4, "bf16": 2}
-    l2_note = (f"inputs larger than L2: finest J {sizes[-1]['nnz'] * 12 / 1e6:.0f} MB, finest inverses "
-               f"{sizes[-1]['n_cells'] * sizes[-1]['n_local'] ** 2 * inv_bytes[split_precision(head)[0]] / 1e6:.0f} MB ({head})")
-    cfg["l2"] = l2_note
+    cfg["l2"] = (f"inputs larger than L2: finest J {sizes[-1]['nnz'] * 12 / 1e6:.0f} MB, finest inverses "
+                 f"{sizes[-1]['n_cells'] * sizes[-1]['n_local'] ** 2 * inv_bytes[split_precision(head)[0]] / 1e6:.0f} MB ({head})")
     cfg["parallelism"] = f"replicas x{world}" if world > 1 else "single GPU"
     line = {
         "metric": "GMG-GMRES s to 1e-8 rel. res (mixed vs FP64, one GB300); Vanka sweep GB/s",
         "value": r["ms_per_solve"] / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": r["ms_per_solve"], "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": dtype_label(head),
+        "dtype": dtype_label(head) + "; FP64 residual products in the V-cycle",
         "data": "synthetic", "config": cfg,
+        "head_precision": head,
         "fp64_s": results["f64"]["ms_per_solve"] / 1e3 if "f64" in results else None,
         "speedup_vs_fp64": (results["f64"]["ms_per_solve"] / r["ms_per_solve"]) if "f64" in results else None,
-        "by_precision": {p: {"s_per_solve": v["ms_per_solve"] / 1e3, "iters": v["iters_timed"],
-                             "rel_res_true": v["rel_res_true_timed"], "setup_ms": v["setup"],
-                             "vanka_sweep_gbs": (v["kernels"]["vanka_local"]["bytes"] / (v["kernels"]["vanka_local"]["ms"] * 1e-3) / 1e9)
-                             if v["kernels"]["vanka_local"]["ms"] > 0 else None,
-                             "spmv_gbs": (v["kernels"]["jacobian_spmv"]["bytes"] / (v["kernels"]["jacobian_spmv"]["ms"] * 1e-3) / 1e9)
-                             if v["kernels"]["jacobian_spmv"]["ms"] > 0 else None,
-                             "finest_vanka_gbs": (v["finest"]["vanka_local"]["bytes"] / (v["finest"]["vanka_local"]["ms"] * 1e-3) / 1e9)
-                             if v["finest"]["vanka_local"]["ms"] > 0 else None,
-                             "finest_spmv_gbs": (v["finest"]["jacobian_spmv"]["bytes"] / (v["finest"]["jacobian_spmv"]["ms"] * 1e-3) / 1e9)
-                             if v["finest"]["jacobian_spmv"]["ms"] > 0 else None,
-                             "finest_vanka_us": 1e3 * v["finest"]["vanka_local"]["ms"] / max(v["finest"]["vanka_local"]["launches"], 1),
-                             "finest_spmv_us": 1e3 * v["finest"]["jacobian_spmv"]["ms"] / max(v["finest"]["jacobian_spmv"]["launches"], 1),
-                             "finest_defect_f32_us": (1e3 * v["finest"]["defect_f32"]["ms"] / v["finest"]["defect_f32"]["launches"])
-                             if v["finest"]["defect_f32"]["launches"] else None,
-                             "finest_defect_f32_gbs": (v["finest"]["defect_f32"]["bytes"] / (v["finest"]["defect_f32"]["ms"] * 1e-3) / 1e9)
-                             if v["finest"]["defect_f32"]["ms"] > 0 else None,
-                             "kernel_ms_per_solve": {k: kv["ms"] / args.steps for k, kv in v["kernels"].items()},
-                             "us_per_launch_by_level": {k: [round(1e3 * e["ms"] / e["launches"], 2) if e["launches"] else None
-                                                            for e in lv] for k, lv in v["per_level"].items()},
-                             "s_per_solve_profiled_pass": v["ms_per_solve_profiled"] / 1e3}
-                         for p, v in results.items()},
+        "error_reference": ("err_vs_fp64_solution: the FP64 GPU solution of the same system in the same run; "
+                            "err_vs_oracle_sample: the FP64 oracle's solution of the bounded oracle sample"),
+        "by_precision": by_precision_rows(results, errs, args.steps),
         "gpu_launches": int(r["launches_per_step"] * args.steps),
         "other_rows": rows,
         "roofline": None,
         "roofline_spmv_f64": spmv_roofline(r, wl, sizes, fp64_peak, args.workload),
-        "roofline_defect_f32": defect_roofline(r, sizes, hbm, "MEASURED_PEAKS.json hbm_gbs (of measured)" if pk
-                                               else "fallback 6800 GB/s", args.workload),
+        "roofline_defect_f32": defect_roofline(results["bf16+f32d"], sizes, hbm, peak_src, args.workload)
+        if "bf16+f32d" in results else None,
         "roofline_vanka_sweep": {"kernel": f"{vk} (y_T = J_T^{{-1}} t_T), finest level, {head} inverses",
                                  "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                                  "frac": (achieved / hbm) if achieved else None,
@@ -831,7 +1094,7 @@ def main():
                                  "traffic_source": traffic["source"] if traffic else "no capture of the current kernel source",
                                  "all_levels_gbs": (r["kernels"]["vanka_local"]["bytes"] / (r["kernels"]["vanka_local"]["ms"] * 1e-3) / 1e9)
                                  if r["kernels"]["vanka_local"]["ms"] > 0 else None,
-                                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if pk else "fallback 6800 GB/s",
+                                 "peak_source": peak_src,
                                  "bytes_per_launch": vl["bytes"] / max(vl["launches"], 1),
                                  "avg_launch_us": 1e3 * vl["ms"] / max(vl["launches"], 1)},
         "vanka_sweep_gbs": achieved,
@@ -840,20 +1103,37 @@ def main():
                 "d2h_bytes_per_step": sizes[-1]["n_dofs"] * 8,
                 "path": f"stm_gmres_solve_host ({head}), pinned host b and x"},
     }
-    # the dominant kernel: the finest-level class with the most event time per solve
+    # the dominant kernel of the head run: the finest-level class with the most event time per solve
     shares = {"roofline_vanka_sweep": r["finest"]["vanka_local"]["ms"],
-              "roofline_spmv_f64": r["finest"]["jacobian_spmv"]["ms"],
-              "roofline_defect_f32": r["finest"]["defect_f32"]["ms"]}
+              "roofline_spmv_f64": r["finest"]["jacobian_spmv"]["ms"]}
     dom = max((k for k in shares if line[k]), key=lambda k: shares[k])
     line["roofline"] = dict(line[dom], dominant_of={k: round(v / args.steps, 3) for k, v in shares.items()},
                             dominant_of_unit="ms per solve, finest level, profiled pass")
     if not args.no_cpu_baseline and world == 1:
         try:
-            o = run_oracle(args.workload, args.rtol, 1)
-            line["cpu_baseline"] = {"value": o["solve_s"][0], "unit": "s", "cores": 1, "kind": "oracle",
-                                    "sample": f"one full FP64 oracle FGMRES solve of the same workload "
-                                              f"({o['iters'][0]} iterations, single-threaded numpy/scipy) after an "
-                                              f"untimed {o['setup_s']:.1f} s oracle setup"}
+            x_out = os.path.join(tempfile.mkdtemp(prefix="stm_xo_"), "x_oracle.npy")
+            nl = sample_levels(wl)
+            # the two thread counts run side by side on disjoint cores: one core for the 1-thread run,
+            # the others for the all-thread run (when the host has more than one core)
+            ncpu = os.cpu_count() or 1
+            split = ncpu > 1 and hasattr(os, "sched_setaffinity")
+            h1 = start_oracle(args.workload, args.rtol, 3, sweeps=3, n_levels=nl, threads=1, x_out=x_out,
+                              cpus=[0] if split else None)
+            if not split:
+                o1 = finish_oracle(h1)
+            hn = start_oracle(args.workload, args.rtol, 3, sweeps=3, n_levels=nl, threads=max(1, ncpu - 1),
+                              cpus=list(range(1, ncpu)) if split else None)
+            if split:
+                o1 = finish_oracle(h1)
+            on = finish_oracle(hn)
+            line["cpu_baseline"] = cpu_baseline_entry(o1, on, sizes[-1]["n_dofs"], sizes[-1]["n_cells"],
+                                                      r["iters_timed"], wl)
+            import numpy as np
+
+            chk = oracle_sample_check(args, wl, precs, np.load(x_out))
+            for p, e in chk.items():
+                line["by_precision"][p]["err_vs_oracle_sample"] = e
+            line["oracle_sample_iters"] = o1["iters"][-1]
         except Exception as e:  # reported, never silently replaced
             line["cpu_baseline"] = {"value": None, "error": str(e)[-300:]}
     print(json.dumps(line))

@@ -152,13 +152,15 @@ typedef struct {
   int max_iter;  /* total iteration limit (the paper treats 1000 as divergence)      */
   int transpose; /* 1: solve J^T x = b (adjoint) with the transposed preconditioner  */
   int use_x0;    /* 1: x_dev holds the initial guess on entry; 0: start from x = 0   */
-  double rtol;   /* stop when ||b - J x||_2 <= rtol ||b||_2 (recurrence estimate)   */
+  double rtol;   /* a cycle ends when the recurrence estimate of ||b - J x||_2 drops to
+                    rtol ||b||_2; the solve ends when the recomputed true residual does (else
+                    it restarts from x)                                                  */
 } stm_gmres_opts;
 
 typedef struct {
   int iters;           /* FGMRES iterations (preconditioner applications)             */
   int restarts;        /* completed restart cycles                                    */
-  int converged;       /* 1 if the recurrence residual reached rtol                   */
+  int converged;       /* 1 if the true residual ||b - J x||_2 <= rtol ||b||_2 at exit  */
   double rel_res_true; /* ||b - J x||_2 / ||b||_2 recomputed at exit                  */
   double rel_res_est;  /* last recurrence estimate                                    */
 } stm_solve_info;
@@ -166,7 +168,9 @@ typedef struct {
 /* Right-preconditioned flexible GMRES (Sec. 3) on the finest level, preconditioned by one
  * V-cycle per iteration, classical Gram-Schmidt with re-orthogonalisation. Synchronises once
  * per iteration to read the new Hessenberg column for the stopping test. Returns
- * STM_ERR_NOT_CONVERGED (x = last iterate, info filled) if max_iter is reached. */
+ * STM_ERR_NOT_CONVERGED (x = last iterate, info filled) if max_iter is reached before the true
+ * residual meets rtol, or on a breakdown (a zero column of the rotated Hessenberg matrix, possible
+ * in flexible GMRES when a preconditioned direction adds nothing). */
 stm_status stm_gmres_solve(stm_hierarchy* h, const double* b_dev, double* x_dev,
                            const stm_gmres_opts* opts, stm_solve_info* info, void* stream);
 
@@ -259,15 +263,15 @@ stm_status stm_copy_jacobian(const stm_hierarchy* h, int level, long long* rowpt
                              int* colidx_host, double* val_host);
 stm_status stm_copy_cell_inverses(const stm_hierarchy* h, int level, double* inv_host);
 
-/* Additive Vanka correction that allocates nothing (the paper has no counterpart; this entry point
- * exists for integration only).
+/* Additive Vanka correction that allocates nothing. The paper has no counterpart: this entry point
+ * exists for integration only.
  *
  * For callers that must not allocate device memory once they are running -- for example code
  * whose device memory is owned by another component's pool allocator, or latency-critical loops
  * that cannot afford the implicit device synchronisation of cudaMalloc/cudaFree. It needs no
  * hierarchy: the caller passes every input and output, and the library allocates nothing.
  *
- * Computes, for all cells T at once (Eq. LocVanka, damped, combined additively):
+ * Computes, for all cells T at once,
  *   d_i += omega * (1/m_i) * sum over the cells T containing i of (J_T^{-1} t_T)_i,
  * with m_i the number of cells whose DoF list contains i (DoFs in no cell are left unchanged).
  *   inv_dev : n_cells cell inverses, FP64, each n_local x n_local COLUMN-major, back to back
@@ -276,11 +280,13 @@ stm_status stm_copy_cell_inverses(const stm_hierarchy* h, int level, double* inv
  *   t_dev   : FP64 [n_dofs] residual r - J d;  d_dev: FP64 [n_dofs], updated in place
  * Limits: n_dofs <= 1048576 (else STM_ERR_INVALID_ARG, nothing launched), 1 <= n_local <= 1024.
  * Scratch: a fixed 16 MiB file-scope device array, present on every device that loads the library
- * until the process exits. The first call on a device looks up that array's device address (with
- * the device current); make that first call before any stream capture. Every call reuses the same
- * array and clears the part it needs, so calls that overlap on the GPU (other streams, other host
- * threads) race with each other and must be serialised by the caller. The shared-DoF sum uses
- * FP64 atomics, so the result matches stm_vanka_sweep(additive) up to summation order. */
+ * until the process exits. Every call looks up that array's device address on the current device
+ * (so calls after cudaDeviceReset, or on another device, get the address valid there); the first
+ * call on a device, and the first after a reset, also loads the library's device code there, so make
+ * it before any stream capture. Every call reuses the same array and clears the part it needs, so
+ * calls that overlap on the GPU (other streams, other host threads) race with each other and must be
+ * serialised by the caller. The shared-DoF sum uses FP64 atomics, so the result matches
+ * stm_vanka_sweep(additive) up to summation order. */
 stm_status stm_vanka_apply_noalloc(long long n_cells, int n_local, long long n_dofs, const double* inv_dev,
                                    const int* idx_dev, const double* t_dev, double* d_dev, double omega,
                                    void* stream);

@@ -248,7 +248,7 @@ static stm_status gmres_core(Hierarchy& H, const double* b, double* x, const stm
   const int G = (int)H.L.size();
   STM_TRY(ensure_krylov(H, m));
   const int nb = H.nblk_dot;
-  const int sblocks = (int)std::min<long long>((N + 255) / 256, 152 * 8LL);
+  const int sblocks = (int)std::min<long long>((N + 255) / 256, sm_count() * 8LL);
   stm_solve_info inf{};
   auto host_norm = [&](const double* v, double* out) -> stm_status {
     STM_TRY(vec_norm_sq(v, N, H.hcol, H.part, nb, s));
@@ -272,11 +272,12 @@ static stm_status gmres_core(Hierarchy& H, const double* b, double* x, const stm
   }
   const double tol = o.rtol * bnorm;
   std::vector<double> Hm((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), hc(m + 2), y(m);
-  int it = 0;
-  bool converged = false;
+  int it = 0, cycles = 0;
+  bool converged = false, breakdown = false;
   double est = 1.0;
   for (;;) {
-    // r = b - J x  -> V[0]
+    // r = b - J x  -> V[0]. The stopping decision is taken on this true residual: a cycle that ends
+    // because the recurrence estimate met rtol comes back here, and restarts if b - J x does not.
     STM_TRY(jacobian_apply(H, G - 1, x, b, H.V, 1, tr, s));
     double beta = 0.0;
     STM_TRY(host_norm(H.V, &beta));
@@ -284,18 +285,18 @@ static stm_status gmres_core(Hierarchy& H, const double* b, double* x, const stm
       set_error("non-finite residual norm");
       return STM_ERR_NONFINITE;
     }
-    est = beta / bnorm;
-    if (beta <= tol || it >= o.max_iter) {
+    if (cycles == 0) est = beta / bnorm;
+    inf.rel_res_true = beta / bnorm;
+    if (beta <= tol || it >= o.max_iter || breakdown) {
       converged = beta <= tol;
-      inf.rel_res_true = beta / bnorm;
       break;
     }
+    ++cycles;
     k_scale_host<<<sblocks, 256, 0, s>>>(H.V, H.V, 1.0 / beta, N); note_launch();
     std::fill(Hm.begin(), Hm.end(), 0.0);
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
     int jd = 0;
-    bool stop = false;
     for (int j = 0; j < m; ++j) {
       double* vj = H.V + (size_t)j * N;
       double* zj = H.Z + (size_t)j * N;
@@ -318,7 +319,10 @@ static stm_status gmres_core(Hierarchy& H, const double* b, double* x, const stm
       }
       for (int i = 0; i <= j; ++i) Hm[(size_t)i * m + j] = hc[i];
       Hm[(size_t)(j + 1) * m + j] = hn;
-      if (hn > 0.0) k_scale_host<<<sblocks, 256, 0, s>>>(H.V + (size_t)(j + 1) * N, H.w, 1.0 / hn, N); note_launch();
+      if (hn > 0.0) {
+        k_scale_host<<<sblocks, 256, 0, s>>>(H.V + (size_t)(j + 1) * N, H.w, 1.0 / hn, N);
+        note_launch();
+      }
       for (int i = 0; i < j; ++i) {
         const double a = Hm[(size_t)i * m + j], bb = Hm[(size_t)(i + 1) * m + j];
         Hm[(size_t)i * m + j] = cs[i] * a + sn[i] * bb;
@@ -326,6 +330,12 @@ static stm_status gmres_core(Hierarchy& H, const double* b, double* x, const stm
       }
       const double a = Hm[(size_t)j * m + j], bb = Hm[(size_t)(j + 1) * m + j];
       const double rho = std::hypot(a, bb);
+      if (!(rho > 0.0)) {
+        // zero Hessenberg column: in flexible GMRES (Sec. 3) the new direction may add nothing even
+        // though the least-squares problem is not solved; keep the columns before it and stop
+        breakdown = true;
+        break;
+      }
       cs[j] = a / rho;
       sn[j] = bb / rho;
       Hm[(size_t)j * m + j] = rho;
@@ -335,11 +345,8 @@ static stm_status gmres_core(Hierarchy& H, const double* b, double* x, const stm
       ++it;
       jd = j + 1;
       est = std::fabs(g[j + 1]) / bnorm;
-      if (std::fabs(g[j + 1]) <= tol || it >= o.max_iter || hn == 0.0) {
-        converged = std::fabs(g[j + 1]) <= tol || hn == 0.0;
-        stop = true;
-        break;
-      }
+      // hn == 0 with rho > 0: the Krylov space is invariant and the least-squares solution exact
+      if (std::fabs(g[j + 1]) <= tol || it >= o.max_iter || hn == 0.0) break;
     }
     // y = H^{-1} g (upper triangular), x += Z y
     for (int i = jd - 1; i >= 0; --i) {
@@ -347,23 +354,19 @@ static stm_status gmres_core(Hierarchy& H, const double* b, double* x, const stm
       for (int k2 = i + 1; k2 < jd; ++k2) t -= Hm[(size_t)i * m + k2] * y[k2];
       y[i] = t / Hm[(size_t)i * m + i];
     }
-    STM_CUDA(cudaMemcpyAsync(H.yvec, y.data(), sizeof(double) * jd, cudaMemcpyHostToDevice, s));
-    STM_TRY(gemv_accumulate(H.Z, jd, H.yvec, x, N, s));
-    if (stop) {
-      STM_TRY(jacobian_apply(H, G - 1, x, b, H.w, 1, tr, s));
-      double rn = 0.0;
-      STM_TRY(host_norm(H.w, &rn));
-      inf.rel_res_true = rn / bnorm;
-      break;
+    if (jd > 0) {
+      STM_CUDA(cudaMemcpyAsync(H.yvec, y.data(), sizeof(double) * jd, cudaMemcpyHostToDevice, s));
+      STM_TRY(gemv_accumulate(H.Z, jd, H.yvec, x, N, s));
     }
-    ++inf.restarts;
   }
   inf.iters = it;
+  inf.restarts = cycles > 0 ? cycles - 1 : 0;
   inf.converged = converged ? 1 : 0;
   inf.rel_res_est = est;
   if (info) *info = inf;
   if (!converged) {
-    set_error("FGMRES reached max_iter");
+    set_error(breakdown ? "FGMRES breakdown: zero column in the Hessenberg matrix before rtol was met"
+                        : "FGMRES reached max_iter");
     return STM_ERR_NOT_CONVERGED;
   }
   return STM_OK;
@@ -622,13 +625,15 @@ stm_status stm_gmres_solve_multi(stm_hierarchy* h, int nrhs, const double* B_dev
       set_error("non-finite right-hand side");
       return STM_ERR_NONFINITE;
     }
-  std::vector<int> iters(32, 0), conv(32, 0), restarts(32, 0);
+  std::vector<int> iters(32, 0), conv(32, 0), cycles(32, 0), broke(32, 0);
   std::vector<double> est(32, 1.0), relres(32, 0.0);
   for (int c = 0; c < 32; ++c)
     if (c >= nrhs || bnorm[c] == 0.0) conv[c] = 1;
   std::vector<double> Hm((size_t)(m + 1) * m * 32), cs(m * 32), sn(m * 32), g((m + 1) * 32);
   int it = 0;
   for (;;) {
+    // true residuals B - J X; a column counts as converged only when its true residual meets rtol
+    // (a cycle that stopped on the recurrence estimate is checked here and restarted if needed)
     STM_TRY(spmm_structured(F, H.mX, H.mB, H.mV, 1, s));
     STM_TRY(col_norms(H.mV, beta));
     bool any = false;
@@ -639,10 +644,12 @@ stm_status stm_gmres_solve_multi(stm_hierarchy* h, int nrhs, const double* B_dev
           set_error("non-finite residual norm");
           return STM_ERR_NONFINITE;
         }
-        est[c] = beta[c] / bnorm[c];
-        if (beta[c] <= opts->rtol * bnorm[c]) conv[c] = 1;
+        if (cycles[c] == 0) est[c] = beta[c] / bnorm[c];
+        relres[c] = beta[c] / bnorm[c];
+        conv[c] = beta[c] <= opts->rtol * bnorm[c];
       }
-      active[c] = !conv[c] && it < opts->max_iter;
+      active[c] = !conv[c] && !broke[c] && it < opts->max_iter;
+      if (active[c]) cycles[c] += 1;
       any = any || active[c];
       fvec[c] = active[c] ? 1.0 / beta[c] : 0.0;
     }
@@ -690,6 +697,11 @@ stm_status stm_gmres_solve_multi(stm_hierarchy* h, int nrhs, const double* B_dev
         }
         const double a = Hc(j, j), b = Hc(j + 1, j);
         const double rho = std::hypot(a, b);
+        if (!(rho > 0.0)) {  // zero Hessenberg column (flexible GMRES breakdown): keep the earlier columns
+          active[c] = 0;
+          broke[c] = 1;
+          continue;
+        }
         cs[j * 32 + c] = a / rho;
         sn[j * 32 + c] = b / rho;
         Hc(j, j) = rho;
@@ -700,8 +712,7 @@ stm_status stm_gmres_solve_multi(stm_hierarchy* h, int nrhs, const double* B_dev
         jd[c] = j + 1;
         est[c] = std::fabs(g[(j + 1) * 32 + c]) / bnorm[c];
         if (std::fabs(g[(j + 1) * 32 + c]) <= opts->rtol * bnorm[c] || hn == 0.0) {
-          conv[c] = 1;
-          active[c] = 0;
+          active[c] = 0;  // estimate met rtol (or an invariant Krylov space): checked at the next top
         } else if (it >= opts->max_iter) {
           active[c] = 0;
         } else {
@@ -725,34 +736,25 @@ stm_status stm_gmres_solve_multi(stm_hierarchy* h, int nrhs, const double* B_dev
     }
     STM_CUDA(cudaMemcpyAsync(H.my, yv.data(), sizeof(double) * jmax * 32, cudaMemcpyHostToDevice, s));
     STM_TRY(mupdate(H.mZ, jmax, H.my, H.mX, N, 1.0, s));
-    for (int c = 0; c < 32; ++c)
-      if (!conv[c]) restarts[c] += 1;
-    if (it >= opts->max_iter) {
-      bool all = true;
-      for (int c = 0; c < nrhs; ++c) all = all && conv[c];
-      if (!all) break;
-    }
   }
-  // true residuals
-  STM_TRY(spmm_structured(F, H.mX, H.mB, H.mW, 1, s));
-  double rn[32];
-  STM_TRY(col_norms(H.mW, rn));
+  // the last loop top computed the true residuals of the returned X
   STM_TRY(multi_from_interleaved(H.mX, X_dev, N, nrhs, s));
   STM_CUDA(cudaStreamSynchronize(s));
-  bool all = true;
+  bool all = true, broken = false;
   for (int c = 0; c < nrhs; ++c) {
-    relres[c] = bnorm[c] > 0.0 ? rn[c] / bnorm[c] : 0.0;
     all = all && conv[c];
+    broken = broken || (broke[c] && !conv[c]);
     if (infos) {
       infos[c].iters = iters[c];
-      infos[c].restarts = restarts[c];
+      infos[c].restarts = cycles[c] > 0 ? cycles[c] - 1 : 0;
       infos[c].converged = conv[c];
       infos[c].rel_res_true = relres[c];
       infos[c].rel_res_est = est[c];
     }
   }
   if (!all) {
-    set_error("multi-RHS FGMRES reached max_iter for some columns");
+    set_error(broken ? "multi-RHS FGMRES breakdown (zero Hessenberg column) in some column"
+                     : "multi-RHS FGMRES reached max_iter for some columns");
     return STM_ERR_NOT_CONVERGED;
   }
   return STM_OK;

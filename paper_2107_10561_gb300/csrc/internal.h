@@ -37,6 +37,9 @@ stm_status cuda_fail(cudaError_t e, const char* what);
   } while (0)
 #endif
 
+// Streaming multiprocessors of the current device (queried once per process)
+int sm_count();
+
 // Launch accounting and optional per-class CUDA-event timing --------------------------------
 extern std::atomic<long long> g_launches;
 inline void note_launch(long long n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }

@@ -66,7 +66,7 @@ stm_status launch_fill_colidx(Level& L, const int* nbr_ptr, const int* nbr, cons
                               cudaStream_t s) {
   const int threads = 256;
   long long warps_needed = L.N;
-  int blocks = (int)std::min<long long>((warps_needed + 7) / 8, 152LL * 64);
+  int blocks = (int)std::min<long long>((warps_needed + 7) / 8, sm_count() * 64LL);
   k_fill_colidx<<<blocks, threads, 0, s>>>(L.rowptr, L.colidx, nbr_ptr, nbr, node_cells, L.cell_nodes,
                                            L.N, L.block, L.R, L.dim, L.K, L.nv, L.np, 1 << L.dim); note_launch();
   STM_CUDA(cudaGetLastError());
@@ -92,7 +92,7 @@ stm_status inject_linearisation(Hierarchy& H, const double* X, cudaStream_t s) {
   const Level& F = H.L.back();
   for (Level& L : H.L) {
     long long total = (long long)L.K * L.dim * L.R;
-    int blocks = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
+    int blocks = (int)std::min<long long>((total + 255) / 256, sm_count() * 16LL);
     k_inject<<<blocks, 256, 0, s>>>(X, L.wnod, L.inj, L.R, L.K, L.dim, F.block, F.R); note_launch();
     STM_CUDA(cudaGetLastError());
   }
@@ -240,7 +240,7 @@ stm_status assemble_level(Hierarchy& H, int g, double nu, cudaStream_t s) {
   for (int col = 0; col < (1 << L.dim); ++col) {
     const int nc = L.colour_off[col + 1] - L.colour_off[col];
     if (nc == 0) continue;
-    const int blocks = std::min(nc, 152 * 8);
+    const int blocks = std::min(nc, sm_count() * 8);
     k_assemble<<<blocks, 256, smem, s>>>(L.colour_cells + L.colour_off[col], nc, L.idx, L.cell_nodes,
                                          L.bmask, L.rank, L.cellrank, L.nn, L.ncell, L.rowptr, L.val,
                                          L.wnod, L.ref, L.ro, ac, L.dim, L.K, L.R, L.n, L.nt); note_launch();

@@ -382,8 +382,8 @@ __global__ void __launch_bounds__(1024) k_block_inverse_smem(double* __restrict_
 
 // Explicit inverse of a dense n x n block in global memory, one pivot at a time (larger blocks).
 static void block_inverse_global(double* M, long long n, int* piv, double* scal, int* flag, cudaStream_t s) {
-  const int vb = (int)std::min<long long>((n + 255) / 256, 152 * 8);
-  const int mb = (int)std::min<long long>((n * n + 255) / 256, 152 * 32);
+  const int vb = (int)std::min<long long>((n + 255) / 256, sm_count() * 8LL);
+  const int mb = (int)std::min<long long>((n * n + 255) / 256, sm_count() * 32LL);
   for (int k = 0; k < n; ++k) {
     k_gj_pivot<<<1, 1024, 0, s>>>(M, n, k, piv, scal, flag); note_launch();
     k_gj_swap_scale<<<vb, 256, 0, s>>>(M, n, k, piv, scal); note_launch();
@@ -505,7 +505,7 @@ stm_status factor_coarse(Hierarchy& H, cudaStream_t s) {
     cudaMemcpyAsync(d_upos, upos.data(), sizeof(long long) * nx, cudaMemcpyHostToDevice, s);
     cudaMemsetAsync(store, 0, sizeof(double) * tot, s);
     cudaMemsetAsync(Xp, 0, sizeof(double) * n * n, s);
-    k_slab_blocks<<<(int)std::min<long long>(n, 152 * 32), 128, 0, s>>>(L.rowptr, L.colidx, L.val, n, d_iperm, d_blk,
+    k_slab_blocks<<<(int)std::min<long long>(n, sm_count() * 32LL), 128, 0, s>>>(L.rowptr, L.colidx, L.val, n, d_iperm, d_blk,
                                                                           d_off, d_dpos, d_lpos, d_upos, store,
                                                                           H.dflag + 1);
     note_launch();
@@ -541,7 +541,7 @@ stm_status factor_coarse(Hierarchy& H, cudaStream_t s) {
     for (int b = 0; b < nx; ++b) {
       const long long nb = off[b + 1] - off[b];
       double* rowb = Xp + off[b] * n;
-      k_copy_block<<<(int)std::min<long long>((nb * nb + 255) / 256, 152 * 8), 256, 0, s>>>(
+      k_copy_block<<<(int)std::min<long long>((nb * nb + 255) / 256, sm_count() * 8LL), 256, 0, s>>>(
           store + dpos[b], nb, nb, nb, rowb + off[b], n);
       note_launch();
       if (b > 0) {

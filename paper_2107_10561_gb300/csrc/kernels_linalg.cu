@@ -7,16 +7,7 @@
 
 namespace stm {
 
-static int sms() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 152;
-  }
-  return n;
-}
+static int sms() { return sm_count(); }
 
 // VL lanes per row (VL = 1, 2, 4, 8, 16 or 32, chosen from the mean row length); values and column
 // indices are streamed once (cache-streaming loads), x stays cached. mode 0: y = A x;

@@ -17,16 +17,7 @@ namespace stm {
 
 constexpr int NR = 32;  // columns of a multi-vector
 
-static int msms() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 152;
-  }
-  return n;
-}
+static int msms() { return sm_count(); }
 
 // ---------------------------------------------------------------------------------------------
 // layout conversion: column-major [nrhs][N] (ld N) <-> interleaved [N][32]

@@ -225,7 +225,7 @@ stm_status assemble_cellvec(Hierarchy& H, int mode, double U, double nu, const i
   for (int col = 0; col < (1 << L.dim); ++col) {
     const int nc = L.colour_off[col + 1] - L.colour_off[col];
     if (!nc) continue;
-    k_cellvec<<<std::min(nc, 152 * 8), 256, smem, s>>>(L.colour_cells + L.colour_off[col], nc, mode, L.idx,
+    k_cellvec<<<std::min(nc, sm_count() * 8), 256, smem, s>>>(L.colour_cells + L.colour_off[col], nc, mode, L.idx,
                                                        L.cell_nodes, L.cell_xyz, L.bmask, L.wnod, L.ref, L.ro, vc,
                                                        L.dim, L.K, L.R, L.n, L.nt, mode == 0 ? vprev : nullptr,
                                                        out);
@@ -242,7 +242,7 @@ stm_status dnu_apply(Hierarchy& H, const double* x, double* y, cudaStream_t s) {
   for (int col = 0; col < (1 << L.dim); ++col) {
     const int nc = L.colour_off[col + 1] - L.colour_off[col];
     if (!nc) continue;
-    k_dnu_apply<<<std::min(nc, 152 * 8), 256, 0, s>>>(L.colour_cells + L.colour_off[col], nc, L.idx, L.bmask, L.ref,
+    k_dnu_apply<<<std::min(nc, sm_count() * 8), 256, 0, s>>>(L.colour_cells + L.colour_off[col], nc, L.idx, L.bmask, L.ref,
                                                       L.ro, vc, L.dim, L.K, L.n, L.nt, x, y);
     note_launch();
     STM_CUDA(cudaGetLastError());

@@ -119,13 +119,13 @@ __global__ void k_build_pval(const long long* __restrict__ rowptr, const double*
 stm_status build_nodeblock(Level& L, cudaStream_t s) { return build_nodeblock_from(L, L.val, L.nval, L.pvalT, s); }
 
 stm_status build_nodeblock_from(const Level& L, const double* val, double* nval, double* pvalT, cudaStream_t s) {
-  const int blocks = (int)std::min<long long>(((long long)L.R * 32 + 255) / 256, 152LL * 8);
+  const int blocks = (int)std::min<long long>(((long long)L.R * 32 + 255) / 256, sm_count() * 8LL);
   k_build_nodeblock<<<blocks, 256, 0, s>>>(L.rowptr, val, L.nbr_ptr, L.ncell, L.nbase, nval, L.block, L.R, L.K,
                                            L.dim, L.np);
   note_launch();
   STM_CUDA(cudaGetLastError());
   const long long npr = (long long)L.K * L.C * L.np;
-  const int pblocks = (int)std::min<long long>((npr + 255) / 256, 152LL * 8);
+  const int pblocks = (int)std::min<long long>((npr + 255) / 256, sm_count() * 8LL);
   k_build_pval<<<std::max(pblocks, 1), 256, 0, s>>>(L.rowptr, val, pvalT, L.block, L.R, L.C, L.K, L.dim, L.np,
                                                     L.nv);
   note_launch();
@@ -445,15 +445,6 @@ stm_status defect_f32(Hierarchy& H, int g, int transpose, const double* x, const
   return spmv_nodeblock_t<float>(L, nv, pv, L.x32, b, y, 1, s);
 }
 
-static int sms_count() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 152;
-  }
-  return n;
-}
+static int sms_count() { return sm_count(); }
 
 }  // namespace stm

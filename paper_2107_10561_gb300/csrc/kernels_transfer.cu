@@ -14,16 +14,7 @@
 
 namespace stm {
 
-static int sm_count_tr() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 152;
-  }
-  return n;
-}
+static int sm_count_tr() { return sm_count(); }
 
 struct TransferGeom {
   long long fblock, cblock;  // DoFs per time node on the fine / coarse level

@@ -4,8 +4,6 @@
 // stm_build_hierarchy allocates. This variant needs no library-owned allocation at all: all of
 // its scratch lives in one fixed-size, file-scope device array that exists from the moment the
 // library is loaded on a device until the process exits.
-#include <mutex>
-
 #include "internal.h"
 
 namespace stm {
@@ -59,26 +57,23 @@ __global__ void k_noalloc_combine(const double* __restrict__ scratch, double* __
   }
 }
 
-// Device address of the scratch array, looked up once per device with that device current.
-static std::mutex g_noalloc_mu;
-static double* g_noalloc_ptr[64] = {nullptr};
-
+// Device address of the scratch array on the current device. Looked up on every call (a cheap
+// query once the library's module is loaded on the device), so a call after cudaDeviceReset or on
+// another device never uses an address from an earlier context.
 static stm_status noalloc_scratch(double** out) {
-  int dev = 0;
-  STM_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) {
-    set_error("stm_vanka_apply_noalloc: device ordinal out of range");
-    return STM_ERR_INVALID_ARG;
-  }
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
-    g_noalloc_ptr[dev] = static_cast<double*>(p);
-  }
-  *out = g_noalloc_ptr[dev];
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+  *out = static_cast<double*>(p);
   return STM_OK;
+}
+
+static int noalloc_sms() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      n <= 0)
+    n = 1;
+  return n;
 }
 
 }  // namespace stm
@@ -105,10 +100,11 @@ extern "C" stm_status stm_vanka_apply_noalloc(long long n_cells, int n_local, lo
   stm_status st = noalloc_scratch(&scratch);
   if (st != STM_OK) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const int vb = (int)std::min<long long>((n_dofs + 255) / 256, 152 * 8LL);
+  const int sms = noalloc_sms();
+  const int vb = (int)std::min<long long>((n_dofs + 255) / 256, sms * 8LL);
   k_noalloc_clear<<<vb, 256, 0, s>>>(scratch, n_dofs);
   note_launch();
-  const int cb = (int)std::min<long long>(n_cells, 152 * 16LL);
+  const int cb = (int)std::min<long long>(n_cells, sms * 16LL);
   k_noalloc_local<<<cb, 128, sizeof(double) * n_local, s>>>(inv_dev, idx_dev, t_dev, scratch, n_cells, n_local,
                                                                n_dofs);
   note_launch();

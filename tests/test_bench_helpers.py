@@ -89,3 +89,34 @@ def test_committed_traffic_records_name_existing_profiles(bench):
         assert os.path.exists(os.path.join(ROOT, e["profile"])), e["profile"]
         assert os.path.exists(os.path.join(ROOT, e["source"])), e["source"]
         assert e["dram_bytes_read"] > 0 and e["dram_bytes_write"] >= 0
+
+
+def test_headline_is_a_conforming_mixed_run(bench):
+    """The headline never comes from the FP32-defect run, however fast it is."""
+    res = {"f64": {"ms_per_solve": 90.0}, "f32": {"ms_per_solve": 70.0}, "bf16": {"ms_per_solve": 60.0},
+           "bf16+f32d": {"ms_per_solve": 40.0}}
+    assert bench.pick_head(res) == "bf16"
+    res["f32"]["ms_per_solve"] = 50.0
+    assert bench.pick_head(res) == "f32"
+    assert bench.pick_head({"f64": {"ms_per_solve": 1.0}, "bf16+f32d": {"ms_per_solve": 0.5}}) == "f64"
+
+
+def test_full_workload_dofs_match_the_level_table(bench):
+    """(k+1)(d R + n_p C) of the obstacle channels: the per-config DoF counts of the workloads."""
+    import synth
+    expect = {"c1_2d_k1": 5956, "c2_2d_k2": 536448, "c3_3d_k1": 962208, "c4_2d_k1": 90112, "c5_3d_k1": 7459392}
+    for name, n in expect.items():
+        assert bench.full_workload_dofs(synth.WORKLOADS[name]) == n
+
+
+def test_cpu_baseline_scaling(bench):
+    import synth
+    o1 = {"threads": 1, "solve_s": [8.0, 9.0, 10.0], "iters": [11, 11, 11], "sweep_s": [0.2, 0.1, 0.3],
+          "setup_s": 50.0, "sizes": {"n_dofs": 1000, "n_cells": 10, "n_local": 170, "n_levels": 2}}
+    on = dict(o1, threads=15, solve_s=[4.0, 5.0, 6.0])
+    e = bench.cpu_baseline_entry(o1, on, 8000, 80, 12, synth.WORKLOADS["c3_3d_k1"])
+    assert e["value"] == pytest.approx(9.0 * 8)
+    assert e["cores"] == 1 and e["kind"] == "oracle"
+    assert e["one_thread"]["sweep_s_scaled"] == pytest.approx(0.2 * 8)
+    assert e["all_threads"]["solve_s_scaled"] == pytest.approx(5.0 * 8)
+    assert e["all_threads"]["threads"] == 15

@@ -38,6 +38,31 @@ def test_c2_2d_k2_full_solve_against_oracle():
         h.close()
 
 
+@pytest.mark.timeout(900)
+def test_c3_3d_k1_two_level_full_solve_against_oracle():
+    """The 3D dG(1) channel of c3_3d_k1 with one refinement level fewer (fine 32x8x8 minus the obstacle,
+    127,920 DoFs, n = 170): the complete oracle solve is affordable there. Both solves to rtol 1e-10;
+    FP64 inverses: iterations +-1 and the solution within 1e-8; FP32 / BF16 inverses (FP64 defects):
+    the solution within 1e-7."""
+    import dataclasses
+
+    from oracle import solvers
+    wl = dataclasses.replace(synth.WORKLOADS["c3_3d_k1"], n_levels=2)
+    o = solvers.Hierarchy(wl, synth.linearisation_point(wl))
+    b = o.fine.dofs_from_lattice(synth.random_rhs(wl))
+    x_o, info_o = o.solve(b, rtol=1e-10)
+    assert info_o["converged"]
+    for prec, tol in (("f64", 1e-8), ("f32", 1e-7), ("bf16", 1e-7)):
+        h = gpu_hierarchy(wl, prec)
+        x = torch.zeros(o.fine.N, dtype=torch.float64, device="cuda")
+        info = h.gmres_solve(torch.from_numpy(b).cuda(), x, rtol=1e-10)
+        assert info["converged"] and info["rel_res_true"] <= 1e-10
+        if prec == "f64":
+            assert abs(info["iters"] - info_o["iters"]) <= 1, (info, info_o)
+        assert rel_max(x.cpu().numpy(), x_o) < tol, prec
+        h.close()
+
+
 # ---------------------------------------------------------------------------------------------
 # c3_3d_k1: sampled checks
 # ---------------------------------------------------------------------------------------------

@@ -1,7 +1,8 @@
 """Multi-right-hand-side path (32 columns sharing one hierarchy) against the single-RHS path and
 the oracle.
 
-One multi-RHS smoothing step equals the single-RHS step column by column: to 1e-12 with FP64
+One multi-RHS smoothing step equals, column by column, the oracle's additive sweep taken with the
+cell inverses the GPU stores (converted to FP64), and the single-RHS GPU step: to 1e-12 with FP64
 inverses (same arithmetic, other summation order), 1e-5 with FP32 inverses (FP32 accumulation),
 and 1e-4 with BF16 inverses on the tensor cores (the gathered block enters as two BF16 parts, i.e.
 to about 2^-16 relative; FP32 accumulation). The lock-stepped FGMRES reaches the same solutions as
@@ -42,6 +43,32 @@ def test_multi_sweep_equals_single_sweeps(name, prec, nrhs):
         d = D[c].clone()
         h.vanka_sweep(g, R[c].contiguous(), d)
         assert rel_max(Dm[c].cpu().numpy(), d.cpu().numpy()) < TOL[prec], (c, prec)
+    h.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("nrhs", [32, 7])
+def test_multi_sweep_against_oracle(name, prec, nrhs):
+    """Every column of one multi-RHS additive step against oracle.solvers.vanka_step (Eq. LocVanka,
+    damped, multiplicity-weighted) on the oracle's J with the inverses as stored on the GPU."""
+    from helpers import oracle_hierarchy
+    from oracle import solvers
+    wl = CASES[name]
+    o = oracle_hierarchy(wl)
+    h = gpu_hierarchy(wl, prec)
+    g = h.finest
+    lev = o.fine
+    inv = h.copy_cell_inverses(g)
+    rng = np.random.default_rng(65)
+    R = rng.standard_normal((nrhs, lev.N))
+    D = rng.standard_normal((nrhs, lev.N))
+    Dm = torch.from_numpy(D).cuda()
+    h.vanka_sweep_multi(g, torch.from_numpy(R).cuda(), Dm)
+    got = Dm.cpu().numpy()
+    for c in range(nrhs):
+        expect = solvers.vanka_step(lev, o.J[-1], inv, D[c], R[c], wl.omega)
+        assert rel_max(got[c], expect) < TOL[prec], (c, prec)
     h.close()
 
 

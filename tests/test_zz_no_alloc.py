@@ -8,7 +8,9 @@ output from the caller and keeps its scratch in a fixed static device array.
 This test calls it through the C-ABI twice in a row and compares both results with one additive
 sweep of stm_vanka_sweep on the same cell inverses and residual (1e-12 relative, the single-sweep
 tolerance of the other parity tests; the two differ only in FP64 summation order). The second call
-also shows that the scratch left behind by the first call is cleared.
+also shows that the scratch left behind by the first call is cleared. It then feeds the oracle's own
+cell inverses and residual through the same entry point and compares the result with the oracle's
+additive sweep (same tolerance).
 """
 import numpy as np
 import pytest
@@ -52,6 +54,24 @@ def test_noalloc_additive_correction_matches_vanka_sweep():
         vanka_apply_noalloc(inv_cm, idx, t, d, wl.omega)
         torch.cuda.synchronize()
         assert _rel(d, d_ref) < 1e-12
+
+    # the oracle's inverses and residual through the same entry point give the oracle's sweep
+    from helpers import oracle_hierarchy
+    from oracle import solvers
+
+    ho = oracle_hierarchy(wl)
+    lo, Jo, invo = ho.fine, ho.J[-1], ho.inv[-1]
+    r_np, d_np = r.cpu().numpy(), d0.cpu().numpy()
+    expect = solvers.vanka_step(lo, Jo, invo, d_np, r_np, wl.omega)
+    t_o = torch.from_numpy(r_np - Jo @ d_np).cuda()
+    inv_o = torch.from_numpy(np.ascontiguousarray(invo.transpose(0, 2, 1))).cuda()
+    idx_o = torch.from_numpy(lo.idx.astype(np.int32)).cuda()
+    for _ in range(2):
+        d = d0.clone()
+        vanka_apply_noalloc(inv_o, idx_o, t_o, d, wl.omega)
+        torch.cuda.synchronize()
+        got = d.cpu().numpy()
+        assert np.abs(got - expect).max() / np.abs(expect).max() < 1e-12
 
     # sizes beyond the fixed scratch capacity are rejected before any launch
     big = torch.zeros(2**20 + 1, dtype=torch.float64, device="cuda")
