@@ -163,6 +163,12 @@ typedef struct {
   int converged;       /* 1 if the true residual ||b - J x||_2 <= rtol ||b||_2 at exit  */
   double rel_res_true; /* ||b - J x||_2 / ||b||_2 recomputed at exit                  */
   double rel_res_est;  /* last recurrence estimate                                    */
+  const double* history; /* relative residual history: entry 0 the initial true residual,
+                            then the recurrence estimate after every iteration and the true
+                            residual at every restart; library-owned host memory, valid
+                            until the next solve on the same hierarchy                  */
+  int n_history;       /* entries of history                                          */
+  double ms_total;     /* host wall time of the call in ms (the call synchronises)    */
 } stm_solve_info;
 
 /* Right-preconditioned flexible GMRES (Sec. 3) on the finest level, preconditioned by one
@@ -189,6 +195,30 @@ stm_status stm_gmres_solve_host(stm_hierarchy* h, const double* b_host, double* 
  *   which = 1: db/dU (b is linear in U);   which = 2: db/dnu (b is affine in nu).
  * b_dev: FP64 [n_dofs of the finest level], overwritten. */
 stm_status stm_assemble_rhs(stm_hierarchy* h, double U, double nu, int which, double* b_dev, void* stream);
+
+/* Load vector of one Newton step on the finest level (Problem 3.1 with f = 0, Eqs. Def:Lh, Def:B_GamD,
+ * linearised as in Eq. linNewEq): b_dev = b(U, nu) + c(w, w) for the linearisation point w whose
+ * finest-level DoF vector is w_dev (only its velocity is used), with b and c as for stm_assemble_rhs
+ * (which = 0). w_dev = NULL takes the point of the last stm_assemble_jacobian. The assembled matrices
+ * and the stored linearisation point are left unchanged. b_dev: FP64 [n_dofs], overwritten.
+ * STM_ERR_STATE for w_dev = NULL before any assembly. */
+stm_status stm_assemble_load(stm_hierarchy* h, double U, double nu, const double* w_dev, double* b_dev,
+                             void* stream);
+
+/* Gradient of the drag-like functional J(X) = j . X of one Newton step J(w; nu) X = b(U, nu) + c(w, w)
+ * with respect to the inflow amplitude U and the viscosity nu (adjoint method; the paper has no
+ * gradient, the formulas follow from differentiating Eq. linNewEq with w fixed):
+ *   solve J^T lambda = j with the transposed GMG-preconditioned FGMRES of stm_gmres_solve
+ *   (opts->transpose and opts->use_x0 are ignored; lambda starts from zero), then
+ *   *dJdU  = lambda . db/dU,
+ *   *dJdnu = lambda . (db/dnu - (dJ/dnu) X),
+ * J assembled at w with this nu and factored (stm_factor_cells) beforehand; X_dev the forward solution
+ * (FP64 [n_dofs]); j_dev the functional weights (stm_functional_weights). lambda_dev: NULL, or an FP64
+ * [n_dofs] buffer that receives lambda. info (may be NULL) describes the adjoint solve. Synchronous.
+ * Errors: the FGMRES errors (STM_ERR_NOT_CONVERGED leaves the gradient outputs untouched). */
+stm_status stm_adjoint_gradient(stm_hierarchy* h, double U, double nu, const double* j_dev, const double* X_dev,
+                                const stm_gmres_opts* opts, stm_solve_info* info, double* lambda_dev,
+                                double* dJdU, double* dJdnu, void* stream);
 
 /* Nonlinear slab problem F(X) = 0 (Sec. 3, Eq. nonlineq) with the data of stm_assemble_rhs:
  *   F(X) = A X + c(X, X) - b(U, nu),  A the linear part of the slab operator, c the convection term,

@@ -31,7 +31,8 @@ class GmresOpts(C.Structure):
 
 class SolveInfo(C.Structure):
     _fields_ = [("iters", C.c_int), ("restarts", C.c_int), ("converged", C.c_int),
-                ("rel_res_true", C.c_double), ("rel_res_est", C.c_double)]
+                ("rel_res_true", C.c_double), ("rel_res_est", C.c_double),
+                ("history", C.POINTER(C.c_double)), ("n_history", C.c_int), ("ms_total", C.c_double)]
 
 
 NEWTON_MAX_STEPS = 32  # STM_NEWTON_MAX_STEPS
@@ -69,6 +70,8 @@ SIGNATURES = {
     "stm_gmres_solve": ([_P, _P, _P, C.POINTER(GmresOpts), C.POINTER(SolveInfo), _P], _I),
     "stm_gmres_solve_host": ([_P, _DP, _DP, C.POINTER(GmresOpts), C.POINTER(SolveInfo), _P], _I),
     "stm_assemble_rhs": ([_P, _D, _D, _I, _P, _P], _I),
+    "stm_assemble_load": ([_P, _D, _D, _P, _P, _P], _I),
+    "stm_adjoint_gradient": ([_P, _D, _D, _P, _P, C.POINTER(GmresOpts), C.POINTER(SolveInfo), _P, _DP, _DP, _P], _I),
     "stm_newton_solve": ([_P, _D, _D, _P, _P, C.POINTER(NewtonOpts), C.POINTER(GmresOpts), C.POINTER(NewtonInfo),
                           _P], _I),
     "stm_functional_weights": ([_P, _IP, _IP, _P, _P], _I),

@@ -4,8 +4,9 @@ One Newton step from a fixed linearisation point w solves J(w; nu) X = b(U, nu) 
 Eq. linNewEq); the drag-like functional is J(X) = j . X (velocity integrated over the wake region and
 the slab). The backward pass solves the adjoint system J^T lambda = j with the same hierarchy
 (transposed SpMV, transposed cell inverses, P / P^T, transposed coarse inverse) and returns
-  dJ/dU = lambda . db/dU,   dJ/dnu = lambda . (db/dnu - (dJ/dnu) X).
-Every vector operation runs in libstm; this module only sequences the calls.
+  dJ/dU = lambda . db/dU,   dJ/dnu = lambda . (db/dnu - (dJ/dnu) X),
+both formed inside libstm (stm_adjoint_gradient). Every vector operation runs in libstm; this module
+only sequences the calls.
 """
 from __future__ import annotations
 
@@ -44,21 +45,15 @@ class SlabFunctional:
     def value_and_state(self, U: float, nu: float):
         self.prepare(nu)
         b = torch.empty_like(self.X_lin)
-        self.h.assemble_rhs(U, nu, b, which=0)
+        self.h.assemble_load(U, nu, b, w=self.X_lin)
         X = self.solve(b)
         return self.h.dot(self.j, X), X
 
     def gradient(self, U: float, nu: float, X: torch.Tensor):
         self.prepare(nu)
-        lam = self.solve(self.j, transpose=True)
-        dbdU = torch.empty_like(X)
-        dbdnu = torch.empty_like(X)
-        dJX = torch.empty_like(X)
-        self.h.assemble_rhs(U, nu, dbdU, which=1)
-        self.h.assemble_rhs(U, nu, dbdnu, which=2)
-        self.h.jacobian_dnu_apply(X, dJX)
-        gU = self.h.dot(lam, dbdU)
-        gnu = self.h.dot(lam, dbdnu) - self.h.dot(lam, dJX)
+        gU, gnu, info = self.h.adjoint_gradient(U, nu, self.j, X, rtol=self.rtol, restart=self.restart,
+                                                max_iter=self.max_iter)
+        self.last_info["adjoint"] = info
         return gU, gnu
 
 

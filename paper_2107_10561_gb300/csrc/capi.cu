@@ -1,4 +1,5 @@
 // C-ABI entry points of libstm (declared in include/stm.h).
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -23,6 +24,20 @@ static stm_status bad_arg(const char* msg) {
 }
 
 static cudaStream_t S(void* p) { return reinterpret_cast<cudaStream_t>(p); }
+
+namespace stm {
+stm_status check_kernel_error(Hierarchy& H, cudaStream_t s) {
+  int e = 0;
+  STM_CUDA(cudaMemcpyAsync(&e, H.dkerr, sizeof(int), cudaMemcpyDeviceToHost, s));
+  STM_CUDA(cudaStreamSynchronize(s));
+  if (e) {
+    STM_CUDA(cudaMemsetAsync(H.dkerr, 0, sizeof(int), s));
+    set_error("a tensor-core pipeline wait timed out (error word " + std::to_string(e) + ")");
+    return STM_ERR_CUDA;
+  }
+  return STM_OK;
+}
+}  // namespace stm
 
 extern "C" {
 
@@ -250,6 +265,7 @@ static stm_status gmres_core(Hierarchy& H, const double* b, double* x, const stm
   const int nb = H.nblk_dot;
   const int sblocks = (int)std::min<long long>((N + 255) / 256, sm_count() * 8LL);
   stm_solve_info inf{};
+  H.hist.clear();
   auto host_norm = [&](const double* v, double* out) -> stm_status {
     STM_TRY(vec_norm_sq(v, N, H.hcol, H.part, nb, s));
     double t = 0.0;
@@ -267,6 +283,7 @@ static stm_status gmres_core(Hierarchy& H, const double* b, double* x, const stm
   if (!o.use_x0 || bnorm == 0.0) STM_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * N, s));
   if (bnorm == 0.0) {
     inf.converged = 1;
+    inf.history = H.hist.data();
     if (info) *info = inf;
     return STM_OK;
   }
@@ -287,6 +304,7 @@ static stm_status gmres_core(Hierarchy& H, const double* b, double* x, const stm
     }
     if (cycles == 0) est = beta / bnorm;
     inf.rel_res_true = beta / bnorm;
+    H.hist.push_back(beta / bnorm);
     if (beta <= tol || it >= o.max_iter || breakdown) {
       converged = beta <= tol;
       break;
@@ -345,6 +363,7 @@ static stm_status gmres_core(Hierarchy& H, const double* b, double* x, const stm
       ++it;
       jd = j + 1;
       est = std::fabs(g[j + 1]) / bnorm;
+      H.hist.push_back(est);
       // hn == 0 with rho > 0: the Krylov space is invariant and the least-squares solution exact
       if (std::fabs(g[j + 1]) <= tol || it >= o.max_iter || hn == 0.0) break;
     }
@@ -363,6 +382,8 @@ static stm_status gmres_core(Hierarchy& H, const double* b, double* x, const stm
   inf.restarts = cycles > 0 ? cycles - 1 : 0;
   inf.converged = converged ? 1 : 0;
   inf.rel_res_est = est;
+  inf.history = H.hist.data();
+  inf.n_history = (int)H.hist.size();
   if (info) *info = inf;
   if (!converged) {
     set_error(breakdown ? "FGMRES breakdown: zero column in the Hessenberg matrix before rtol was met"
@@ -381,7 +402,10 @@ stm_status stm_gmres_solve(stm_hierarchy* h, const double* b, double* x, const s
     set_error("gmres_solve before factor_cells");
     return STM_ERR_STATE;
   }
-  return gmres_core(h->H, b, x, *opts, info, S(stream));
+  const auto t0 = std::chrono::steady_clock::now();
+  const stm_status st = gmres_core(h->H, b, x, *opts, info, S(stream));
+  if (info) info->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return st;
 }
 
 stm_status stm_gmres_solve_host(stm_hierarchy* h, const double* b_host, double* x_host, const stm_gmres_opts* opts,
@@ -515,6 +539,61 @@ stm_status stm_assemble_rhs(stm_hierarchy* h, double U, double nu, int which, do
   return assemble_cellvec(h->H, which, U, nu, nullptr, nullptr, b_dev, S(stream));
 }
 
+stm_status stm_assemble_load(stm_hierarchy* h, double U, double nu, const double* w_dev, double* b_dev,
+                             void* stream) {
+  if (!h || !b_dev) return bad_arg("NULL argument");
+  Hierarchy& H = h->H;
+  cudaStream_t s = S(stream);
+  if (!w_dev) {
+    if (!H.assembled) {
+      set_error("assemble_load without w needs the linearisation point of assemble_jacobian");
+      return STM_ERR_STATE;
+    }
+    return assemble_cellvec(H, 0, U, nu, nullptr, nullptr, b_dev, s);
+  }
+  const Level& F = H.L.back();
+  if (!H.ag_wnod) STM_CUDA(cudaMalloc(&H.ag_wnod, sizeof(double) * (size_t)F.K * F.dim * F.R));
+  STM_TRY(inject_level(H, (int)H.L.size() - 1, w_dev, H.ag_wnod, s));
+  return assemble_cellvec(H, 0, U, nu, nullptr, nullptr, b_dev, s, nullptr, H.ag_wnod);
+}
+
+stm_status stm_adjoint_gradient(stm_hierarchy* h, double U, double nu, const double* j_dev, const double* X_dev,
+                                const stm_gmres_opts* opts, stm_solve_info* info, double* lambda_dev,
+                                double* dJdU, double* dJdnu, void* stream) {
+  if (!h || !j_dev || !X_dev || !opts || !dJdU || !dJdnu) return bad_arg("NULL argument");
+  if (opts->restart < 1 || opts->restart > 200 || opts->max_iter < 0 || !(opts->rtol >= 0.0))
+    return bad_arg("restart in [1,200], max_iter >= 0, rtol >= 0");
+  Hierarchy& H = h->H;
+  if (!H.factored) {
+    set_error("adjoint_gradient before factor_cells");
+    return STM_ERR_STATE;
+  }
+  const long long N = H.L.back().N;
+  cudaStream_t s = S(stream);
+  if (!H.ag_buf) STM_CUDA(cudaMalloc(&H.ag_buf, sizeof(double) * 4 * (size_t)N));
+  double* dbdU = H.ag_buf;  // db/dU, db/dnu and (dJ/dnu) X back to back: one batched dot with lambda
+  double* dbdnu = dbdU + N;
+  double* dJX = dbdnu + N;
+  double* lam = lambda_dev ? lambda_dev : dJX + N;
+  stm_gmres_opts o = *opts;
+  o.transpose = 1;
+  o.use_x0 = 0;
+  const auto t0 = std::chrono::steady_clock::now();
+  const stm_status st = gmres_core(H, j_dev, lam, o, info, s);  // J^T lambda = j
+  if (info) info->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (st != STM_OK) return st;
+  STM_TRY(assemble_cellvec(H, 1, U, nu, nullptr, nullptr, dbdU, s));
+  STM_TRY(assemble_cellvec(H, 2, U, nu, nullptr, nullptr, dbdnu, s));
+  STM_TRY(dnu_apply(H, X_dev, dJX, s));
+  STM_TRY(batched_dots(dbdU, 3, lam, N, H.hcol, H.part, H.nblk_dot, s));
+  double dots[3] = {0.0, 0.0, 0.0};
+  STM_CUDA(cudaMemcpyAsync(dots, H.hcol, sizeof(double) * 3, cudaMemcpyDeviceToHost, s));
+  STM_CUDA(cudaStreamSynchronize(s));
+  *dJdU = dots[0];
+  *dJdnu = dots[1] - dots[2];
+  return STM_OK;
+}
+
 stm_status stm_functional_weights(stm_hierarchy* h, const int* wake_lo, const int* wake_hi, double* j_dev,
                                   void* stream) {
   if (!h || !wake_lo || !wake_hi || !j_dev) return bad_arg("NULL argument");
@@ -561,7 +640,8 @@ stm_status stm_vanka_sweep_multi(stm_hierarchy* h, int level, int nrhs, const do
   STM_TRY(multi_to_interleaved(R_dev, L.mr, L.N, nrhs, s));
   STM_TRY(multi_to_interleaved(D_dev, L.md, L.N, nrhs, s));
   STM_TRY(vanka_step_multi(H, level, L.mr, L.md, false, s));
-  return multi_from_interleaved(L.md, D_dev, L.N, nrhs, s);
+  STM_TRY(multi_from_interleaved(L.md, D_dev, L.N, nrhs, s));
+  return check_kernel_error(H, s);
 }
 
 static stm_status ensure_krylov_multi(Hierarchy& H, int m) {
@@ -626,6 +706,7 @@ stm_status stm_gmres_solve_multi(stm_hierarchy* h, int nrhs, const double* B_dev
       return STM_ERR_NONFINITE;
     }
   std::vector<int> iters(32, 0), conv(32, 0), cycles(32, 0), broke(32, 0);
+  for (auto& v : H.mhist) v.clear();
   std::vector<double> est(32, 1.0), relres(32, 0.0);
   for (int c = 0; c < 32; ++c)
     if (c >= nrhs || bnorm[c] == 0.0) conv[c] = 1;
@@ -646,6 +727,7 @@ stm_status stm_gmres_solve_multi(stm_hierarchy* h, int nrhs, const double* B_dev
         }
         if (cycles[c] == 0) est[c] = beta[c] / bnorm[c];
         relres[c] = beta[c] / bnorm[c];
+        H.mhist[c].push_back(relres[c]);
         conv[c] = beta[c] <= opts->rtol * bnorm[c];
       }
       active[c] = !conv[c] && !broke[c] && it < opts->max_iter;
@@ -675,7 +757,7 @@ stm_status stm_gmres_solve_multi(stm_hierarchy* h, int nrhs, const double* B_dev
         STM_TRY(mdots(H.mW, 1, H.mW, N, H.mh + (j + 1) * 32, H.mpart, nb, s));
       }
       STM_CUDA(cudaMemcpyAsync(hbuf.data(), H.mh, sizeof(double) * (j + 2) * 32, cudaMemcpyDeviceToHost, s));
-      STM_CUDA(cudaStreamSynchronize(s));
+      STM_TRY(check_kernel_error(H, s));
       ++it;
       jmax = j + 1;
       bool still = false;
@@ -711,6 +793,7 @@ stm_status stm_gmres_solve_multi(stm_hierarchy* h, int nrhs, const double* B_dev
         iters[c] += 1;
         jd[c] = j + 1;
         est[c] = std::fabs(g[(j + 1) * 32 + c]) / bnorm[c];
+        H.mhist[c].push_back(est[c]);
         if (std::fabs(g[(j + 1) * 32 + c]) <= opts->rtol * bnorm[c] || hn == 0.0) {
           active[c] = 0;  // estimate met rtol (or an invariant Krylov space): checked at the next top
         } else if (it >= opts->max_iter) {
@@ -750,6 +833,8 @@ stm_status stm_gmres_solve_multi(stm_hierarchy* h, int nrhs, const double* B_dev
       infos[c].converged = conv[c];
       infos[c].rel_res_true = relres[c];
       infos[c].rel_res_est = est[c];
+      infos[c].history = H.mhist[c].data();
+      infos[c].n_history = (int)H.mhist[c].size();
     }
   }
   if (!all) {

@@ -740,6 +740,8 @@ stm_status build_levels(Hierarchy& H) {
   }
   STM_CUDA(cudaMalloc((void**)&H.dflag, sizeof(int) * 4));
   STM_CUDA(cudaMemset(H.dflag, 0, sizeof(int) * 4));
+  STM_CUDA(cudaMalloc((void**)&H.dkerr, sizeof(int)));
+  STM_CUDA(cudaMemset(H.dkerr, 0, sizeof(int)));
   STM_CUDA(cudaMalloc((void**)&H.dbad, sizeof(long long) * 2));
   return STM_OK;
 }
@@ -759,8 +761,8 @@ void free_hierarchy(Hierarchy& H) {
     for (void* q : ptrs)
       if (q) cudaFree(q);
   }
-  void* hp[] = {H.cinv, H.cpart, H.dflag, H.dbad, H.V, H.Z, H.w, H.hcol, H.part, H.yvec, H.bbuf, H.xbuf,
-                H.nw_negF, H.nw_D, H.nw_Xt, H.nw_B, H.nw_Ft,
+  void* hp[] = {H.cinv, H.cpart, H.dflag, H.dkerr, H.dbad, H.V, H.Z, H.w, H.hcol, H.part, H.yvec, H.bbuf, H.xbuf,
+                H.nw_negF, H.nw_D, H.nw_Xt, H.nw_B, H.nw_Ft, H.ag_buf, H.ag_wnod,
                 H.mV, H.mZ, H.mW, H.mB, H.mX, H.mh, H.mpart, H.mf, H.my};
   for (void* q : hp)
     if (q) cudaFree(q);

@@ -40,6 +40,28 @@ stm_status cuda_fail(cudaError_t e, const char* what);
 // Streaming multiprocessors of the current device (queried once per process)
 int sm_count();
 
+// BF16 bits of the value nearest to x (ties to even), rounded once from the FP64 bit fields: 8
+// significant bits, exponent range of FP32. Zero, values below the BF16 normal range, overflow and
+// non-finite values take the FP32 route (exact for zero, infinities and NaN).
+__device__ __forceinline__ uint32_t bf16_bits_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const uint32_t sign = (uint32_t)(b >> 48) & 0x8000u;
+  const int e = (int)((b >> 52) & 0x7FF) - 1023;
+  if (e < -126 || e > 127) {
+    const uint32_t f = __float_as_uint((float)x);
+    if ((f & 0x7F800000u) == 0x7F800000u) return (f >> 16) | ((f & 0xFFFFu) ? 0x40u : 0u);
+    const uint32_t lsb = (f >> 16) & 1u;
+    return (f + 0x7FFFu + lsb) >> 16;
+  }
+  const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;  // 52 stored bits, 7 are kept
+  uint32_t r = sign | ((uint32_t)(e + 127) << 7) | (uint32_t)(mant >> 45);
+  const unsigned long long rest = mant & ((1ull << 45) - 1);
+  const unsigned long long half = 1ull << 44;
+  if (rest > half || (rest == half && (r & 1u))) ++r;  // a carry moves into the exponent as it should
+  return r;
+}
+__device__ __forceinline__ double bf16_bits_to_double(uint32_t h) { return (double)__uint_as_float(h << 16); }
+
 // Launch accounting and optional per-class CUDA-event timing --------------------------------
 extern std::atomic<long long> g_launches;
 inline void note_launch(long long n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
@@ -171,6 +193,7 @@ struct Hierarchy {
   long long N0 = 0;
   double* cpart = nullptr;  // [ceil(N0 / kCoarseTChunk)][N0] partial sums of the transposed coarse solve
   int* dflag = nullptr;           // device flags: [0] singular flag, [1..2] bad cell (int64 split)
+  int* dkerr = nullptr;           // device error word of the tensor-core pipelines (bounded waits)
   long long* dbad = nullptr;
   // FGMRES work space (finest level)
   int restart_cap = 0;
@@ -184,6 +207,12 @@ struct Hierarchy {
   double* xbuf = nullptr;
   // damped Newton (allocated on first use): -F, step D, trial iterate, b + c(X, X), trial's -F
   double *nw_negF = nullptr, *nw_D = nullptr, *nw_Xt = nullptr, *nw_B = nullptr, *nw_Ft = nullptr;
+  // adjoint gradient and explicit-point load vector (allocated on first use): db/dU, db/dnu,
+  // (dJ/dnu) X, lambda; nodal linearisation velocity of an explicit point
+  double *ag_buf = nullptr, *ag_wnod = nullptr;
+  // residual histories of the last single- and multi-right-hand-side solves (host)
+  std::vector<double> hist;
+  std::vector<double> mhist[32];
   int nblk_dot = 0;
   // multi-right-hand-side FGMRES work space ([.][N][32])
   int mrestart_cap = 0;
@@ -261,8 +290,11 @@ stm_status smoother_defect(Hierarchy& H, int g, const double* x, const double* b
 stm_status vanka_step(Hierarchy& H, int g, const double* r, double* d, int transpose,
                       bool d_is_zero, cudaStream_t s, bool d32_current = false);
 stm_status coarse_apply(Hierarchy& H, const double* r, double* d, int transpose, cudaStream_t s);
+// wnod: nodal linearisation velocity [K][d][R] of the finest level to use instead of the stored one
 stm_status assemble_cellvec(Hierarchy& H, int mode, double U, double nu, const int* wake_lo, const int* wake_hi,
-                            double* out, cudaStream_t s, const double* vprev = nullptr);
+                            double* out, cudaStream_t s, const double* vprev = nullptr, const double* wnod = nullptr);
+// wnod = the velocity of the finest-level DoF vector X at the nodes of level g ([K][d][R_g])
+stm_status inject_level(const Hierarchy& H, int g, const double* X, double* wnod, cudaStream_t s);
 stm_status dnu_apply(Hierarchy& H, const double* x, double* y, cudaStream_t s);
 // multi-right-hand-side path (kernels_multi.cu), multi-vectors interleaved [N][32]
 stm_status multi_to_interleaved(const double* src, double* dst, long long N, int nrhs, cudaStream_t s);
@@ -270,6 +302,12 @@ stm_status multi_from_interleaved(const double* src, double* dst, long long N, i
 stm_status spmm_structured(const Level& L, const double* X, const double* B, double* Y, int mode, cudaStream_t s);
 stm_status ensure_multi(Hierarchy& H);
 stm_status vanka_step_multi(Hierarchy& H, int g, const double* R, double* Dm, bool d_is_zero, cudaStream_t s);
+// Y[c][i][32] (FP32) = J_c^{-1} T_c on the tcgen05 tensor cores, BF16 inverses of leading dimension ld
+// (kernels_mrhs_tc.cu); err: device word set when a pipeline wait times out
+bool mrhs_tc_supported(int n, int ld);
+stm_status mrhs_tc_apply(const Level& L, int ld, const double* T, float* Y, int* err, cudaStream_t s);
+// reads and clears the device error word of the tensor-core kernels (synchronous)
+stm_status check_kernel_error(Hierarchy& H, cudaStream_t s);
 stm_status vcycle_multi(Hierarchy& H, const double* R_fine, double* D_fine, cudaStream_t s);
 stm_status mdots(const double* V, int nv, const double* w, long long n, double* out, double* part, int nblk,
                  cudaStream_t s);

@@ -88,6 +88,17 @@ __global__ void k_inject(const double* __restrict__ X, double* __restrict__ wnod
   }
 }
 
+stm_status inject_level(const Hierarchy& H, int g, const double* X, double* wnod, cudaStream_t s) {
+  const Level& F = H.L.back();
+  const Level& L = H.L[g];
+  long long total = (long long)L.K * L.dim * L.R;
+  int blocks = (int)std::min<long long>((total + 255) / 256, sm_count() * 16LL);
+  k_inject<<<std::max(blocks, 1), 256, 0, s>>>(X, wnod, L.inj, L.R, L.K, L.dim, F.block, F.R);
+  note_launch();
+  STM_CUDA(cudaGetLastError());
+  return STM_OK;
+}
+
 stm_status inject_linearisation(Hierarchy& H, const double* X, cudaStream_t s) {
   const Level& F = H.L.back();
   for (Level& L : H.L) {

@@ -16,7 +16,7 @@ template <typename S> __device__ __forceinline__ S to_store(double v);
 template <> __device__ __forceinline__ double to_store<double>(double v) { return v; }
 template <> __device__ __forceinline__ float to_store<float>(double v) { return (float)v; }
 template <> __device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16>(double v) {
-  return __float2bfloat16_rn((float)v);
+  return __ushort_as_bfloat16((unsigned short)bf16_bits_rn(v));  // one rounding, straight from FP64
 }
 
 // Position in the CSR values of J_g of the entry (local row al, local col be) of cell c.

@@ -4,9 +4,10 @@
 //  * SpMM with J_g: the structured pattern of k_spmv_struct, one warp per node (cell) with the
 //    32 lanes on the 32 right-hand sides: each value of J is read once for all columns (broadcast).
 //  * Vanka local solves Y_T = J_T^{-1} T_T for a 32-column block (a6'' of the hot path): with BF16
-//    inverses on the tensor cores (mma.sync m16n8k16, FP32 accumulation); the gathered block T is
-//    split into T_hi + T_lo BF16 parts so that the only rounding is that of the stored inverse.
-//    FP32 / FP64 inverses use CUDA cores.
+//    inverses on the tcgen05 tensor cores (kernels_mrhs_tc.cu: TMA-staged inverses, FP32 accumulators
+//    in tensor memory, the gathered block split into T_hi + T_lo BF16 parts so that the only rounding
+//    is that of the stored inverse), Y in FP32; FP32 / FP64 inverses (and BF16 ones whose stored
+//    columns are not whole 16-byte units) on CUDA cores, Y in FP32 / FP64.
 //  * additive combine, transfers, coarse solve and the V-cycle (Algorithm 1) on 32 columns.
 #include <cstdint>
 #include <type_traits>
@@ -191,132 +192,17 @@ stm_status csr_multi(const long long* rowptr, const int* col, const double* val,
 // ---------------------------------------------------------------------------------------------
 // Vanka local solves on 32 columns
 // ---------------------------------------------------------------------------------------------
-__device__ __forceinline__ unsigned smem_addr(const void* p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(smem)), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(smem)), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::); }
-__device__ __forceinline__ void ldmatrix_x4_trans(unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3,
-                                                  const void* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-               : "r"(smem_addr(p)));
-}
-__device__ __forceinline__ void mma_bf16(float* c, unsigned a0, unsigned a1, unsigned a2, unsigned a3, unsigned b0,
-                                         unsigned b1) {
-  asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-               : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-               : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
+// CUDA-core variant (FP32 / FP64 inverses; BF16 ones whose columns are not whole 16-byte units):
+// lane = column, warps over rows, Inv read by broadcast; FP64 accumulation and Y for FP64 inverses,
+// FP32 otherwise.
+__device__ __forceinline__ float inv_to_acc(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float inv_to_acc(float v) { return v; }
+__device__ __forceinline__ double inv_to_acc(double v) { return v; }
 
-// Tensor-core geometry of one level (BF16 inverses).
-struct TCGeom {
-  int n, ld;      // local size and stored leading dimension (rows, multiple of 8)
-  int MT, KT;     // 16-row tiles of the output / 16-wide steps of the contraction
-  int lds;        // shared-memory row length (elements) of the A tile, conflict-free for ldmatrix
-  int ldt;        // shared-memory row length of the T tiles
-};
-
-// Y_T[n][32] = Inv_T[n][n] (BF16, column-major with leading dimension ld) * T_T[n][32].
-// Shared memory: A tile stored as in global (one "row" per column j, i contiguous), padded with
-// zeros to KT*16 columns and MT*16 rows; T_hi / T_lo as [32][ldt] (k contiguous per column).
-// Warp w computes output row tiles w, w + nwarps, ... over all 4 column tiles of 8.
-__global__ void __launch_bounds__(256) k_vanka_mrhs_tc(const __nv_bfloat16* __restrict__ inv,
-                                                       const int* __restrict__ idx, const double* __restrict__ T,
-                                                       double* __restrict__ Yout, int ncells, TCGeom g) {
-  extern __shared__ __align__(16) unsigned char smb[];
-  __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(smb);                 // [KT*16][lds]
-  __nv_bfloat16* Th = As + (size_t)g.KT * 16 * g.lds;                         // [32][ldt]
-  __nv_bfloat16* Tl = Th + (size_t)NR * g.ldt;                                // [32][ldt]
-  const int tid = threadIdx.x, nth = blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5, nwarps = nth >> 5;
-  // zero the padding once: columns j >= n of A, rows i >= ld of A, k >= n of T
-  for (int e = tid; e < g.KT * 16 * g.lds; e += nth) {
-    const int j = e / g.lds, i = e - j * g.lds;
-    if (j >= g.n || i >= g.ld) As[e] = __float2bfloat16(0.0f);
-  }
-  for (int e = tid; e < NR * g.ldt; e += nth) {
-    const int k = e % g.ldt;
-    if (k >= g.n) {
-      Th[e] = __float2bfloat16(0.0f);
-      Tl[e] = __float2bfloat16(0.0f);
-    }
-  }
-  // 16-byte copies when the stored columns are 16-byte aligned (ld % 8 == 0), 4-byte copies otherwise
-  const int ch_el = (g.ld % 8 == 0) ? 8 : 2;
-  const int chunks_per_col = g.ld / ch_el;
-  for (int c = blockIdx.x; c < ncells; c += gridDim.x) {
-    __syncthreads();
-    // A: asynchronous 16-byte copies of the stored columns
-    const __nv_bfloat16* M = inv + (size_t)c * g.n * g.ld;
-    for (int e = tid; e < g.n * chunks_per_col; e += nth) {
-      const int j = e / chunks_per_col, ch = e - j * chunks_per_col;
-      if (ch_el == 8) cp_async16(As + (size_t)j * g.lds + ch * 8, M + (size_t)j * g.ld + ch * 8);
-      else cp_async4(As + (size_t)j * g.lds + ch * 2, M + (size_t)j * g.ld + ch * 2);
-    }
-    // T: gather 32 columns of every local DoF, split into BF16 hi + lo
-    const int* ic = idx + (long long)c * g.n;
-    for (int e = tid; e < g.n * NR; e += nth) {
-      const int k = e / NR, col = e - k * NR;
-      const double v = T[(long long)ic[k] * NR + col];
-      const __nv_bfloat16 hi = __double2bfloat16(v);
-      const __nv_bfloat16 lo = __double2bfloat16(v - (double)__bfloat162float(hi));
-      Th[col * g.ldt + k] = hi;
-      Tl[col * g.ldt + k] = lo;
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    const int gq = lane >> 2, tq = lane & 3;
-    for (int mt = warp; mt < g.MT; mt += nwarps) {
-      float acc[4][4];
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-        for (int r = 0; r < 4; ++r) acc[nt][r] = 0.0f;
-      for (int kt = 0; kt < g.KT; ++kt) {
-        // A fragments (row-major 16x16 tile of Inv) from the column-major tile by a transposed ldmatrix:
-        // sub-matrices (rows +0/+8, k +0/+8) for lanes 0-7, 8-15, 16-23, 24-31
-        const int sub = lane >> 3, r8 = lane & 7;
-        const int io = (sub & 1) * 8, ko = (sub >> 1) * 8;
-        unsigned a0, a1, a2, a3;
-        ldmatrix_x4_trans(a0, a1, a2, a3, As + (size_t)(kt * 16 + ko + r8) * g.lds + mt * 16 + io);
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-          const int ncol = nt * 8 + gq;
-          const unsigned* th = reinterpret_cast<const unsigned*>(Th + ncol * g.ldt + kt * 16);
-          const unsigned* tl = reinterpret_cast<const unsigned*>(Tl + ncol * g.ldt + kt * 16);
-          mma_bf16(acc[nt], a0, a1, a2, a3, th[tq], th[tq + 4]);
-          mma_bf16(acc[nt], a0, a1, a2, a3, tl[tq], tl[tq + 4]);
-        }
-      }
-      // C fragment: rows gq / gq + 8, columns 2 tq, 2 tq + 1 of each 8-column tile
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        const int r0 = mt * 16 + gq, r1 = r0 + 8, cc = nt * 8 + 2 * tq;
-        if (r0 < g.n) {
-          Yout[((long long)c * g.n + r0) * NR + cc] = acc[nt][0];
-          Yout[((long long)c * g.n + r0) * NR + cc + 1] = acc[nt][1];
-        }
-        if (r1 < g.n) {
-          Yout[((long long)c * g.n + r1) * NR + cc] = acc[nt][2];
-          Yout[((long long)c * g.n + r1) * NR + cc + 1] = acc[nt][3];
-        }
-      }
-    }
-  }
-}
-
-// CUDA-core variant for FP32 / FP64 inverses: lane = column, warps over rows, Inv read by broadcast.
-template <typename S>
+template <typename S, typename A>
 __global__ void __launch_bounds__(256) k_vanka_mrhs_cc(const S* __restrict__ inv, const int* __restrict__ idx,
-                                                       const double* __restrict__ T, double* __restrict__ Yout,
+                                                       const double* __restrict__ T, A* __restrict__ Yout,
                                                        int ncells, int n, int ld) {
-  using A = typename std::conditional<sizeof(S) == 8, double, float>::type;
   extern __shared__ __align__(16) unsigned char smc[];
   A* Ts = reinterpret_cast<A*>(smc);  // [n][32]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -331,34 +217,24 @@ __global__ void __launch_bounds__(256) k_vanka_mrhs_cc(const S* __restrict__ inv
     const S* M = inv + (size_t)c * n * ld;
     for (int i = warp; i < n; i += nwarps) {
       A s = 0;
-      for (int j = 0; j < n; ++j) s += (A)M[(size_t)j * ld + i] * Ts[j * NR + lane];
-      Yout[((long long)c * n + i) * NR + lane] = (double)s;
+      for (int j = 0; j < n; ++j) s += (A)inv_to_acc(M[(size_t)j * ld + i]) * Ts[j * NR + lane];
+      Yout[((long long)c * n + i) * NR + lane] = s;
     }
   }
 }
 
-// d[i][c] += omega / m_i * sum over the owners of i of Y[pos][c]
-__global__ void k_vanka_gather_multi(double* __restrict__ d, const double* __restrict__ Y, const int* __restrict__ own_ptr,
+// d[i][c] += omega / m_i * sum over the owners of i of Y[pos][c]  (Y in FP32 or FP64)
+template <typename A>
+__global__ void k_vanka_gather_multi(double* __restrict__ d, const A* __restrict__ Y, const int* __restrict__ own_ptr,
                                      const int* __restrict__ own_pos, const double* __restrict__ wmult, long long N,
                                      double omega) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N * NR; e += (long long)gridDim.x * blockDim.x) {
     const long long i = e / NR;
     const int col = (int)(e - i * NR);
     double s = 0.0;
-    for (int p = own_ptr[i]; p < own_ptr[i + 1]; ++p) s += Y[(long long)own_pos[p] * NR + col];
+    for (int p = own_ptr[i]; p < own_ptr[i + 1]; ++p) s += (double)Y[(long long)own_pos[p] * NR + col];
     d[e] += omega * wmult[i] * s;
   }
-}
-
-static TCGeom tc_geometry(const Level& L, int ld) {
-  TCGeom g;
-  g.n = L.n;
-  g.ld = ld;
-  g.MT = (ld + 15) / 16;
-  g.KT = (L.n + 15) / 16;
-  g.lds = g.MT * 16 + 8;
-  g.ldt = g.KT * 16 + 8;
-  return g;
 }
 
 stm_status ensure_multi(Hierarchy& H) {
@@ -384,35 +260,41 @@ stm_status vanka_step_multi(Hierarchy& H, int g, const double* R, double* Dm, bo
   }
   const int prec = H.p.inv_precision;
   const InvLayout lay = inv_layout(L.n, prec);
+  const bool tc = prec == STM_BF16 && mrhs_tc_supported(L.n, lay.ld);
+  const bool y64 = prec == STM_F64;
   {
+    // algorithmic bytes: the stored inverses, the index map, the 32 gathered FP64 columns of every
+    // local DoF and the 32 written columns of Y (FP64 with FP64 inverses, FP32 otherwise)
     ProfScope ps(&H, STM_KCLASS_VANKA_LOCAL, s,
                  (double)L.C * ((double)L.n * L.n * (prec == STM_F64 ? 8 : prec == STM_F32 ? 4 : 2) + 4.0 * L.n +
-                                16.0 * NR * L.n),
+                                (8.0 + (y64 ? 8.0 : 4.0)) * NR * L.n),
                  g);
-    if (prec == STM_BF16) {
-      const TCGeom tg = tc_geometry(L, lay.ld);
-      const size_t smem = sizeof(__nv_bfloat16) * ((size_t)tg.KT * 16 * tg.lds + 2 * (size_t)NR * tg.ldt);
-      STM_CUDA(cudaFuncSetAttribute(k_vanka_mrhs_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      const int threads = std::min(256, std::max(64, tg.MT * 32));
-      const int blocks = std::min(L.C, msms() * 4);
-      k_vanka_mrhs_tc<<<blocks, threads, smem, s>>>((const __nv_bfloat16*)L.inv, L.idx, T, L.mY, L.C, tg);
+    if (tc) {
+      STM_TRY(mrhs_tc_apply(L, lay.ld, T, reinterpret_cast<float*>(L.mY), H.dkerr, s));
     } else {
-      const size_t smem = (prec == STM_F64 ? 8 : 4) * (size_t)L.n * NR;
       const int blocks = std::min(L.C, msms() * 8);
-      if (prec == STM_F64) {
-        STM_CUDA(cudaFuncSetAttribute(k_vanka_mrhs_cc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_vanka_mrhs_cc<double><<<blocks, 256, smem, s>>>((const double*)L.inv, L.idx, T, L.mY, L.C, L.n, lay.ld);
-      } else {
-        STM_CUDA(cudaFuncSetAttribute(k_vanka_mrhs_cc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_vanka_mrhs_cc<float><<<blocks, 256, smem, s>>>((const float*)L.inv, L.idx, T, L.mY, L.C, L.n, lay.ld);
-      }
+#define MRHS_CC(S_, A_)                                                                                          \
+  do {                                                                                                          \
+    const size_t smem = sizeof(A_) * (size_t)L.n * NR;                                                          \
+    STM_CUDA(cudaFuncSetAttribute(k_vanka_mrhs_cc<S_, A_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+    k_vanka_mrhs_cc<S_, A_><<<blocks, 256, smem, s>>>((const S_*)L.inv, L.idx, T, reinterpret_cast<A_*>(L.mY), L.C, \
+                                                      L.n, lay.ld);                                             \
+  } while (0)
+      if (prec == STM_F64) MRHS_CC(double, double);
+      else if (prec == STM_F32) MRHS_CC(float, float);
+      else MRHS_CC(__nv_bfloat16, float);
+#undef MRHS_CC
+      note_launch();
+      STM_CUDA(cudaGetLastError());
     }
-    note_launch();
-    STM_CUDA(cudaGetLastError());
   }
   ProfScope ps(&H, STM_KCLASS_VANKA_COMBINE, s, 0.0, g);
   const int blocks = (int)std::min<long long>((L.N * NR + 255) / 256, msms() * 16LL);
-  k_vanka_gather_multi<<<blocks, 256, 0, s>>>(Dm, L.mY, L.own_ptr, L.own_pos, L.wmult, L.N, H.p.omega);
+  if (y64)
+    k_vanka_gather_multi<double><<<blocks, 256, 0, s>>>(Dm, L.mY, L.own_ptr, L.own_pos, L.wmult, L.N, H.p.omega);
+  else
+    k_vanka_gather_multi<float><<<blocks, 256, 0, s>>>(Dm, reinterpret_cast<const float*>(L.mY), L.own_ptr, L.own_pos,
+                                                       L.wmult, L.N, H.p.omega);
   note_launch();
   STM_CUDA(cudaGetLastError());
   return STM_OK;

@@ -207,7 +207,7 @@ static VecConst make_vc(const Hierarchy& H, const Level& L, double U, double nu)
 }
 
 stm_status assemble_cellvec(Hierarchy& H, int mode, double U, double nu, const int* wake_lo, const int* wake_hi,
-                            double* out, cudaStream_t s, const double* vprev) {
+                            double* out, cudaStream_t s, const double* vprev, const double* wnod) {
   Level& L = H.L.back();
   VecConst vc = make_vc(H, L, U, nu);
   const int f = 1 << ((int)H.L.size() - 1);
@@ -226,7 +226,7 @@ stm_status assemble_cellvec(Hierarchy& H, int mode, double U, double nu, const i
     const int nc = L.colour_off[col + 1] - L.colour_off[col];
     if (!nc) continue;
     k_cellvec<<<std::min(nc, sm_count() * 8), 256, smem, s>>>(L.colour_cells + L.colour_off[col], nc, mode, L.idx,
-                                                       L.cell_nodes, L.cell_xyz, L.bmask, L.wnod, L.ref, L.ro, vc,
+                                                       L.cell_nodes, L.cell_xyz, L.bmask, wnod ? wnod : L.wnod, L.ref, L.ro, vc,
                                                        L.dim, L.K, L.R, L.n, L.nt, mode == 0 ? vprev : nullptr,
                                                        out);
     note_launch();

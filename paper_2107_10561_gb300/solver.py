@@ -146,8 +146,10 @@ class Hierarchy:
 
     @staticmethod
     def _info(inf):
+        hist = [inf.history[i] for i in range(inf.n_history)] if inf.history and inf.n_history > 0 else []
         return dict(iters=inf.iters, restarts=inf.restarts, converged=bool(inf.converged),
-                    rel_res_true=inf.rel_res_true, rel_res_est=inf.rel_res_est)
+                    rel_res_true=inf.rel_res_true, rel_res_est=inf.rel_res_est, history=hist,
+                    ms_total=inf.ms_total)
 
     def gmres_solve(self, b, x, rtol=1e-10, restart=30, max_iter=1000, transpose=False, use_x0=False,
                     stream=None, raise_on_fail=True):
@@ -180,6 +182,28 @@ class Hierarchy:
         """b = b(U, nu) + c(w, w) (which=0), db/dU (1) or db/dnu (2) on the finest level."""
         _lib.check(self.lib.stm_assemble_rhs(self.h, float(U), float(nu), int(which), _ptr(b, self.n_dofs(), "b"),
                                              _stream(stream)), "stm_assemble_rhs")
+
+    def assemble_load(self, U, nu, b, w=None, stream=None):
+        """b = b(U, nu) + c(w, w) on the finest level for the linearisation point w (device DoF vector;
+        None: the point of the last assemble_jacobian)."""
+        n = self.n_dofs()
+        _lib.check(self.lib.stm_assemble_load(self.h, float(U), float(nu), None if w is None else _ptr(w, n, "w"),
+                                              _ptr(b, n, "b"), _stream(stream)), "stm_assemble_load")
+
+    def adjoint_gradient(self, U, nu, j, X, lam=None, rtol=1e-12, restart=30, max_iter=1000, stream=None):
+        """(dJ/dU, dJ/dnu, info) of J = j . X for the Newton step J(w; nu) X = b(U, nu) + c(w, w): the
+        library solves J^T lambda = j and forms lambda . db/dU and lambda . (db/dnu - (dJ/dnu) X)."""
+        n = self.n_dofs()
+        o = self._opts(restart, max_iter, rtol, True, False)
+        inf = _lib.SolveInfo()
+        gU, gnu = C.c_double(), C.c_double()
+        st = self.lib.stm_adjoint_gradient(self.h, float(U), float(nu), _ptr(j, n, "j"), _ptr(X, n, "X"), C.byref(o),
+                                           C.byref(inf), None if lam is None else _ptr(lam, n, "lambda"),
+                                           C.byref(gU), C.byref(gnu), _stream(stream))
+        info = self._info(inf)
+        info["status"] = _lib.STATUS_NAMES.get(st, st)
+        _lib.check(st, "stm_adjoint_gradient")
+        return gU.value, gnu.value, info
 
     def newton_solve(self, X, U, nu=None, max_newton=20, max_halvings=8, abs_tol=1e-10, reduction=1e4,
                      rtol=1e-10, restart=30, max_iter=1000, prev=None, stream=None, raise_on_fail=True):
@@ -214,7 +238,7 @@ class Hierarchy:
             infos.append(self.newton_solve(X, U, prev=prev, **newton_kw))
             states.append(X)
             if j is not None:
-                values.append(float(torch.dot(j, X)))
+                values.append(self.dot(j, X))
             prev = X
         return states, infos, values
 

@@ -48,6 +48,23 @@ def lattice_to_gpu(h, state, level=None):
     return torch.from_numpy(np.ascontiguousarray(state.reshape(-1)[idx])).cuda()
 
 
+def round_bf16(a):
+    """FP64 -> the nearest BF16 value (8 significant bits, ties to even), returned in FP64: one
+    rounding straight from FP64. Normal BF16 range only (no BF16 subnormals)."""
+    a = np.asarray(a, dtype=np.float64)
+    m, e = np.frexp(a)  # a = m 2^e, 0.5 <= |m| < 1; m * 256 is exact and np.rint rounds ties to even
+    return np.ldexp(np.rint(m * 256.0) / 256.0, e)
+
+
+def round_storage(inv, prec):
+    """Cell inverses rounded to their storage precision (FP64 values)."""
+    if prec == "f32":
+        return inv.astype(np.float32).astype(np.float64)
+    if prec == "bf16":
+        return round_bf16(inv)
+    return inv
+
+
 def rel_max(a, b):
     a, b = np.asarray(a), np.asarray(b)
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)

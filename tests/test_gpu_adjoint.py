@@ -89,3 +89,48 @@ def test_autograd_gradients_c4_2d_k1():
     assert abs(float(U.grad) - fdU) <= 1e-5 * abs(fdU), (float(U.grad), fdU)
     assert abs(float(nu.grad) - fdnu) <= 1e-5 * abs(fdnu), (float(nu.grad), fdnu)
     h.close()
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+def test_assemble_load_at_an_explicit_point(name):
+    """stm_assemble_load(U, nu, w): b(U, nu) + c(w, w) for a point w other than the assembled one equals
+    the oracle's Newton-step load at w, and leaves the assembled Jacobian untouched."""
+    from oracle import adjoint
+    wl = SMALL[name]
+    lev, X_lin, _ = oracle_fine(wl)
+    h = gpu_hierarchy(wl, factor=False)
+    w2 = X_lin + 0.05 * np.random.default_rng(58).standard_normal(lev.N)
+    x = torch.from_numpy(np.random.default_rng(59).standard_normal(lev.N)).cuda()
+    y0, y1 = torch.empty_like(x), torch.empty_like(x)
+    h.spmv(h.finest, x, y0)
+    b = torch.empty_like(x)
+    h.assemble_load(0.3, wl.nu, b, w=torch.from_numpy(w2).cuda())
+    assert rel_max(b.cpu().numpy(), adjoint.newton_rhs(lev, w2, 0.3, wl.nu, wl.tau)) < 1e-12
+    h.spmv(h.finest, x, y1)
+    assert torch.equal(y0, y1)
+    h.assemble_load(0.3, wl.nu, b)  # w = the assembled point
+    assert rel_max(b.cpu().numpy(), adjoint.newton_rhs(lev, X_lin, 0.3, wl.nu, wl.tau)) < 1e-12
+    h.close()
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+def test_adjoint_gradient_entry_point(name):
+    """stm_adjoint_gradient (adjoint FGMRES solve and the two gradient combinations inside the library)
+    against the oracle's adjoint gradient from direct solves; lambda against the oracle's J^T solve."""
+    from oracle import adjoint
+    wl = SMALL[name]
+    lev, X_lin, j = oracle_fine(wl)
+    h = gpu_hierarchy(wl)
+    U = 0.3
+    b = torch.empty(lev.N, dtype=torch.float64, device="cuda")
+    h.assemble_load(U, wl.nu, b)
+    X = torch.zeros_like(b)
+    h.gmres_solve(b, X, rtol=1e-13)
+    lam = torch.empty_like(b)
+    gU, gnu, info = h.adjoint_gradient(U, wl.nu, torch.from_numpy(j).cuda(), X, lam=lam, rtol=1e-13)
+    assert info["converged"] and info["history"] and info["history"][0] == pytest.approx(1.0)
+    Jo, gUo, gnuo, _, lam_o = adjoint.adjoint_gradient(lev, X_lin, U, wl.nu, wl.tau, j)
+    assert abs(gU - gUo) <= 1e-7 * abs(gUo), (gU, gUo)
+    assert abs(gnu - gnuo) <= 1e-7 * abs(gnuo), (gnu, gnuo)
+    assert rel_max(lam.cpu().numpy(), lam_o) < 1e-8
+    h.close()

@@ -2,7 +2,8 @@
 the oracle.
 
 One multi-RHS smoothing step equals, column by column, the oracle's additive sweep taken with the
-cell inverses the GPU stores (converted to FP64), and the single-RHS GPU step: to 1e-12 with FP64
+oracle's cell inverses rounded to the storage precision (one rounding from FP64), and the
+single-RHS GPU step: to 1e-12 with FP64
 inverses (same arithmetic, other summation order), 1e-5 with FP32 inverses (FP32 accumulation),
 and 1e-4 with BF16 inverses on the tensor cores (the gathered block enters as two BF16 parts, i.e.
 to about 2^-16 relative; FP32 accumulation). The lock-stepped FGMRES reaches the same solutions as
@@ -51,15 +52,16 @@ def test_multi_sweep_equals_single_sweeps(name, prec, nrhs):
 @pytest.mark.parametrize("nrhs", [32, 7])
 def test_multi_sweep_against_oracle(name, prec, nrhs):
     """Every column of one multi-RHS additive step against oracle.solvers.vanka_step (Eq. LocVanka,
-    damped, multiplicity-weighted) on the oracle's J with the inverses as stored on the GPU."""
-    from helpers import oracle_hierarchy
+    damped, multiplicity-weighted) on the oracle's J, with the oracle's inverses rounded to the
+    storage precision as the GPU stores them."""
+    from helpers import oracle_hierarchy, round_storage
     from oracle import solvers
     wl = CASES[name]
     o = oracle_hierarchy(wl)
     h = gpu_hierarchy(wl, prec)
     g = h.finest
     lev = o.fine
-    inv = h.copy_cell_inverses(g)
+    inv = round_storage(o.inv[-1], prec)
     rng = np.random.default_rng(65)
     R = rng.standard_normal((nrhs, lev.N))
     D = rng.standard_normal((nrhs, lev.N))

@@ -258,8 +258,8 @@ def test_single_sweep_mixed_precision(name, prec):
     rng = np.random.default_rng(38)
     r = rng.standard_normal(lev.N)
     d = rng.standard_normal(lev.N)
-    dt = torch.bfloat16 if prec == "bf16" else torch.float32
-    inv_r = torch.from_numpy(o.inv[g]).to(dt).double().numpy()
+    from helpers import round_storage
+    inv_r = round_storage(o.inv[g], prec)
     t = (r - o.J[g] @ d).astype(np.float32).astype(np.float64)
     y = np.einsum("cij,cj->ci", inv_r, t[lev.idx])
     corr = np.zeros(lev.N)
