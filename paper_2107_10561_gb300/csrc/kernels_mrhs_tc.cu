@@ -46,7 +46,7 @@ constexpr int kGatherWarps = 8;
 constexpr int kEpiWarp0 = 10;
 constexpr int kStages = 2;          // inverse and B stages
 constexpr int kTmemCols = 256;      // 2 accumulator sets x 2 output tiles x 64 columns
-constexpr uint32_t kPollLimit = 1u << 22;
+constexpr uint64_t kWaitNs = 1000000000ull;  // one second per wait at most
 
 struct TcGeom {
   int n, ld;          // local size, stored rows per column (multiple of 8)
@@ -82,10 +82,20 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait for the phase with the given parity; false (and the error word set) on timeout.
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for the phase with the given parity, for at most kWaitNs of wall time; false (and the error
+// word set) on timeout.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
-  for (uint32_t i = 0; i < kPollLimit; ++i)
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t i = 1;; ++i) {
     if (mbar_try(bar, parity)) return true;
+    if ((i & 255u) == 0 && global_ns() - t0 > kWaitNs) break;
+  }
   atomicOr(err, code);
   return false;
 }
