@@ -491,6 +491,8 @@ static stm_status build_level(const stm_params& p, int g, Level& L, std::vector<
   for (int nd = 0; nd < R; ++nd)
     nbase[nd + 1] = nbase[nd] + (long long)(L.K * d) * ((long long)L.K * d * nn[nd] + (long long)np * ncell[nd]);
   STM_TRY(upload(&L.nbase, nbase));
+  STM_CUDA(cudaMalloc((void**)&L.spmv_work, sizeof(unsigned) * 2));
+  STM_CUDA(cudaMemset(L.spmv_work, 0, sizeof(unsigned) * 2));
   STM_CUDA(cudaMalloc((void**)&L.nval, sizeof(double) * nbase[R]));
   L.nval_len = nbase[R];
   {
@@ -752,7 +754,7 @@ void free_hierarchy(Hierarchy& H) {
   H.cap_stream = nullptr;
   for (Level& L : H.L) {
     void* ptrs[] = {L.idx, L.cell_nodes, L.cell_xyz, L.bmask, L.rank, L.cellrank, L.nn, L.ncell, L.rowptr, L.nbr_ptr, L.nbr,
-                    L.node_cells, L.job_nodes, L.nbase, L.nval, L.pvalT, L.nvalJT, L.pvalJT, L.nval32, L.pval32,
+                    L.node_cells, L.job_nodes, L.nbase, L.spmv_work, L.nval, L.pvalT, L.nvalJT, L.pvalJT, L.nval32, L.pval32,
                     L.nvalJT32, L.pvalJT32, L.x32,
                     L.colidx, L.val, L.valT, L.ref, L.inj, L.wnod, L.inv, L.wmult, L.own_ptr,
                     L.own_pos, L.last_owner, L.colour_cells, L.Y, L.P_rowptr, L.P_col, L.P_val,
@@ -763,6 +765,7 @@ void free_hierarchy(Hierarchy& H) {
   }
   void* hp[] = {H.cinv, H.cpart, H.dflag, H.dkerr, H.dbad, H.V, H.Z, H.w, H.hcol, H.part, H.yvec, H.bbuf, H.xbuf,
                 H.nw_negF, H.nw_D, H.nw_Xt, H.nw_B, H.nw_Ft, H.ag_buf, H.ag_wnod,
+                H.cs_off, H.cs_pos, H.cs_rowslab, H.cs_perm, H.cs_store, H.cs_u, H.cs_v, H.cs_mu, H.cs_mv,
                 H.mV, H.mZ, H.mW, H.mB, H.mX, H.mh, H.mpart, H.mf, H.my};
   for (void* q : hp)
     if (q) cudaFree(q);

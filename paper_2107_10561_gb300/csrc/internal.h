@@ -138,6 +138,7 @@ struct Level {
   // t = m*nv + j of row pr at pvalT[((pr/32)*d*nv + t)*32 + pr%32] (rows padded to a multiple of 32)
   double* pvalT = nullptr;
   double *nvalJT = nullptr, *pvalJT = nullptr;  // the same two copies for J^T (built with valT)
+  unsigned* spmv_work = nullptr;  // [2] unit counter and finished-CTA count of the FP64 product (zeroed)
   // FP32 copies of nval/pvalT (and of nvalJT/pvalJT) in the same layout, for the V-cycle's defects
   // r - J_g d with defect_precision = STM_F32; null otherwise
   float *nval32 = nullptr, *pval32 = nullptr, *nvalJT32 = nullptr, *pvalJT32 = nullptr;
@@ -192,6 +193,15 @@ struct Hierarchy {
   double* cinv = nullptr;
   long long N0 = 0;
   double* cpart = nullptr;  // [ceil(N0 / kCoarseTChunk)][N0] partial sums of the transposed coarse solve
+  // coarse solve through the block LU factors in x-slab order (large coarse levels; cinv is then not
+  // formed): cs_nx slabs, row offsets cs_off [nx + 1], block offsets cs_pos [6][nx] into cs_store
+  // (S^{-1}, G, W, S^{-T}, P, Q), slab of every permuted row, permuted position of every row; work
+  // vectors for one column and for 32 interleaved columns
+  bool coarse_slab = false;
+  int cs_nx = 0;
+  long long *cs_off = nullptr, *cs_pos = nullptr;
+  int *cs_rowslab = nullptr, *cs_perm = nullptr;
+  double *cs_store = nullptr, *cs_u = nullptr, *cs_v = nullptr, *cs_mu = nullptr, *cs_mv = nullptr;
   int* dflag = nullptr;           // device flags: [0] singular flag, [1..2] bad cell (int64 split)
   int* dkerr = nullptr;           // device error word of the tensor-core pipelines (bounded waits)
   long long* dbad = nullptr;
@@ -290,6 +300,9 @@ stm_status smoother_defect(Hierarchy& H, int g, const double* x, const double* b
 stm_status vanka_step(Hierarchy& H, int g, const double* r, double* d, int transpose,
                       bool d_is_zero, cudaStream_t s, bool d32_current = false);
 stm_status coarse_apply(Hierarchy& H, const double* r, double* d, int transpose, cudaStream_t s);
+// the coarse solve through the slab block-LU factors (kernels_coarse.cu): one column, or 32 interleaved
+stm_status coarse_slab_apply(Hierarchy& H, const double* r, double* d, int transpose, cudaStream_t s);
+stm_status coarse_slab_apply_multi(Hierarchy& H, const double* R, double* D, cudaStream_t s);
 // wnod: nodal linearisation velocity [K][d][R] of the finest level to use instead of the stored one
 stm_status assemble_cellvec(Hierarchy& H, int mode, double U, double nu, const int* wake_lo, const int* wake_hi,
                             double* out, cudaStream_t s, const double* vprev = nullptr, const double* wnod = nullptr);

@@ -1,0 +1,212 @@
+// Direct coarse solve of Algorithm 1 (d_1 = J_1^{-1} r_1, or J_1^{-T} r_1 in the adjoint V-cycle) through
+// the block LU factors of J_1 in x-slab order (kernels_factor.cu), for coarse levels too large for the
+// dense explicit inverse to pay (3D: 18,000 DoFs, 2.6 GB as a dense inverse).
+//
+// In slab order J_1 is block tridiagonal; with S_b the Schur complements and A_{b,c} its blocks,
+//   J_1 = L U,  L: diagonal S_b, sub-diagonal A_{b,b-1};  U: unit diagonal, super-diagonal W_b = S_b^{-1} A_{b,b+1}.
+// Forward solve  J_1 x = r:   z_b = S_b^{-1} r_b (all slabs at once);  y_b = z_b - G_b y_{b-1}, G_b = S_b^{-1} A_{b,b-1};
+//                              x_b = y_b - W_b x_{b+1}.
+// Transposed     J_1^T x = r: w_b = r_b - P_b w_{b-1}, P_b = W_{b-1}^T;  s_b = S_b^{-T} w_b (all slabs);
+//                              x_b = s_b - Q_b x_{b+1}, Q_b = S_b^{-T} A_{b+1,b}^T.
+// Every matrix is stored row-major per block, so each product is a warp-per-row dot product over
+// contiguous rows. The two dependent chains (nx - 1 steps each) run inside one cooperative kernel with
+// a grid-wide barrier between steps; while a step waits at the barrier each warp prefetches into L2 the
+// rows it will read in the next step. About 5x fewer bytes and FP64 FMAs than the explicit inverse.
+// A 32-column variant (interleaved [N][32] multi-vectors, lane = column) serves the multi-RHS V-cycle.
+#include <cooperative_groups.h>
+
+#include "internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace stm {
+namespace {
+
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+struct SlabView {
+  int nx;
+  long long n;
+  const long long* off;   // [nx + 1] first permuted row of every slab
+  const long long* pos;   // [6][nx] block offsets in store: Sinv, G, W, Sinvt, P, Q (-1: absent)
+  const int* rowslab;     // [n] slab of every permuted row
+  const int* perm;        // [n] permuted position of every row of J_1
+  const double* store;
+};
+
+enum { M_SINV = 0, M_G = 1, M_W = 2, M_SINVT = 3, M_P = 4, M_Q = 5 };
+
+// y[row] (-)= sum_k M[row - off_b][k] x[off_c + k] for the rows of slab b (warp per row). NR = 1: one
+// vector; NR = 32: interleaved 32-column vectors, lane = column.
+template <int NR>
+__device__ __forceinline__ void slab_rows(const SlabView& S, const double* M, int b, int c, const double* x,
+                                          double* y, bool subtract, long long w0, long long nw, int lane) {
+  const long long r0 = S.off[b], nb = S.off[b + 1] - r0;
+  const long long c0 = S.off[c], nc = S.off[c + 1] - c0;
+  for (long long rr = w0; rr < nb; rr += nw) {
+    const double* m = M + rr * nc;
+    double acc = 0.0;
+    if (NR == 1) {
+      for (long long k = lane; k < nc; k += 32) acc = fma(__ldg(m + k), x[c0 + k], acc);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) y[r0 + rr] = subtract ? y[r0 + rr] - acc : acc;
+    } else {
+      for (long long k = 0; k < nc; ++k) acc = fma(__ldg(m + k), x[(c0 + k) * 32 + lane], acc);
+      double* o = y + (r0 + rr) * 32 + lane;
+      *o = subtract ? *o - acc : acc;
+    }
+  }
+}
+
+// Prefetch into L2 the rows of block M (slab b, columns of slab c) that warp w0 will read.
+__device__ __forceinline__ void slab_prefetch(const SlabView& S, const double* M, int b, int c, long long w0,
+                                              long long nw, int lane) {
+  const long long nb = S.off[b + 1] - S.off[b], nc = S.off[c + 1] - S.off[c];
+  for (long long rr = w0; rr < nb; rr += nw) {
+    const char* row = reinterpret_cast<const char*>(M + rr * nc);
+    const long long bytes = nc * 8;
+    for (long long o = (long long)lane * 128; o < bytes; o += 32 * 128) prefetch_l2(row + o);
+  }
+}
+
+template <int NR>
+__global__ void __launch_bounds__(256) k_coarse_slab(SlabView S, const double* __restrict__ r, double* __restrict__ d,
+                                                     double* __restrict__ u, double* __restrict__ v, int transpose) {
+  cg::grid_group grid = cg::this_grid();
+  const int lane = threadIdx.x & 31;
+  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nt = (long long)gridDim.x * blockDim.x;
+  const int nx = S.nx;
+  auto mat = [&](int kind, int b) -> const double* { return S.store + S.pos[kind * nx + b]; };
+  // gather into slab order
+  for (long long e = gt; e < S.n * NR; e += nt) {
+    const long long i = e / NR;
+    u[(long long)S.perm[i] * NR + (e - i * NR)] = r[e];
+  }
+  grid.sync();
+  if (!transpose) {
+    // z_b = S_b^{-1} r_b for every slab: every warp takes rows across all slabs
+    for (long long row = gw; row < S.n; row += nw) {
+      const int b = S.rowslab[row];
+      const long long nb = S.off[b + 1] - S.off[b];
+      const double* m = mat(M_SINV, b) + (row - S.off[b]) * nb;
+      const long long c0 = S.off[b];
+      if (NR == 1) {
+        double acc = 0.0;
+        for (long long k = lane; k < nb; k += 32) acc = fma(__ldg(m + k), u[c0 + k], acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) v[row] = acc;
+      } else {
+        double acc = 0.0;
+        for (long long k = 0; k < nb; ++k) acc = fma(__ldg(m + k), u[(c0 + k) * 32 + lane], acc);
+        v[row * 32 + lane] = acc;
+      }
+    }
+    if (nx > 1) slab_prefetch(S, mat(M_G, 1), 1, 0, gw, nw, lane);
+    grid.sync();
+    for (int b = 1; b < nx; ++b) {  // y_b = z_b - G_b y_{b-1}
+      slab_rows<NR>(S, mat(M_G, b), b, b - 1, v, v, true, gw, nw, lane);
+      if (b + 1 < nx) slab_prefetch(S, mat(M_G, b + 1), b + 1, b, gw, nw, lane);
+      else slab_prefetch(S, mat(M_W, nx - 2), nx - 2, nx - 1, gw, nw, lane);
+      grid.sync();
+    }
+    for (int b = nx - 2; b >= 0; --b) {  // x_b = y_b - W_b x_{b+1}
+      slab_rows<NR>(S, mat(M_W, b), b, b + 1, v, v, true, gw, nw, lane);
+      if (b > 0) slab_prefetch(S, mat(M_W, b - 1), b - 1, b, gw, nw, lane);
+      grid.sync();
+    }
+  } else {
+    if (nx > 1) slab_prefetch(S, mat(M_P, 1), 1, 0, gw, nw, lane);
+    for (int b = 1; b < nx; ++b) {  // w_b = r_b - P_b w_{b-1}
+      slab_rows<NR>(S, mat(M_P, b), b, b - 1, u, u, true, gw, nw, lane);
+      if (b + 1 < nx) slab_prefetch(S, mat(M_P, b + 1), b + 1, b, gw, nw, lane);
+      grid.sync();
+    }
+    for (long long row = gw; row < S.n; row += nw) {  // s_b = S_b^{-T} w_b
+      const int b = S.rowslab[row];
+      const long long nb = S.off[b + 1] - S.off[b];
+      const double* m = mat(M_SINVT, b) + (row - S.off[b]) * nb;
+      const long long c0 = S.off[b];
+      if (NR == 1) {
+        double acc = 0.0;
+        for (long long k = lane; k < nb; k += 32) acc = fma(__ldg(m + k), u[c0 + k], acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) v[row] = acc;
+      } else {
+        double acc = 0.0;
+        for (long long k = 0; k < nb; ++k) acc = fma(__ldg(m + k), u[(c0 + k) * 32 + lane], acc);
+        v[row * 32 + lane] = acc;
+      }
+    }
+    if (nx > 1) slab_prefetch(S, mat(M_Q, nx - 2), nx - 2, nx - 1, gw, nw, lane);
+    grid.sync();
+    for (int b = nx - 2; b >= 0; --b) {  // x_b = s_b - Q_b x_{b+1}
+      slab_rows<NR>(S, mat(M_Q, b), b, b + 1, v, v, true, gw, nw, lane);
+      if (b > 0) slab_prefetch(S, mat(M_Q, b - 1), b - 1, b, gw, nw, lane);
+      grid.sync();
+    }
+  }
+  // back to the row order of J_1
+  for (long long e = gt; e < S.n * NR; e += nt) {
+    const long long i = e / NR;
+    d[e] = v[(long long)S.perm[i] * NR + (e - i * NR)];
+  }
+}
+
+template <int NR>
+stm_status launch_slab(Hierarchy& H, const double* r, double* d, int transpose, cudaStream_t s) {
+  static int occ = 0;
+  if (!occ) {
+    STM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_coarse_slab<NR>, 256, 0));
+    if (occ < 1) {
+      set_error("coarse slab solve: kernel does not fit on an SM");
+      return STM_ERR_CUDA;
+    }
+  }
+  SlabView S;
+  S.nx = H.cs_nx;
+  S.n = H.N0;
+  S.off = H.cs_off;
+  S.pos = H.cs_pos;
+  S.rowslab = H.cs_rowslab;
+  S.perm = H.cs_perm;
+  S.store = H.cs_store;
+  double* u = NR == 1 ? H.cs_u : H.cs_mu;
+  double* v = NR == 1 ? H.cs_v : H.cs_mv;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(std::min(occ, 2) * sm_count()));
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  STM_CUDA(cudaLaunchKernelEx(&cfg, k_coarse_slab<NR>, S, r, d, u, v, transpose));
+  note_launch();
+  return STM_OK;
+}
+
+}  // namespace
+
+stm_status coarse_slab_apply(Hierarchy& H, const double* r, double* d, int transpose, cudaStream_t s) {
+  return launch_slab<1>(H, r, d, transpose, s);
+}
+
+stm_status coarse_slab_apply_multi(Hierarchy& H, const double* R, double* D, cudaStream_t s) {
+  if (!H.cs_mu) {
+    STM_CUDA(cudaMalloc(&H.cs_mu, sizeof(double) * 32 * (size_t)H.N0));
+    STM_CUDA(cudaMalloc(&H.cs_mv, sizeof(double) * 32 * (size_t)H.N0));
+  }
+  return launch_slab<32>(H, R, D, 0, s);
+}
+
+}  // namespace stm

@@ -415,6 +415,25 @@ __global__ void k_unpermute(const double* __restrict__ Xp, const int* __restrict
   }
 }
 
+// dst (cols x rows) = src^T (src rows x cols, both row-major)
+__global__ void k_transpose(const double* __restrict__ src, long long rows, long long cols, double* __restrict__ dst) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < rows * cols;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / cols, j = e - i * cols;
+    dst[j * rows + i] = src[e];
+  }
+}
+static void transpose_block(const double* src, long long rows, long long cols, double* dst, cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return;
+  k_transpose<<<(int)std::min<long long>((rows * cols + 255) / 256, sm_count() * 8LL), 256, 0, s>>>(src, rows, cols, dst);
+  note_launch();
+}
+
+// Coarse levels from this size on are solved through the slab block-LU factors instead of an explicit
+// inverse: the dense inverse costs N^2 FP64 FMAs per solve (0.5 ms at 18,000 DoFs), the factors about a
+// fifth of that plus two chains of nx - 1 dependent slab products.
+constexpr long long kCoarseSlabMinDofs = 8000;
+
 // Slab ordering of level 0 (host, once).
 static void coarse_slabs(const Level& L, std::vector<int>& iperm, std::vector<int>& blk, std::vector<long long>& off) {
   const int d = L.dim, nx = L.cells[0];
@@ -449,6 +468,7 @@ stm_status factor_coarse(Hierarchy& H, cudaStream_t s) {
   const long long n = L.N;
   const int nx = L.cells[0];
   H.N0 = n;
+  const bool use_slab = n >= kCoarseSlabMinDofs && nx >= 2;
   std::vector<int> iperm, blk;
   std::vector<long long> off;
   coarse_slabs(L, iperm, blk, off);
@@ -477,21 +497,21 @@ stm_status factor_coarse(Hierarchy& H, cudaStream_t s) {
     if (cudaMalloc(&d_iperm, sizeof(int) * n) || cudaMalloc(&d_blk, sizeof(int) * n) ||
         cudaMalloc(&d_off, sizeof(long long) * (nx + 2)) || cudaMalloc(&d_dpos, sizeof(long long) * nx) ||
         cudaMalloc(&d_lpos, sizeof(long long) * nx) || cudaMalloc(&d_upos, sizeof(long long) * nx) ||
-        cudaMalloc(&store, sizeof(double) * tot) || cudaMalloc(&Xp, sizeof(double) * n * n) ||
+        cudaMalloc(&store, sizeof(double) * tot) || (!use_slab && cudaMalloc(&Xp, sizeof(double) * n * n)) ||
         cudaMalloc(&piv, sizeof(int) * maxnb) || cudaMalloc(&scal, sizeof(double) * 2)) {
       cudaGetLastError();
       set_error("coarse factorisation: out of device memory");
       fail(STM_ERR_OOM);
       break;
     }
-    if (!H.cinv && cudaMalloc(&H.cinv, sizeof(double) * n * n)) {
+    if (!use_slab && !H.cinv && cudaMalloc(&H.cinv, sizeof(double) * n * n)) {
       cudaGetLastError();
       set_error("coarse factorisation: out of device memory");
       fail(STM_ERR_OOM);
       break;
     }
     // scratch of the transposed coarse solve, allocated here so that solves can be graph-captured
-    if (!H.cpart && cudaMalloc(&H.cpart, sizeof(double) * ((n + kCoarseTChunk - 1) / kCoarseTChunk) * n)) {
+    if (!use_slab && !H.cpart && cudaMalloc(&H.cpart, sizeof(double) * ((n + kCoarseTChunk - 1) / kCoarseTChunk) * n)) {
       cudaGetLastError();
       set_error("coarse factorisation: out of device memory");
       fail(STM_ERR_OOM);
@@ -504,7 +524,7 @@ stm_status factor_coarse(Hierarchy& H, cudaStream_t s) {
     cudaMemcpyAsync(d_lpos, lpos.data(), sizeof(long long) * nx, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(d_upos, upos.data(), sizeof(long long) * nx, cudaMemcpyHostToDevice, s);
     cudaMemsetAsync(store, 0, sizeof(double) * tot, s);
-    cudaMemsetAsync(Xp, 0, sizeof(double) * n * n, s);
+    if (Xp) cudaMemsetAsync(Xp, 0, sizeof(double) * n * n, s);
     k_slab_blocks<<<(int)std::min<long long>(n, sm_count() * 32LL), 128, 0, s>>>(L.rowptr, L.colidx, L.val, n, d_iperm, d_blk,
                                                                           d_off, d_dpos, d_lpos, d_upos, store,
                                                                           H.dflag + 1);
@@ -536,6 +556,73 @@ stm_status factor_coarse(Hierarchy& H, cudaStream_t s) {
         const long long np_ = off[b] - off[b - 1];
         dgemm((int)nb, (int)np_, (int)nb, 1.0, Db, nb, store + lpos[b], np_, 0.0, store + gpos[b], np_, s);
       }
+    }
+    if (use_slab) {
+      // keep the factors: S_b^{-1}, G_b, W_b for J_0 x = r and S_b^{-T}, P_b = W_{b-1}^T,
+      // Q_b = (A_{b+1,b} S_b^{-1})^T for J_0^T x = r, row-major per block
+      enum { M_SINV = 0, M_G, M_W, M_SINVT, M_P, M_Q };
+      std::vector<long long> cpos(6 * (size_t)nx, -1);
+      long long ct = 0, maxe = 0;
+      for (int b = 0; b < nx; ++b) {
+        const long long nb = off[b + 1] - off[b];
+        const long long npv = b > 0 ? off[b] - off[b - 1] : 0, nnx = b + 1 < nx ? off[b + 2] - off[b + 1] : 0;
+        cpos[M_SINV * nx + b] = ct; ct += nb * nb;
+        if (npv) { cpos[M_G * nx + b] = ct; ct += nb * npv; }
+        if (nnx) { cpos[M_W * nx + b] = ct; ct += nb * nnx; }
+        cpos[M_SINVT * nx + b] = ct; ct += nb * nb;
+        if (npv) { cpos[M_P * nx + b] = ct; ct += nb * npv; }
+        if (nnx) { cpos[M_Q * nx + b] = ct; ct += nb * nnx; maxe = std::max(maxe, nb * nnx); }
+      }
+      double* E = nullptr;
+      if ((!H.cs_store && cudaMalloc(&H.cs_store, sizeof(double) * ct)) || cudaMalloc(&E, sizeof(double) * std::max(maxe, 1LL)) ||
+          (!H.cs_u && cudaMalloc(&H.cs_u, sizeof(double) * n)) || (!H.cs_v && cudaMalloc(&H.cs_v, sizeof(double) * n))) {
+        cudaGetLastError();
+        if (E) cudaFree(E);
+        set_error("coarse factorisation: out of device memory");
+        fail(STM_ERR_OOM);
+        break;
+      }
+      for (int b = 0; b < nx; ++b) {
+        const long long nb = off[b + 1] - off[b];
+        const long long npv = b > 0 ? off[b] - off[b - 1] : 0, nnx = b + 1 < nx ? off[b + 2] - off[b + 1] : 0;
+        double* cs = H.cs_store;
+        const int cb = (int)std::min<long long>((nb * nb + 255) / 256, sm_count() * 8LL);
+        k_copy_block<<<cb, 256, 0, s>>>(store + dpos[b], nb, nb, nb, cs + cpos[M_SINV * nx + b], nb);
+        note_launch();
+        transpose_block(store + dpos[b], nb, nb, cs + cpos[M_SINVT * nx + b], s);
+        if (npv) {
+          k_copy_block<<<cb, 256, 0, s>>>(store + gpos[b], nb, npv, npv, cs + cpos[M_G * nx + b], npv);
+          note_launch();
+          // P_b = W_{b-1}^T: W_{b-1} is nb_{b-1} x nb_b
+          transpose_block(store + wpos[b - 1], npv, nb, cs + cpos[M_P * nx + b], s);
+        }
+        if (nnx) {
+          k_copy_block<<<cb, 256, 0, s>>>(store + wpos[b], nb, nnx, nnx, cs + cpos[M_W * nx + b], nnx);
+          note_launch();
+          // E = A_{b+1,b} S_b^{-1} (nb_{b+1} x nb_b), Q_b = E^T
+          dgemm((int)nnx, (int)nb, (int)nb, 1.0, store + lpos[b + 1], nb, store + dpos[b], nb, 0.0, E, nb, s);
+          transpose_block(E, nnx, nb, cs + cpos[M_Q * nx + b], s);
+        }
+      }
+      std::vector<long long> hoff(off.begin(), off.begin() + nx + 1);
+      if (!H.cs_off) cudaMalloc(&H.cs_off, sizeof(long long) * (nx + 1));
+      if (!H.cs_pos) cudaMalloc(&H.cs_pos, sizeof(long long) * 6 * nx);
+      if (!H.cs_rowslab) cudaMalloc(&H.cs_rowslab, sizeof(int) * n);
+      if (!H.cs_perm) cudaMalloc(&H.cs_perm, sizeof(int) * n);
+      cudaMemcpyAsync(H.cs_off, hoff.data(), sizeof(long long) * (nx + 1), cudaMemcpyHostToDevice, s);
+      cudaMemcpyAsync(H.cs_pos, cpos.data(), sizeof(long long) * 6 * nx, cudaMemcpyHostToDevice, s);
+      cudaMemcpyAsync(H.cs_rowslab, blk.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s);
+      cudaMemcpyAsync(H.cs_perm, iperm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s);
+      const cudaError_t e1 = cudaGetLastError(), e2 = cudaStreamSynchronize(s);
+      cudaFree(E);
+      if (e1 != cudaSuccess || e2 != cudaSuccess) {
+        set_error("coarse factorisation: CUDA error");
+        fail(STM_ERR_CUDA);
+        break;
+      }
+      H.cs_nx = nx;
+      H.coarse_slab = true;
+      break;
     }
     // Z = L^{-1} (block lower triangular) into the block rows of Xp
     for (int b = 0; b < nx; ++b) {

@@ -172,6 +172,10 @@ __global__ void k_dense_gemv_t_sum(const double* __restrict__ part, long long n,
 
 stm_status coarse_apply(Hierarchy& H, const double* r, double* d, int transpose, cudaStream_t s) {
   const long long n = H.N0;
+  if (H.coarse_slab) {
+    ProfScope ps(&H, STM_KCLASS_COARSE, s, 0.0);
+    return coarse_slab_apply(H, r, d, transpose, s);
+  }
   ProfScope ps(&H, STM_KCLASS_COARSE, s, 8.0 * (double)n * (double)n + 16.0 * (double)n);
   if (!transpose) {
     const int blocks = (int)std::min<long long>((n + 7) / 8, (long long)sms() * 16);

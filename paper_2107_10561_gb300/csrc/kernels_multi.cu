@@ -335,11 +335,15 @@ stm_status vcycle_multi(Hierarchy& H, const double* R_fine, double* D_fine, cuda
     r = Lc.mr;
   }
   {
-    ProfScope ps(&H, STM_KCLASS_COARSE, s, 8.0 * (double)H.N0 * H.N0);
-    const int blocks = (int)std::min<long long>((H.N0 * 32 + 255) / 256, (long long)msms() * 8);
-    k_dense_gemm_multi<<<blocks, 256, 0, s>>>(H.cinv, H.N0, r, H.L[0].md);
-    note_launch();
-    STM_CUDA(cudaGetLastError());
+    ProfScope ps(&H, STM_KCLASS_COARSE, s, H.coarse_slab ? 0.0 : 8.0 * (double)H.N0 * H.N0);
+    if (H.coarse_slab) {
+      STM_TRY(coarse_slab_apply_multi(H, r, H.L[0].md, s));
+    } else {
+      const int blocks = (int)std::min<long long>((H.N0 * 32 + 255) / 256, (long long)msms() * 8);
+      k_dense_gemm_multi<<<blocks, 256, 0, s>>>(H.cinv, H.N0, r, H.L[0].md);
+      note_launch();
+      STM_CUDA(cudaGetLastError());
+    }
   }
   for (int g = 1; g < G; ++g) {
     Level& L = H.L[g];

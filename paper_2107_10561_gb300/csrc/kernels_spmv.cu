@@ -23,13 +23,13 @@ namespace stm {
 
 __host__ __device__ constexpr int pow2ceil(int v) { return v <= 1 ? 1 : 2 * pow2ceil((v + 1) / 2); }
 
-// Reduce-scatter over the VL lanes of a group: on entry every lane holds NA partial sums; on exit
-// acc[0] of lane L holds the full group sum of accumulator scatter_index(L). Each halving step
-// trades half of the accumulators with the partner lane, so the FP64 adds total NA - 1 + the
-// remaining log2(VL/NA) steps instead of NA * log2(VL).
+// Reduce-scatter over the VL lanes of a group: on entry every lane holds NA partial sums; each halving
+// step trades half of the accumulators still held with the partner lane. With NA <= VL, acc[0] of lane
+// L ends as the full group sum of accumulator scatter_index(L) (NA - 1 + the remaining log2(VL/NA)
+// adds instead of NA * log2(VL)); with NA > VL, acc[0 .. NA/VL - 1] of lane L end as the full sums of
+// accumulators scatter_index(L) + 0 .. NA/VL - 1 (NA (1 - 1/VL) adds).
 template <int VL, int NA, typename T>
 __device__ __forceinline__ void reduce_scatter(T* acc, int lane) {
-  static_assert(NA <= VL, "one accumulator per lane at most");
   int cnt = NA;
 #pragma unroll
   for (int off = VL / 2; off >= 1; off >>= 1) {
@@ -323,6 +323,126 @@ __global__ void __launch_bounds__(256, ((sizeof(TV) == 4 && VL > 8) || K < 3) ? 
   }
 }
 
+// FP64 product with work handed out at run time. The work is cut into units: velocity units of GPW
+// nodes (one group of VL lanes per node; job order reversed, so the nodes with most neighbours come
+// first) followed by pressure units of 32 rows (one lane per row). A persistent grid of the resident
+// CTA count takes units from one device counter (lane 0 of a warp fetches, the warp shares it), so every
+// SM stays busy to the last unit and the end of the launch waits for one unit at most; the last CTA to
+// finish resets the counter for the next launch (launches on one hierarchy are serialised). The group
+// sums go through the reduce-scatter above: with more accumulators than lanes (2D), each lane ends with
+// K*d/VL row sums (6 FP64 adds per node with VL = 4, K*d = 6), so the FP64 pipe spends its issue slots
+// on the 2 nnz FMAs.
+template <int VL, int K, int D>
+__global__ void __launch_bounds__(256) k_spmv_nb_dyn(
+    const double* __restrict__ nval, const double* __restrict__ pvalT, const long long* __restrict__ nbase,
+    const int* __restrict__ nbr_ptr, const int* __restrict__ nbr, const int* __restrict__ ncell,
+    const int* __restrict__ node_cells, const int* __restrict__ cell_nodes, const int* __restrict__ job_nodes,
+    long long block, int R, int C, const double* __restrict__ x, const double* __restrict__ b,
+    double* __restrict__ y, int mode, unsigned* __restrict__ work, unsigned nvu, unsigned ntot) {
+  constexpr int GPW = 32 / VL;
+  constexpr int KD = K * D;
+  constexpr int NP = D + 1;
+  constexpr int MAXC = 1 << D;
+  constexpr int NV = D == 2 ? 9 : 27;
+  constexpr int NAV = pow2ceil(KD);
+  constexpr int HOLD = NAV > VL ? NAV / VL : 1;  // row sums each lane holds after the reduce-scatter
+  constexpr int NAV_R = NAV < VL ? NAV : VL;
+  const int lw = threadIdx.x & 31;
+  const int lane = lw & (VL - 1);
+  const int gw = lw / VL;
+  int wmask_v;
+  const int kv = NAV > VL ? scatter_index<VL, NAV>(lane, &wmask_v) : scatter_index<VL, NAV_R>(lane, &wmask_v);
+  for (;;) {
+    unsigned u = 0;
+    if (lw == 0) u = atomicAdd(work, 1u);
+    u = __shfl_sync(0xffffffffu, u, 0);
+    if (u >= ntot) break;
+    if (u < nvu) {
+      const long long job = (long long)(nvu - 1 - u) * GPW + gw;
+      const bool ok = job < R;
+      const int i = ok ? job_nodes[job] : 0;
+      double acc[NAV];
+#pragma unroll
+      for (int r = 0; r < NAV; ++r) acc[r] = 0.0;
+      if (ok) {
+        const int p0 = nbr_ptr[i], nn = nbr_ptr[i + 1] - p0, nc = ncell[i];
+        const double* blk = nval + nbase[i];
+        const int npv = KD * nn;
+        int j = lane, bm = 0;
+        while (j >= nn) { j -= nn; ++bm; }
+        for (int p = lane; p < npv; p += VL) {
+          const int bb = bm / D, m = bm - bb * D;
+          const double xv = __ldg(x + bb * block + (long long)m * R + nbr[p0 + j]);
+          double vv[KD];
+          load_position<KD>(blk + (long long)p * KD, vv);
+#pragma unroll
+          for (int r = 0; r < KD; ++r) acc[r] = fma(vv[r], xv, acc[r]);
+          j += VL;
+          while (j >= nn) { j -= nn; ++bm; }
+        }
+        for (int tq = lane; tq < NP * nc; tq += VL) {
+          const int ci = tq / NP, q = tq - ci * NP;
+          const long long pc = (long long)D * R + (long long)node_cells[(long long)i * MAXC + ci] * NP + q;
+          const double* v = blk + (long long)(npv + tq) * KD;
+#pragma unroll
+          for (int a = 0; a < K; ++a) {
+            const double xp = __ldg(x + a * block + pc);
+#pragma unroll
+            for (int l = 0; l < D; ++l) acc[a * D + l] = fma(__ldcs(v + a * D + l), xp, acc[a * D + l]);
+          }
+        }
+      }
+      reduce_scatter<VL, NAV>(acc, lane);
+      if (ok && (lane & wmask_v) == 0) {
+#pragma unroll
+        for (int h = 0; h < HOLD; ++h) {
+          const int rr = kv + h;
+          if (rr < KD) {
+            const int a = rr / D, l = rr - a * D;
+            const long long row = a * block + (long long)l * R + i;
+            if (mode == 0) y[row] = acc[h];
+            else if (mode == 1) y[row] = b[row] - acc[h];
+            else y[row] += acc[h];
+          }
+        }
+      }
+    } else {
+      // pressure rows pr = (a*C + c)*n_p + q: one lane per row over the warp-transposed copy
+      const long long pr = (long long)(u - nvu) * 32 + lw;
+      const long long npr = (long long)K * C * NP;
+      if (pr < npr) {
+        const int a = (int)(pr / ((long long)C * NP));
+        const long long cq = pr - (long long)a * C * NP;
+        const long long c = cq / NP;
+        const long long row = a * block + (long long)D * R + cq;
+        const double* vr = pvalT + ((pr >> 5) * (D * NV)) * 32 + (pr & 31);
+        const int* cn = cell_nodes + c * NV;
+        const double* xa = x + a * block;
+        double sacc = 0.0;
+#pragma unroll
+        for (int m = 0; m < D; ++m) {
+#pragma unroll 9
+          for (int jj = 0; jj < NV; ++jj)
+            sacc = fma(__ldcs(vr + (m * NV + jj) * 32), __ldg(xa + (long long)m * R + __ldg(cn + jj)), sacc);
+        }
+        if (mode == 0) y[row] = sacc;
+        else if (mode == 1) y[row] = b[row] - sacc;
+        else y[row] += sacc;
+      }
+    }
+  }
+  // the last CTA to finish resets the counter: every warp has fetched a unit past the end by then
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(work + 1, 1u) == gridDim.x - 1) {
+      work[0] = 0u;
+      work[1] = 0u;
+      __threadfence();
+    }
+  }
+}
+
 static int sms_count();
 
 template <typename TV, int VL, int K, int D>
@@ -389,9 +509,57 @@ static stm_status spmv_nodeblock_t(const Level& L, const TV* nval, const TV* pva
   return STM_OK;
 }
 
+template <int VL, int K, int D>
+static stm_status launch_nb_dyn(const Level& L, const double* nval, const double* pvalT, const double* x,
+                                const double* b, double* y, int mode, cudaStream_t s) {
+  constexpr int GPW = 32 / VL;
+  static int occ = 0;  // resident CTAs per SM of this instantiation
+  if (!occ) {
+    STM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_nb_dyn<VL, K, D>, 256, 0));
+    if (occ < 1) occ = 1;
+  }
+  const long long npr = (long long)K * L.C * (D + 1);
+  const unsigned nvu = (unsigned)((L.R + GPW - 1) / GPW);
+  const unsigned ntot = nvu + (unsigned)((npr + 31) / 32);
+  const int blocks = (int)std::max<long long>(1, std::min<long long>((long long)occ * sms_count(), (ntot + 7) / 8));
+  k_spmv_nb_dyn<VL, K, D><<<blocks, 256, 0, s>>>(nval, pvalT, L.nbase, L.nbr_ptr, L.nbr, L.ncell, L.node_cells,
+                                                 L.cell_nodes, L.job_nodes, L.block, L.R, L.C, x, b, y, mode,
+                                                 L.spmv_work, nvu, ntot);
+  note_launch();
+  STM_CUDA(cudaGetLastError());
+  return STM_OK;
+}
+
 stm_status spmv_nodeblock(const Level& L, const double* nval, const double* pvalT, const double* x, const double* b,
                           double* y, int mode, cudaStream_t s) {
-  return spmv_nodeblock_t<double>(L, nval, pvalT, x, b, y, mode, s);
+  // lanes per node as for the static product: short groups on large levels, 16 / 32 on small ones
+  const long long per_sm_threads = 1024;
+  int cls = 0;
+  if ((long long)L.R * (L.dim == 2 ? 4 : 8) < (long long)sms_count() * per_sm_threads) cls = 100;
+  if ((long long)L.R * 16 < (long long)sms_count() * per_sm_threads / 4) cls = 200;
+  switch (L.dim * 10 + L.K + cls) {
+    case 21: return launch_nb_dyn<4, 1, 2>(L, nval, pvalT, x, b, y, mode, s);
+    case 22: return launch_nb_dyn<4, 2, 2>(L, nval, pvalT, x, b, y, mode, s);
+    case 23: return launch_nb_dyn<4, 3, 2>(L, nval, pvalT, x, b, y, mode, s);
+    case 31: return launch_nb_dyn<8, 1, 3>(L, nval, pvalT, x, b, y, mode, s);
+    case 32: return launch_nb_dyn<8, 2, 3>(L, nval, pvalT, x, b, y, mode, s);
+    case 33: return launch_nb_dyn<8, 3, 3>(L, nval, pvalT, x, b, y, mode, s);
+    case 121: return launch_nb_dyn<16, 1, 2>(L, nval, pvalT, x, b, y, mode, s);
+    case 122: return launch_nb_dyn<16, 2, 2>(L, nval, pvalT, x, b, y, mode, s);
+    case 123: return launch_nb_dyn<16, 3, 2>(L, nval, pvalT, x, b, y, mode, s);
+    case 131: return launch_nb_dyn<16, 1, 3>(L, nval, pvalT, x, b, y, mode, s);
+    case 132: return launch_nb_dyn<16, 2, 3>(L, nval, pvalT, x, b, y, mode, s);
+    case 133: return launch_nb_dyn<16, 3, 3>(L, nval, pvalT, x, b, y, mode, s);
+    case 221: return launch_nb_dyn<32, 1, 2>(L, nval, pvalT, x, b, y, mode, s);
+    case 222: return launch_nb_dyn<32, 2, 2>(L, nval, pvalT, x, b, y, mode, s);
+    case 223: return launch_nb_dyn<32, 3, 2>(L, nval, pvalT, x, b, y, mode, s);
+    case 231: return launch_nb_dyn<32, 1, 3>(L, nval, pvalT, x, b, y, mode, s);
+    case 232: return launch_nb_dyn<32, 2, 3>(L, nval, pvalT, x, b, y, mode, s);
+    case 233: return launch_nb_dyn<32, 3, 3>(L, nval, pvalT, x, b, y, mode, s);
+    default:
+      set_error("node-block SpMV: unsupported (dim, k)");
+      return STM_ERR_INVALID_ARG;
+  }
 }
 
 // FP32 copy of an FP64 array (round to nearest)
