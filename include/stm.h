@@ -286,6 +286,19 @@ stm_status stm_vanka_sweep_multi(stm_hierarchy* h, int level, int nrhs, const do
 stm_status stm_gmres_solve_multi(stm_hierarchy* h, int nrhs, const double* B_dev, double* X_dev,
                                  const stm_gmres_opts* opts, stm_solve_info* infos, void* stream);
 
+/* One additive smoothing step (Eq. LocVanka, damped, multiplicity-weighted) on level g >= 1 for n_fwd
+ * right-hand sides of J d = r and n_adj of the adjoint system J^T d = r at once, with one pass over the
+ * stored cell inverses: forward columns get d += omega W sum_T R_T^T J_T^{-1} R_T (r - J d), adjoint
+ * columns d += omega W sum_T R_T^T J_T^{-T} R_T (r - J^T d). With BF16 inverses both local products run
+ * on the tensor cores from the same shared-memory copy of each inverse (read as J_T^{-1} and as J_T^{-T}).
+ * Rf/Df: [n_fwd][n_dofs], Ra/Da: [n_adj][n_dofs], column-major FP64 on the device (D updated in place),
+ * 0 <= n_fwd, n_adj <= 16. Synchronises once at the end (reports a timed-out tensor-core pipeline as
+ * STM_ERR_CUDA). The paper smooths one system at a time; pairing forward and adjoint columns over one read
+ * of the inverses (which dominate the bytes of a sweep, Sec. 4.3) is this library's addition, for a
+ * forward solve and its adjoint that share J. */
+stm_status stm_vanka_sweep_fused(stm_hierarchy* h, int level, int n_fwd, const double* Rf_dev, double* Df_dev,
+                                 int n_adj, const double* Ra_dev, double* Da_dev, void* stream);
+
 /* Copies of internal data for verification (synchronous, caller-owned host buffers):
  * the CSR of J_g (rowptr: n_dofs+1, colidx/val: nnz) and the cell inverses of level g >= 1 as
  * FP64, row-major per cell ([n_cells][n][n], converted from the stored precision). */

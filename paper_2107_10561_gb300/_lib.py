@@ -79,6 +79,7 @@ SIGNATURES = {
     "stm_dot": ([_P, _P, _P, _L, _DP, _P], _I),
     "stm_vanka_sweep_multi": ([_P, _I, _I, _P, _P, _P], _I),
     "stm_gmres_solve_multi": ([_P, _I, _P, _P, C.POINTER(GmresOpts), C.POINTER(SolveInfo), _P], _I),
+    "stm_vanka_sweep_fused": ([_P, _I, _I, _P, _P, _I, _P, _P, _P], _I),
     "stm_copy_jacobian": ([_P, _I, _LP, _IP, _DP], _I),
     "stm_copy_cell_inverses": ([_P, _I, _DP], _I),
     "stm_vanka_apply_noalloc": ([_L, _I, _L, _P, _P, _P, _P, _D, _P], _I),

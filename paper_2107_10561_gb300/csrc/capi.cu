@@ -644,6 +644,35 @@ stm_status stm_vanka_sweep_multi(stm_hierarchy* h, int level, int nrhs, const do
   return check_kernel_error(H, s);
 }
 
+stm_status stm_vanka_sweep_fused(stm_hierarchy* h, int level, int n_fwd, const double* Rf_dev, double* Df_dev,
+                                 int n_adj, const double* Ra_dev, double* Da_dev, void* stream) {
+  if (!h) return bad_arg("NULL argument");
+  if (n_fwd < 0 || n_fwd > 16 || n_adj < 0 || n_adj > 16 || n_fwd + n_adj < 1)
+    return bad_arg("n_fwd and n_adj must be in [0, 16], at least one column");
+  if ((n_fwd && (!Rf_dev || !Df_dev)) || (n_adj && (!Ra_dev || !Da_dev))) return bad_arg("NULL argument");
+  STM_TRY(need_level(h->H, level, 1));
+  if (!h->H.factored) {
+    set_error("vanka_sweep_fused before factor_cells");
+    return STM_ERR_STATE;
+  }
+  Hierarchy& H = h->H;
+  if (H.p.smoother != STM_VANKA_ADDITIVE) return bad_arg("the fused smoothing step implements the additive smoother");
+  STM_TRY(ensure_multi(H));
+  Level& L = H.L[level];
+  cudaStream_t s = S(stream);
+  // interleaved block: columns 0-15 forward, 16-31 adjoint (unused columns zero)
+  STM_CUDA(cudaMemsetAsync(L.mr, 0, sizeof(double) * (size_t)L.N * 32, s));
+  STM_CUDA(cudaMemsetAsync(L.md, 0, sizeof(double) * (size_t)L.N * 32, s));
+  STM_TRY(multi_columns_in(Rf_dev, L.mr, L.N, n_fwd, 0, s));
+  STM_TRY(multi_columns_in(Df_dev, L.md, L.N, n_fwd, 0, s));
+  STM_TRY(multi_columns_in(Ra_dev, L.mr, L.N, n_adj, 16, s));
+  STM_TRY(multi_columns_in(Da_dev, L.md, L.N, n_adj, 16, s));
+  STM_TRY(vanka_step_multi(H, level, L.mr, L.md, false, s, 16));
+  STM_TRY(multi_columns_out(L.md, Df_dev, L.N, n_fwd, 0, s));
+  STM_TRY(multi_columns_out(L.md, Da_dev, L.N, n_adj, 16, s));
+  return check_kernel_error(H, s);
+}
+
 static stm_status ensure_krylov_multi(Hierarchy& H, int m) {
   const size_t N = (size_t)H.L.back().N, NRs = 32;
   if (H.mrestart_cap >= m && H.mV) return STM_OK;

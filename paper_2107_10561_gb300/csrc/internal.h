@@ -312,13 +312,24 @@ stm_status dnu_apply(Hierarchy& H, const double* x, double* y, cudaStream_t s);
 // multi-right-hand-side path (kernels_multi.cu), multi-vectors interleaved [N][32]
 stm_status multi_to_interleaved(const double* src, double* dst, long long N, int nrhs, cudaStream_t s);
 stm_status multi_from_interleaved(const double* src, double* dst, long long N, int nrhs, cudaStream_t s);
-stm_status spmm_structured(const Level& L, const double* X, const double* B, double* Y, int mode, cudaStream_t s);
+// columns [col0, col0 + ncols) of an interleaved [N][32] block from / to a column-major [ncols][N] array
+stm_status multi_columns_in(const double* src, double* dst, long long N, int ncols, int col0, cudaStream_t s);
+stm_status multi_columns_out(const double* src, double* dst, long long N, int ncols, int col0, cudaStream_t s);
+// columns split..31 use J^T (L.valT, which must exist when split < 32)
+stm_status spmm_structured(const Level& L, const double* X, const double* B, double* Y, int mode, cudaStream_t s,
+                           int split = 32);
 stm_status ensure_multi(Hierarchy& H);
-stm_status vanka_step_multi(Hierarchy& H, int g, const double* R, double* Dm, bool d_is_zero, cudaStream_t s);
+// split < 32: columns split..31 are adjoint columns (defect with J^T, local products with J_T^{-T});
+// with split = 16 and BF16 inverses on the tensor cores both come from one pass over the inverses
+stm_status vanka_step_multi(Hierarchy& H, int g, const double* R, double* Dm, bool d_is_zero, cudaStream_t s,
+                            int split = 32);
 // Y[c][i][32] (FP32) = J_c^{-1} T_c on the tcgen05 tensor cores, BF16 inverses of leading dimension ld
 // (kernels_mrhs_tc.cu); err: device word set when a pipeline wait times out
+// fused = true: columns 0-15 get Y = J^{-1} T, columns 16-31 Y = J^{-T} T from the same inverse tile
 bool mrhs_tc_supported(int n, int ld);
-stm_status mrhs_tc_apply(const Level& L, int ld, const double* T, float* Y, int* err, cudaStream_t s);
+bool mrhs_tc_fused_supported(int n, int ld);
+stm_status mrhs_tc_apply(const Level& L, int ld, const double* T, float* Y, int* err, cudaStream_t s,
+                         bool fused = false);
 // reads and clears the device error word of the tensor-core kernels (synchronous)
 stm_status check_kernel_error(Hierarchy& H, cudaStream_t s);
 stm_status vcycle_multi(Hierarchy& H, const double* R_fine, double* D_fine, cudaStream_t s);

@@ -185,6 +185,11 @@ __host__ __device__ inline SmemLayout smem_layout(const TcGeom& g) {
 // Barrier indices
 enum { FULL_A = 0, EMPTY_A = 2, FULL_B = 4, EMPTY_B = 6, TM_FULL = 8, TM_EMPTY = 10 };
 
+// FUSED = false: 32 forward columns, Y = Inv T. FUSED = true: columns 0-15 forward (Y = Inv T), columns
+// 16-31 adjoint (Y = Inv^T T) from the same inverse tile: B holds [forward hi | forward lo | adjoint hi |
+// adjoint lo] (16 columns each); per output tile one MMA chain reads the tile as Inv (MN-major A) against
+// B columns 0-31 and one reads it as Inv^T (K-major A) against B columns 32-63.
+template <bool FUSED>
 __global__ void __launch_bounds__(kThreads, 1) k_vanka_mrhs_tc5(const __grid_constant__ CUtensorMap inv_map,
                                                                  const int* __restrict__ idx,
                                                                  const double* __restrict__ T,
@@ -250,6 +255,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_vanka_mrhs_tc5(const __grid_con
     // ---- MMA issuer ---------------------------------------------------------------------------
     if (lane == 0) {
       const uint32_t id = idesc_bf16(128, 64, true);
+      const uint32_t id_f = idesc_bf16(128, 32, true), id_a = idesc_bf16(128, 32, false);
       int it = 0, last = -1;
       for (int c = blockIdx.x; c < ncells; c += gridDim.x, ++it) {
         const int s = it & 1;
@@ -262,10 +268,27 @@ __global__ void __launch_bounds__(kThreads, 1) k_vanka_mrhs_tc5(const __grid_con
         for (int t = 0; t < g.MT; ++t) {
           const uint32_t at = a0 + (uint32_t)(t == 0 ? 0 : g.t1_chunk) * (uint32_t)g.CB;
           const uint32_t d = tmem + (uint32_t)(s * 128 + t * 64);
-          for (int ks = 0; ks < g.KS; ++ks) {
-            const uint64_t ad = sdesc(at + (uint32_t)ks * 256u, 128u, (uint32_t)g.CB);
-            const uint64_t bd = sdesc(b0 + (uint32_t)ks * 2048u, 1024u, 128u);
-            mma_bf16(d, ad, bd, id, ks > 0 ? 1u : 0u);
+          if (!FUSED) {
+            for (int ks = 0; ks < g.KS; ++ks) {
+              const uint64_t ad = sdesc(at + (uint32_t)ks * 256u, 128u, (uint32_t)g.CB);
+              const uint64_t bd = sdesc(b0 + (uint32_t)ks * 2048u, 1024u, 128u);
+              mma_bf16(d, ad, bd, id, ks > 0 ? 1u : 0u);
+            }
+          } else {
+            // forward: Inv (M = i) against B columns 0-31 into accumulator columns 0-31
+            for (int ks = 0; ks < g.KS; ++ks) {
+              const uint64_t ad = sdesc(at + (uint32_t)ks * 256u, 128u, (uint32_t)g.CB);
+              const uint64_t bd = sdesc(b0 + (uint32_t)ks * 2048u, 1024u, 128u);
+              mma_bf16(d, ad, bd, id_f, ks > 0 ? 1u : 0u);
+            }
+            // adjoint: Inv^T (M = j, rows t1_chunk*8.. of tile 1, K = i) against B columns 32-63 into
+            // accumulator columns 32-63
+            const uint32_t aj = a0 + (uint32_t)(t == 0 ? 0 : g.t1_chunk * 8) * 16u;
+            for (int ks = 0; ks < g.KS; ++ks) {
+              const uint64_t ad = sdesc(aj + (uint32_t)ks * 2u * (uint32_t)g.CB, (uint32_t)g.CB, 128u);
+              const uint64_t bd = sdesc(b0 + (uint32_t)ks * 2048u + 512u, 1024u, 128u);
+              mma_bf16(d + 32u, ad, bd, id_a, ks > 0 ? 1u : 0u);
+            }
           }
         }
         mma_commit(bar(EMPTY_A + s));
@@ -311,9 +334,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_vanka_mrhs_tc5(const __grid_con
                                    hi[6] | (hi[7] << 16));
         const uint4 Lo = make_uint4(lo[0] | (lo[1] << 16), lo[2] | (lo[3] << 16), lo[4] | (lo[5] << 16),
                                     lo[6] | (lo[7] << 16));
-        // core matrix (n-group, k-chunk q) at q*1024 + group*128, row (n % 8) at 16 * (n % 8)
-        *reinterpret_cast<uint4*>(bs + q * 1024 + (lane >> 3) * 128 + (lane & 7) * 16) = H;
-        *reinterpret_cast<uint4*>(bs + q * 1024 + (4 + (lane >> 3)) * 128 + (lane & 7) * 16) = Lo;
+        // B column of this lane's hi and lo parts; core matrix (n-group, k-chunk q) at q*1024 + group*128,
+        // row (n % 8) at 16 * (n % 8)
+        const int nh = FUSED ? (lane < 16 ? lane : 16 + lane) : lane;
+        const int nl = FUSED ? (lane < 16 ? 16 + lane : 32 + lane) : 32 + lane;
+        *reinterpret_cast<uint4*>(bs + q * 1024 + (nh >> 3) * 128 + (nh & 7) * 16) = H;
+        *reinterpret_cast<uint4*>(bs + q * 1024 + (nl >> 3) * 128 + (nl & 7) * 16) = Lo;
       }
       fence_async_smem();
       __syncwarp();
@@ -339,6 +365,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_vanka_mrhs_tc5(const __grid_con
         tmem_ld32(ta, hi);
         tmem_ld32(ta + 32u, lo);
         tmem_wait_ld();
+        if (FUSED) {
+          // accumulator columns: 0-15 forward hi, 16-31 forward lo, 32-47 adjoint hi, 48-63 adjoint lo;
+          // regroup as hi = [forward hi | adjoint hi], lo = [forward lo | adjoint lo]
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            const float fl = hi[16 + k];
+            hi[16 + k] = lo[k];
+            lo[k] = fl;
+          }
+        }
         // own row into the staging tile, 16-byte chunks XOR-swizzled by row
 #pragma unroll
         for (int ch = 0; ch < 8; ++ch) {
@@ -419,9 +455,12 @@ TcGeom tc_geom(int n, int ld) {
 // The tensor-core path applies when the stored BF16 columns are whole 16-byte units (TMA strides) and
 // the cell fits two 128-row output tiles.
 bool mrhs_tc_supported(int n, int ld) { return ld % 8 == 0 && ld <= 256 && n <= ld && n <= 256 && n >= 1; }
+// The fused form reads output tile 1 of the adjoint product from row ld - 128 of the contraction rows,
+// which must then coincide with tile 1 of the forward product: ld = 16 ceil(n / 16), or one tile.
+bool mrhs_tc_fused_supported(int n, int ld) { return mrhs_tc_supported(n, ld) && (ld <= 128 || ld == 16 * ((n + 15) / 16)); }
 
-stm_status mrhs_tc_apply(const Level& L, int ld, const double* T, float* Y, int* err, cudaStream_t s) {
-  if (!mrhs_tc_supported(L.n, ld)) {
+stm_status mrhs_tc_apply(const Level& L, int ld, const double* T, float* Y, int* err, cudaStream_t s, bool fused) {
+  if (!mrhs_tc_supported(L.n, ld) || (fused && !mrhs_tc_fused_supported(L.n, ld))) {
     set_error("multi-RHS tensor-core product: unsupported local size");
     return STM_ERR_INVALID_ARG;
   }
@@ -444,9 +483,14 @@ stm_status mrhs_tc_apply(const Level& L, int ld, const double* T, float* Y, int*
   const TcGeom g = tc_geom(L.n, ld);
   const SmemLayout sl = smem_layout(g);
   const int smem = (int)sl.total + 1024;
-  STM_CUDA(cudaFuncSetAttribute(k_vanka_mrhs_tc5, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   const int blocks = std::min(L.C, sm_count());
-  k_vanka_mrhs_tc5<<<blocks, kThreads, smem, s>>>(map, L.idx, T, Y, L.C, g, err);
+  if (fused) {
+    STM_CUDA(cudaFuncSetAttribute(k_vanka_mrhs_tc5<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    k_vanka_mrhs_tc5<true><<<blocks, kThreads, smem, s>>>(map, L.idx, T, Y, L.C, g, err);
+  } else {
+    STM_CUDA(cudaFuncSetAttribute(k_vanka_mrhs_tc5<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    k_vanka_mrhs_tc5<false><<<blocks, kThreads, smem, s>>>(map, L.idx, T, Y, L.C, g, err);
+  }
   note_launch();
   STM_CUDA(cudaGetLastError());
   return STM_OK;

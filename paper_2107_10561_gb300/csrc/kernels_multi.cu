@@ -37,6 +37,40 @@ __global__ void k_from_interleaved(const double* __restrict__ src, double* __res
     dst[e] = src[i * NR + c];
   }
 }
+// columns [col0, col0 + ncols) of the interleaved block from a column-major source (others untouched)
+__global__ void k_to_interleaved_at(const double* __restrict__ src, double* __restrict__ dst, long long N, int ncols,
+                                    int col0) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N * ncols; e += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(e / N);
+    const long long i = e - (long long)c * N;
+    dst[i * NR + col0 + c] = src[e];
+  }
+}
+__global__ void k_from_interleaved_at(const double* __restrict__ src, double* __restrict__ dst, long long N, int ncols,
+                                      int col0) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N * ncols; e += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(e / N);
+    const long long i = e - (long long)c * N;
+    dst[e] = src[i * NR + col0 + c];
+  }
+}
+stm_status multi_columns_in(const double* src, double* dst, long long N, int ncols, int col0, cudaStream_t s) {
+  if (ncols <= 0) return STM_OK;
+  k_to_interleaved_at<<<(int)std::min<long long>((N * ncols + 255) / 256, msms() * 16LL), 256, 0, s>>>(src, dst, N, ncols,
+                                                                                                      col0);
+  note_launch();
+  STM_CUDA(cudaGetLastError());
+  return STM_OK;
+}
+stm_status multi_columns_out(const double* src, double* dst, long long N, int ncols, int col0, cudaStream_t s) {
+  if (ncols <= 0) return STM_OK;
+  k_from_interleaved_at<<<(int)std::min<long long>((N * ncols + 255) / 256, msms() * 16LL), 256, 0, s>>>(src, dst, N,
+                                                                                                        ncols, col0);
+  note_launch();
+  STM_CUDA(cudaGetLastError());
+  return STM_OK;
+}
+
 stm_status multi_to_interleaved(const double* src, double* dst, long long N, int nrhs, cudaStream_t s) {
   k_to_interleaved<<<(int)std::min<long long>((N * NR + 255) / 256, msms() * 16LL), 256, 0, s>>>(src, dst, N, nrhs);
   note_launch();
@@ -58,11 +92,13 @@ __global__ void __launch_bounds__(256) k_spmm_struct(
     const long long* __restrict__ rowptr, const double* __restrict__ val, const int* __restrict__ nbr_ptr,
     const int* __restrict__ nbr, const int* __restrict__ ncell, const int* __restrict__ node_cells,
     const int* __restrict__ cell_nodes, long long block, int R, int C, int nv, const double* __restrict__ X,
-    const double* __restrict__ B, double* __restrict__ Y, int mode) {
+    const double* __restrict__ B, double* __restrict__ Y, int mode, const double* __restrict__ valT, int split) {
   constexpr int KD = K * D;
   constexpr int NP = D + 1;
   constexpr int MAXC = 1 << D;
   const int lane = threadIdx.x & 31;
+  // lanes (columns) from split on multiply by J^T: its values on the same (symmetric) pattern
+  if (lane >= split) val = valT;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long job = warp; job < (long long)R + C; job += nwarps) {
@@ -142,13 +178,18 @@ __global__ void __launch_bounds__(256) k_spmm_struct(
   }
 }
 
-stm_status spmm_structured(const Level& L, const double* X, const double* B, double* Y, int mode, cudaStream_t s) {
+stm_status spmm_structured(const Level& L, const double* X, const double* B, double* Y, int mode, cudaStream_t s,
+                           int split) {
+  if (split < NR && !L.valT) {
+    set_error("multi-RHS SpMM: the values of J^T are not built");
+    return STM_ERR_STATE;
+  }
   const long long jobs = (long long)L.R + L.C;
   const int blocks = (int)std::min<long long>((jobs * 32 + 255) / 256, (long long)msms() * 8);
   const int key = L.dim * 10 + L.K;
 #define SPMM(K, D) \
   k_spmm_struct<K, D><<<blocks, 256, 0, s>>>(L.rowptr, L.val, L.nbr_ptr, L.nbr, L.ncell, L.node_cells, L.cell_nodes, \
-                                             L.block, L.R, L.C, L.nv, X, B, Y, mode)
+                                             L.block, L.R, L.C, L.nv, X, B, Y, mode, L.valT, split)
   switch (key) {
     case 21: SPMM(1, 2); break;
     case 22: SPMM(2, 2); break;
@@ -199,10 +240,11 @@ __device__ __forceinline__ float inv_to_acc(__nv_bfloat16 v) { return __bfloat16
 __device__ __forceinline__ float inv_to_acc(float v) { return v; }
 __device__ __forceinline__ double inv_to_acc(double v) { return v; }
 
+// Lanes from split on apply the transposed inverse (adjoint columns).
 template <typename S, typename A>
 __global__ void __launch_bounds__(256) k_vanka_mrhs_cc(const S* __restrict__ inv, const int* __restrict__ idx,
                                                        const double* __restrict__ T, A* __restrict__ Yout,
-                                                       int ncells, int n, int ld) {
+                                                       int ncells, int n, int ld, int split) {
   extern __shared__ __align__(16) unsigned char smc[];
   A* Ts = reinterpret_cast<A*>(smc);  // [n][32]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -215,9 +257,13 @@ __global__ void __launch_bounds__(256) k_vanka_mrhs_cc(const S* __restrict__ inv
     }
     __syncthreads();
     const S* M = inv + (size_t)c * n * ld;
+    const bool adj = lane >= split;
     for (int i = warp; i < n; i += nwarps) {
+      // forward: (J_T^{-1})_{ij} = M[j*ld + i]; adjoint: (J_T^{-T})_{ij} = M[i*ld + j]
+      const S* mr = adj ? M + (size_t)i * ld : M + i;
+      const size_t st = adj ? 1 : (size_t)ld;
       A s = 0;
-      for (int j = 0; j < n; ++j) s += (A)inv_to_acc(M[(size_t)j * ld + i]) * Ts[j * NR + lane];
+      for (int j = 0; j < n; ++j) s += (A)inv_to_acc(mr[(size_t)j * st]) * Ts[j * NR + lane];
       Yout[((long long)c * n + i) * NR + lane] = s;
     }
   }
@@ -250,17 +296,24 @@ stm_status ensure_multi(Hierarchy& H) {
   return STM_OK;
 }
 
-stm_status vanka_step_multi(Hierarchy& H, int g, const double* R, double* Dm, bool d_is_zero, cudaStream_t s) {
+stm_status vanka_step_multi(Hierarchy& H, int g, const double* R, double* Dm, bool d_is_zero, cudaStream_t s,
+                            int split) {
   Level& L = H.L[g];
   const double* T = R;
+  if (split < NR) STM_TRY(ensure_transpose(H, g, s));
   if (!d_is_zero) {
     ProfScope ps(&H, STM_KCLASS_JACOBIAN_SPMV, s, 8.0 * (double)L.nnz + 24.0 * NR * (double)L.N, g);
-    STM_TRY(spmm_structured(L, Dm, R, L.mt, 1, s));
+    STM_TRY(spmm_structured(L, Dm, R, L.mt, 1, s, split));
     T = L.mt;
   }
   const int prec = H.p.inv_precision;
   const InvLayout lay = inv_layout(L.n, prec);
-  const bool tc = prec == STM_BF16 && mrhs_tc_supported(L.n, lay.ld);
+  const bool fused = split == 16;
+  if (split != NR && !fused) {
+    set_error("multi-RHS smoothing: adjoint columns start at column 16");
+    return STM_ERR_INVALID_ARG;
+  }
+  const bool tc = prec == STM_BF16 && (fused ? mrhs_tc_fused_supported(L.n, lay.ld) : mrhs_tc_supported(L.n, lay.ld));
   const bool y64 = prec == STM_F64;
   {
     // algorithmic bytes: the stored inverses, the index map, the 32 gathered FP64 columns of every
@@ -270,7 +323,7 @@ stm_status vanka_step_multi(Hierarchy& H, int g, const double* R, double* Dm, bo
                                 (8.0 + (y64 ? 8.0 : 4.0)) * NR * L.n),
                  g);
     if (tc) {
-      STM_TRY(mrhs_tc_apply(L, lay.ld, T, reinterpret_cast<float*>(L.mY), H.dkerr, s));
+      STM_TRY(mrhs_tc_apply(L, lay.ld, T, reinterpret_cast<float*>(L.mY), H.dkerr, s, fused));
     } else {
       const int blocks = std::min(L.C, msms() * 8);
 #define MRHS_CC(S_, A_)                                                                                          \
@@ -278,7 +331,7 @@ stm_status vanka_step_multi(Hierarchy& H, int g, const double* R, double* Dm, bo
     const size_t smem = sizeof(A_) * (size_t)L.n * NR;                                                          \
     STM_CUDA(cudaFuncSetAttribute(k_vanka_mrhs_cc<S_, A_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
     k_vanka_mrhs_cc<S_, A_><<<blocks, 256, smem, s>>>((const S_*)L.inv, L.idx, T, reinterpret_cast<A_*>(L.mY), L.C, \
-                                                      L.n, lay.ld);                                             \
+                                                      L.n, lay.ld, split);                                      \
   } while (0)
       if (prec == STM_F64) MRHS_CC(double, double);
       else if (prec == STM_F32) MRHS_CC(float, float);

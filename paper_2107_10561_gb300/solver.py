@@ -268,6 +268,21 @@ class Hierarchy:
         _lib.check(self.lib.stm_vanka_sweep_multi(self.h, level, nrhs, _ptr(R, nrhs * n, "R"), _ptr(D, nrhs * n, "D"),
                                                   _stream(stream)), "stm_vanka_sweep_multi")
 
+    def vanka_sweep_fused(self, level, Rf, Df, Ra, Da, stream=None):
+        """One additive smoothing step for forward columns (Rf, Df: CUDA float64 [n_fwd <= 16, n_dofs]) and
+        adjoint columns (Ra, Da: [n_adj <= 16, n_dofs]) from one pass over the cell inverses."""
+        n = self.n_dofs(level)
+        nf = 0 if Rf is None else Rf.shape[0]
+        na = 0 if Ra is None else Ra.shape[0]
+        for A, B, k in ((Rf, Df, nf), (Ra, Da, na)):
+            if k and (tuple(A.shape) != (k, n) or tuple(B.shape) != (k, n)):
+                raise ValueError("R and D must be [ncols, n_dofs(level)]")
+        _lib.check(self.lib.stm_vanka_sweep_fused(self.h, level, nf, _ptr(Rf, nf * n, "Rf") if nf else None,
+                                                  _ptr(Df, nf * n, "Df") if nf else None, na,
+                                                  _ptr(Ra, na * n, "Ra") if na else None,
+                                                  _ptr(Da, na * n, "Da") if na else None, _stream(stream)),
+                   "stm_vanka_sweep_fused")
+
     def gmres_solve_multi(self, B, X, rtol=1e-8, restart=30, max_iter=1000, use_x0=False, stream=None,
                           raise_on_fail=True):
         """Lock-stepped FGMRES for every column of B: CUDA float64 [nrhs <= 32, n_dofs]; returns per-column infos."""

@@ -106,3 +106,33 @@ def test_multi_gmres_matches_single_solves(prec):
         xd = spla.spsolve(o.J[-1].tocsc(), B[c].cpu().numpy())
         assert rel_max(X[c].cpu().numpy(), xd) < 1e-6
     h.close()
+
+
+@pytest.mark.parametrize("name", ["3d_k1", "2d_k2", "2d_k1"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("nf,na", [(16, 16), (5, 11), (16, 0), (0, 3)])
+def test_fused_forward_adjoint_sweep_against_oracle(name, prec, nf, na):
+    """stm_vanka_sweep_fused: forward columns against oracle.solvers.vanka_step on J, adjoint columns
+    against the transposed oracle step (J^T, J_T^{-T}), one pass over the inverses on the GPU."""
+    from helpers import oracle_hierarchy, round_storage
+    from oracle import solvers
+    wl = CASES[name]
+    o = oracle_hierarchy(wl)
+    h = gpu_hierarchy(wl, prec)
+    g = h.finest
+    lev = o.fine
+    inv = round_storage(o.inv[-1], prec)
+    rng = np.random.default_rng(66)
+    Rf, Df = rng.standard_normal((nf, lev.N)), rng.standard_normal((nf, lev.N))
+    Ra, Da = rng.standard_normal((na, lev.N)), rng.standard_normal((na, lev.N))
+    dRf, dDf = torch.from_numpy(Rf).cuda(), torch.from_numpy(Df).cuda()
+    dRa, dDa = torch.from_numpy(Ra).cuda(), torch.from_numpy(Da).cuda()
+    h.vanka_sweep_fused(g, dRf if nf else None, dDf if nf else None, dRa if na else None, dDa if na else None)
+    gf, ga = dDf.cpu().numpy(), dDa.cpu().numpy()
+    for c in range(nf):
+        expect = solvers.vanka_step(lev, o.J[-1], inv, Df[c], Rf[c], wl.omega)
+        assert rel_max(gf[c], expect) < TOL[prec], ("forward", c)
+    for c in range(na):
+        expect = solvers.vanka_step(lev, o.J[-1], inv, Da[c], Ra[c], wl.omega, transpose=True)
+        assert rel_max(ga[c], expect) < TOL[prec], ("adjoint", c)
+    h.close()
