@@ -62,6 +62,51 @@ __device__ __forceinline__ uint32_t bf16_bits_rn(double x) {
 }
 __device__ __forceinline__ double bf16_bits_to_double(uint32_t h) { return (double)__uint_as_float(h << 16); }
 
+// x = hi + lo + (rounding of lo) with hi = the BF16 value nearest to x and lo = the BF16 value nearest to
+// x - hi (which FP64 holds exactly), both taken from the FP64 bit fields with integer operations only:
+// no FP64 pipe instructions in the common case. Out-of-range exponents (x or lo outside the BF16
+// normal range, zero, non-finite) take the bf16_bits_rn route above.
+__device__ __forceinline__ void bf16_split_rn(double x, uint32_t& hi, uint32_t& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const uint32_t sign = (uint32_t)(b >> 48) & 0x8000u;
+  const int e = (int)((b >> 52) & 0x7FF) - 1023;
+  if (e < -74 || e > 127) {
+    hi = bf16_bits_rn(x);
+    lo = bf16_bits_rn(x - bf16_bits_to_double(hi));
+    return;
+  }
+  const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
+  uint32_t h = sign | ((uint32_t)(e + 127) << 7) | (uint32_t)(mant >> 45);
+  long long rem = (long long)(mant & ((1ull << 45) - 1));  // x - (truncated hi) in units of 2^(e - 52)
+  const long long half = 1ll << 44;
+  if (rem > half || (rem == half && (h & 1u))) {
+    ++h;                    // rounded up (a carry moves into the exponent as it should)
+    rem -= (1ll << 45);     // the remainder is now negative
+  }
+  hi = h;
+  if (rem == 0) {
+    lo = 0u;
+    return;
+  }
+  const uint32_t ls = rem < 0 ? (sign ^ 0x8000u) : sign;
+  const unsigned long long a = (unsigned long long)(rem < 0 ? -rem : rem);  // < 2^45
+  const int p = 63 - __clzll((long long)a);                                  // leading bit, 0..44
+  const int le = p + e - 52;                                                 // exponent of |x - hi|
+  if (le < -126) {
+    lo = bf16_bits_rn(x - bf16_bits_to_double(hi));
+    return;
+  }
+  if (p <= 7) {
+    lo = ls | ((uint32_t)(le + 127) << 7) | ((uint32_t)(a << (7 - p)) & 0x7Fu);
+    return;
+  }
+  const int sh = p - 7;
+  uint32_t l = ls | ((uint32_t)(le + 127) << 7) | ((uint32_t)(a >> sh) & 0x7Fu);
+  const unsigned long long rest = a & ((1ull << sh) - 1), hl = 1ull << (sh - 1);
+  if (rest > hl || (rest == hl && (l & 1u))) ++l;
+  lo = l;
+}
+
 // Launch accounting and optional per-class CUDA-event timing --------------------------------
 extern std::atomic<long long> g_launches;
 inline void note_launch(long long n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }

@@ -4,7 +4,7 @@
 //
 // One persistent CTA per SM walks its cells in a warp-specialised pipeline:
 //   warp 0      streams the cell's stored BF16 inverse into shared memory with TMA
-//               (cp.async.bulk.tensor, one 8-row box per 8 stored rows, two-stage ring);
+//               (cp.async.bulk.tensor, one 64-row box per 64 stored rows, two-stage ring);
 //   warp 1      allocates the tensor memory and issues tcgen05.mma (one elected thread):
 //               D[128 rows][64 cols] += Inv[rows][16 k] x B[16 k][64 cols] over the contraction, FP32
 //               accumulators in TMEM (two accumulator sets, so the epilogue of one cell overlaps the
@@ -16,17 +16,19 @@
 //   warps 10-13 read the accumulators back with tcgen05.ld (one TMEM lane per output row), add the
 //               hi and lo halves and store Y in FP32, coalesced through a swizzled staging tile.
 //
-// Operand layouts (no swizzle, 8x16-byte core matrices). The inverse is stored column-major
-// (element (i, j) at j*ld + i). TMA box a copies rows 8a..8a+7 of every column j into the chunk
-// at a*CB, column j at 16*j; so chunk a, rows 16j..16j+15 form core matrices of 8 j-rows x 8 i-values:
-//   forward product  Inv   (M = i, K = j): MN-major A, MN-chunk stride (SBO) = CB, K-group stride
-//                    (LBO) = 128 B;
-//   adjoint product  Inv^T (M = j, K = i): the same bytes as a K-major A, M-group stride (SBO) = 128 B,
-//                    K-chunk stride (LBO) = CB.
-// B (gathered columns, written by warps 2-9): K-major, core (n-group g, k-chunk q) at q*1024 + g*128.
-// Rows past n in every chunk and chunks past ld/8 stay zero (written once), so the padded contraction
-// adds nothing. Output rows: tile 0 = rows 0..127; for ld > 128, tile 1 = the last 128 stored rows
-// (it overlaps tile 0, whose rows it skips in the epilogue).
+// Operand layouts. The inverse is stored column-major (element (i, j) at j*ld + i). TMA box b copies rows
+// 64b..64b+63 (128 bytes) of every column j into shared memory with the 128-byte swizzle: box b holds
+// RJ rows (one per column j, rows past n zero) of 64 i-values, in 8-row atoms of 1024 bytes. The same
+// bytes serve both products:
+//   forward  Inv   (M = i, K = j): MN-major A, 128B swizzle; MN atoms of 64 i one box apart (LBO),
+//            8-row K groups 1024 B apart (SBO); a 16-wide K step moves two atoms;
+//   adjoint  Inv^T (M = j, K = i): K-major A, 128B swizzle; 8-row M groups 1024 B apart (SBO); a
+//            16-wide K step moves 32 bytes inside the 128-byte row, four steps per box.
+// Output tiles of 128 rows start at rows 0 and 64 (the second only for ld > 128; its rows below 128
+// repeat tile 0 and are skipped in the epilogue), for i in the forward and j in the adjoint product.
+// B (gathered columns, written by warps 2-9): K-major without swizzle, core matrices of 8 columns x 16
+// bytes, core (n-group g, k-chunk q) at q*1024 + g*128. Rows past n of B and of every box stay zero
+// (written once), so the padded contraction adds nothing.
 //
 // Every wait on an mbarrier gives up after a bounded number of polls, sets the level's error word and
 // lets the CTA finish (after waiting, again bounded, for its own copies and products in flight), so a
@@ -49,15 +51,15 @@ constexpr int kTmemCols = 256;      // 2 accumulator sets x 2 output tiles x 64 
 constexpr uint64_t kWaitNs = 1000000000ull;  // one second per wait at most
 
 struct TcGeom {
-  int n, ld;          // local size, stored rows per column (multiple of 8)
+  int n, ld;          // local size, stored rows per column (multiple of 8, at most 192)
   int KS;             // 16-wide contraction steps: ceil(n / 16)
-  int CB;             // bytes of one 8-row chunk in shared memory: KS * 16 rows * 16 B
-  int CHS;            // chunks of the shared A tile: max(ld / 8, 16)
   int MT;             // output tiles of 128 rows: 1 (ld <= 128) or 2
-  int t1_chunk;       // first chunk of output tile 1: ld / 8 - 16
-  unsigned a_bytes;   // CHS * CB
+  int RJ;             // rows (columns j of the inverse) of one box in shared memory: 128 or 192
+  int BOXB;           // bytes of one box: RJ * 128
+  int NB;             // boxes TMA fills per cell: ceil(ld / 64)
+  unsigned a_bytes;   // boxes allocated per stage (2 or 3, zero beyond NB) x BOXB
   unsigned b_bytes;   // KS * 2048 (16 k x 64 columns x 2 B per step)
-  unsigned tx_bytes;  // bytes TMA delivers per cell: (ld / 8) * n * 16
+  unsigned tx_bytes;  // bytes TMA delivers per cell: NB * 64 * n * 2 (out-of-range rows count, as zeros)
 };
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -117,6 +119,10 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
 __device__ __forceinline__ uint64_t sdesc(uint32_t start, uint32_t lbo, uint32_t sbo) {
   return (uint64_t)((start >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
          ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// The same with the 128-byte swizzle (layout type 2 in bits 61-63); atoms must start on 1024-byte boundaries.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t start, uint32_t lbo, uint32_t sbo) {
+  return sdesc(start, lbo, sbo) | (2ull << 61);
 }
 // Instruction descriptor of tcgen05.mma kind::f16: D in FP32, A and B in BF16, A MN-major (a_mn) or
 // K-major, B K-major, N columns, M rows.
@@ -243,8 +249,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_vanka_mrhs_tc5(const __grid_con
         ok = mbar_wait(bar(EMPTY_A + s), u ^ 1u, err, 1);
         if (!ok) break;
         mbar_expect_tx(bar(FULL_A + s), g.tx_bytes);
-        for (int a = 0; a < g.ld / 8; ++a)
-          tma_load_3d(sbase + L.a[s] + (uint32_t)a * (uint32_t)g.CB, &inv_map, 8 * a, 0, c, bar(FULL_A + s));
+        for (int b = 0; b < g.NB; ++b)
+          tma_load_3d(sbase + L.a[s] + (uint32_t)b * (uint32_t)g.BOXB, &inv_map, 64 * b, 0, c, bar(FULL_A + s));
         last_c[s] = it;
       }
       // the copies of the last two cells must have landed before the CTA may finish
@@ -266,26 +272,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_vanka_mrhs_tc5(const __grid_con
         tc_fence_after();
         const uint32_t a0 = sbase + L.a[s], b0 = sbase + L.b[s];
         for (int t = 0; t < g.MT; ++t) {
-          const uint32_t at = a0 + (uint32_t)(t == 0 ? 0 : g.t1_chunk) * (uint32_t)g.CB;
           const uint32_t d = tmem + (uint32_t)(s * 128 + t * 64);
-          if (!FUSED) {
+          // forward: Inv rows i = 64t .. 64t + 127 = boxes t, t + 1; K = j in whole 8-row atoms
+          const uint32_t af = a0 + (uint32_t)t * (uint32_t)g.BOXB;
+          for (int ks = 0; ks < g.KS; ++ks) {
+            const uint64_t ad = sdesc_sw128(af + (uint32_t)ks * 2048u, (uint32_t)g.BOXB, 1024u);
+            const uint64_t bd = sdesc(b0 + (uint32_t)ks * 2048u, 1024u, 128u);
+            if (!FUSED) mma_bf16(d, ad, bd, id, ks > 0 ? 1u : 0u);
+            else mma_bf16(d, ad, bd, id_f, ks > 0 ? 1u : 0u);
+          }
+          if (FUSED) {
+            // adjoint: Inv^T rows j = 64t .. 64t + 127 of every box, K = i: 32 bytes per step inside a box
             for (int ks = 0; ks < g.KS; ++ks) {
-              const uint64_t ad = sdesc(at + (uint32_t)ks * 256u, 128u, (uint32_t)g.CB);
-              const uint64_t bd = sdesc(b0 + (uint32_t)ks * 2048u, 1024u, 128u);
-              mma_bf16(d, ad, bd, id, ks > 0 ? 1u : 0u);
-            }
-          } else {
-            // forward: Inv (M = i) against B columns 0-31 into accumulator columns 0-31
-            for (int ks = 0; ks < g.KS; ++ks) {
-              const uint64_t ad = sdesc(at + (uint32_t)ks * 256u, 128u, (uint32_t)g.CB);
-              const uint64_t bd = sdesc(b0 + (uint32_t)ks * 2048u, 1024u, 128u);
-              mma_bf16(d, ad, bd, id_f, ks > 0 ? 1u : 0u);
-            }
-            // adjoint: Inv^T (M = j, rows t1_chunk*8.. of tile 1, K = i) against B columns 32-63 into
-            // accumulator columns 32-63
-            const uint32_t aj = a0 + (uint32_t)(t == 0 ? 0 : g.t1_chunk * 8) * 16u;
-            for (int ks = 0; ks < g.KS; ++ks) {
-              const uint64_t ad = sdesc(aj + (uint32_t)ks * 2u * (uint32_t)g.CB, (uint32_t)g.CB, 128u);
+              const uint32_t aj = a0 + (uint32_t)(ks >> 2) * (uint32_t)g.BOXB + (uint32_t)t * 64u * 128u +
+                                  (uint32_t)(ks & 3) * 32u;
+              const uint64_t ad = sdesc_sw128(aj, 16u, 1024u);
               const uint64_t bd = sdesc(b0 + (uint32_t)ks * 2048u + 512u, 1024u, 128u);
               mma_bf16(d + 32u, ad, bd, id_a, ks > 0 ? 1u : 0u);
             }
@@ -326,10 +327,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_vanka_mrhs_tc5(const __grid_con
         if (q >= nchunks) continue;
         uint32_t hi[8], lo[8];
 #pragma unroll
-        for (int kk = 0; kk < 8; ++kk) {
-          hi[kk] = bf16_bits_rn(v[r][kk]);
-          lo[kk] = bf16_bits_rn(v[r][kk] - bf16_bits_to_double(hi[kk]));
-        }
+        for (int kk = 0; kk < 8; ++kk) bf16_split_rn(v[r][kk], hi[kk], lo[kk]);
         const uint4 H = make_uint4(hi[0] | (hi[1] << 16), hi[2] | (hi[3] << 16), hi[4] | (hi[5] << 16),
                                    hi[6] | (hi[7] << 16));
         const uint4 Lo = make_uint4(lo[0] | (lo[1] << 16), lo[2] | (lo[3] << 16), lo[4] | (lo[5] << 16),
@@ -357,7 +355,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_vanka_mrhs_tc5(const __grid_con
       if (!__all_sync(0xffffffffu, mbar_wait(bar(TM_FULL + s), u, err, 8))) break;
       tc_fence_after();
       for (int t = 0; t < g.MT; ++t) {
-        const int row0 = (t == 0 ? 0 : g.t1_chunk * 8) + 32 * q;  // first output row of this warp
+        const int row0 = 64 * t + 32 * q;  // first output row of this warp
         if (t == 1 && row0 + 31 < 128) continue;                  // rows already written by tile 0
         if (row0 >= g.n) continue;
         const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(s * 128 + t * 64);
@@ -440,13 +438,13 @@ TcGeom tc_geom(int n, int ld) {
   g.n = n;
   g.ld = ld;
   g.KS = (n + 15) / 16;
-  g.CB = g.KS * 16 * 16;
-  g.CHS = std::max(ld / 8, 16);
   g.MT = ld > 128 ? 2 : 1;
-  g.t1_chunk = ld / 8 - 16;
-  g.a_bytes = (unsigned)(g.CHS * g.CB);
+  g.RJ = g.MT == 2 ? 192 : 128;
+  g.BOXB = g.RJ * 128;
+  g.NB = (ld + 63) / 64;
+  g.a_bytes = (unsigned)((g.MT == 2 ? 3 : 2) * g.BOXB);
   g.b_bytes = (unsigned)(g.KS * 2048);
-  g.tx_bytes = (unsigned)((ld / 8) * n * 16);
+  g.tx_bytes = (unsigned)(g.NB * 64 * n * 2);
   return g;
 }
 
@@ -454,10 +452,8 @@ TcGeom tc_geom(int n, int ld) {
 
 // The tensor-core path applies when the stored BF16 columns are whole 16-byte units (TMA strides) and
 // the cell fits two 128-row output tiles.
-bool mrhs_tc_supported(int n, int ld) { return ld % 8 == 0 && ld <= 256 && n <= ld && n <= 256 && n >= 1; }
-// The fused form reads output tile 1 of the adjoint product from row ld - 128 of the contraction rows,
-// which must then coincide with tile 1 of the forward product: ld = 16 ceil(n / 16), or one tile.
-bool mrhs_tc_fused_supported(int n, int ld) { return mrhs_tc_supported(n, ld) && (ld <= 128 || ld == 16 * ((n + 15) / 16)); }
+bool mrhs_tc_supported(int n, int ld) { return ld % 8 == 0 && ld <= 192 && n <= ld && n >= 1; }
+bool mrhs_tc_fused_supported(int n, int ld) { return mrhs_tc_supported(n, ld); }
 
 stm_status mrhs_tc_apply(const Level& L, int ld, const double* T, float* Y, int* err, cudaStream_t s, bool fused) {
   if (!mrhs_tc_supported(L.n, ld) || (fused && !mrhs_tc_fused_supported(L.n, ld))) {
@@ -467,14 +463,14 @@ stm_status mrhs_tc_apply(const Level& L, int ld, const double* T, float* Y, int*
   if (L.C == 0) return STM_OK;
   EncodeTiledFn enc = nullptr;
   STM_TRY(encode_fn(&enc));
-  // the level's BF16 inverses as a 3-D tensor [C][n columns][ld rows], box = 8 rows x n columns
+  // the level's BF16 inverses as a 3-D tensor [C][n columns][ld rows], box = 64 rows x n columns
   alignas(64) CUtensorMap map;
   const cuuint64_t dims[3] = {(cuuint64_t)ld, (cuuint64_t)L.n, (cuuint64_t)L.C};
   const cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)ld * L.n * 2};
-  const cuuint32_t box[3] = {8, (cuuint32_t)L.n, 1};
+  const cuuint32_t box[3] = {64, (cuuint32_t)L.n, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, L.inv, dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     set_error("cuTensorMapEncodeTiled failed for the cell inverses (code " + std::to_string((int)r) + ")");
