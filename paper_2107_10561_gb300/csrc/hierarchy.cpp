@@ -759,7 +759,7 @@ void free_hierarchy(Hierarchy& H) {
                     L.colidx, L.val, L.valT, L.ref, L.inj, L.wnod, L.inv, L.wmult, L.own_ptr,
                     L.own_pos, L.last_owner, L.colour_cells, L.Y, L.P_rowptr, L.P_col, L.P_val,
                     L.Rt_rowptr, L.Rt_col, L.Rt_val, L.tv_ptr, L.tv_node, L.tv_w, L.tc_ptr, L.tc_node,
-                    L.tc_w, L.cparent, L.cbits, L.cchildren, L.d, L.r, L.t, L.md, L.mr, L.mt, L.mY};
+                    L.tc_w, L.cparent, L.cbits, L.cchildren, L.d, L.r, L.t, L.md, L.mr, L.mt, L.mY, L.mt16};
     for (void* q : ptrs)
       if (q) cudaFree(q);
   }

@@ -227,6 +227,7 @@ struct Level {
   double *d = nullptr, *r = nullptr, *t = nullptr;
   // multi-right-hand-side work space ([N][32] interleaved; mY: [C*n][32]), allocated on first use
   double *md = nullptr, *mr = nullptr, *mt = nullptr, *mY = nullptr;
+  uint32_t* mt16 = nullptr;       // [N][32] the smoothing step's residual block as packed BF16 (lo << 16 | hi)
 };
 
 struct Hierarchy {
@@ -361,8 +362,9 @@ stm_status multi_from_interleaved(const double* src, double* dst, long long N, i
 stm_status multi_columns_in(const double* src, double* dst, long long N, int ncols, int col0, cudaStream_t s);
 stm_status multi_columns_out(const double* src, double* dst, long long N, int ncols, int col0, cudaStream_t s);
 // columns split..31 use J^T (L.valT, which must exist when split < 32)
+// T16 (mode 1 only, may be null): the result also as packed BF16 hi + lo parts (lo << 16 | hi)
 stm_status spmm_structured(const Level& L, const double* X, const double* B, double* Y, int mode, cudaStream_t s,
-                           int split = 32);
+                           int split = 32, uint32_t* T16 = nullptr);
 stm_status ensure_multi(Hierarchy& H);
 // split < 32: columns split..31 are adjoint columns (defect with J^T, local products with J_T^{-T});
 // with split = 16 and BF16 inverses on the tensor cores both come from one pass over the inverses
@@ -373,7 +375,8 @@ stm_status vanka_step_multi(Hierarchy& H, int g, const double* R, double* Dm, bo
 // fused = true: columns 0-15 get Y = J^{-1} T, columns 16-31 Y = J^{-T} T from the same inverse tile
 bool mrhs_tc_supported(int n, int ld);
 bool mrhs_tc_fused_supported(int n, int ld);
-stm_status mrhs_tc_apply(const Level& L, int ld, const double* T, float* Y, int* err, cudaStream_t s,
+// T16: the residual block as packed BF16 hi + lo parts (lo << 16 | hi), [N][32]
+stm_status mrhs_tc_apply(const Level& L, int ld, const uint32_t* T16, float* Y, int* err, cudaStream_t s,
                          bool fused = false);
 // reads and clears the device error word of the tensor-core kernels (synchronous)
 stm_status check_kernel_error(Hierarchy& H, cudaStream_t s);

@@ -9,10 +9,11 @@
 //               D[128 rows][64 cols] += Inv[rows][16 k] x B[16 k][64 cols] over the contraction, FP32
 //               accumulators in TMEM (two accumulator sets, so the epilogue of one cell overlaps the
 //               products of the next);
-//   warps 2-9   gather the 32 FP64 residual columns of the cell's DoFs (one 256-byte line per DoF of
-//               the interleaved [N][32] multi-vector), split each value into BF16 hi + lo parts
-//               (t = hi + lo to about 2^-16 relative, so the only rounding of note is the stored
-//               inverse's) and write them as the B operand: columns 0-31 hi, 32-63 lo;
+//   warps 2-9   gather the 32 residual columns of the cell's DoFs (one 128-byte line per DoF of the
+//               interleaved [N][32] block, each value already split into BF16 hi + lo parts by the
+//               kernel that wrote it: t = hi + lo to about 2^-16 relative, so the only rounding of
+//               note is the stored inverse's) and write them as the B operand: columns 0-31 hi,
+//               32-63 lo; the loads of the next cell are in flight while the current one is written;
 //   warps 10-13 read the accumulators back with tcgen05.ld (one TMEM lane per output row), add the
 //               hi and lo halves and store Y in FP32, coalesced through a swizzled staging tile.
 //
@@ -198,7 +199,7 @@ enum { FULL_A = 0, EMPTY_A = 2, FULL_B = 4, EMPTY_B = 6, TM_FULL = 8, TM_EMPTY =
 template <bool FUSED>
 __global__ void __launch_bounds__(kThreads, 1) k_vanka_mrhs_tc5(const __grid_constant__ CUtensorMap inv_map,
                                                                  const int* __restrict__ idx,
-                                                                 const double* __restrict__ T,
+                                                                 const uint32_t* __restrict__ T16,
                                                                  float* __restrict__ Y, int ncells, TcGeom g,
                                                                  int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
@@ -301,37 +302,39 @@ __global__ void __launch_bounds__(kThreads, 1) k_vanka_mrhs_tc5(const __grid_con
       if (last >= 0) mbar_wait(bar(TM_FULL + (last & 1)), (uint32_t)(last >> 1) & 1u, err, 32);
     }
   } else if (warp < kEpiWarp0) {
-    // ---- gather: 32 FP64 columns per local DoF -> BF16 hi (columns 0-31) + lo (32-63) --------
+    // ---- gather: 32 packed columns per local DoF -> BF16 hi (B columns 0-31) + lo (32-63) ---------
     const int gw = warp - 2;
     const int nchunks = 2 * g.KS;  // 8-row k-chunks of the B tile
-    int it = 0;
-    for (int c = blockIdx.x; c < ncells; c += gridDim.x, ++it) {
-      const int s = it & 1;
-      const uint32_t u = (uint32_t)(it >> 1) & 1u;
+    uint32_t cur[3][8], nxt[3][8];
+    auto load_cell = [&](int c, uint32_t (*v)[8]) {
       const int* ic = idx + (long long)c * g.n;
-      double v[3][8];
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
         const int q = gw + r * kGatherWarps;
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk) {
           const int k = 8 * q + kk;
-          v[r][kk] = (q < nchunks && k < g.n) ? __ldg(T + (long long)__ldg(ic + k) * kNR + lane) : 0.0;
+          v[r][kk] = (q < nchunks && k < g.n) ? __ldg(T16 + (long long)__ldg(ic + k) * kNR + lane) : 0u;
         }
       }
+    };
+    if (blockIdx.x < ncells) load_cell(blockIdx.x, cur);
+    int it = 0;
+    for (int c = blockIdx.x; c < ncells; c += gridDim.x, ++it) {
+      const int s = it & 1;
+      const uint32_t u = (uint32_t)(it >> 1) & 1u;
+      if (c + (int)gridDim.x < ncells) load_cell(c + gridDim.x, nxt);  // next cell's loads in flight
       if (!__all_sync(0xffffffffu, mbar_wait(bar(EMPTY_B + s), u ^ 1u, err, 4))) break;
       unsigned char* bs = base + L.b[s];
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
         const int q = gw + r * kGatherWarps;
         if (q >= nchunks) continue;
-        uint32_t hi[8], lo[8];
-#pragma unroll
-        for (int kk = 0; kk < 8; ++kk) bf16_split_rn(v[r][kk], hi[kk], lo[kk]);
-        const uint4 H = make_uint4(hi[0] | (hi[1] << 16), hi[2] | (hi[3] << 16), hi[4] | (hi[5] << 16),
-                                   hi[6] | (hi[7] << 16));
-        const uint4 Lo = make_uint4(lo[0] | (lo[1] << 16), lo[2] | (lo[3] << 16), lo[4] | (lo[5] << 16),
-                                    lo[6] | (lo[7] << 16));
+        // 8 consecutive k of this lane's column: hi halves into one 16-byte row, lo halves into another
+        const uint4 H = make_uint4(__byte_perm(cur[r][0], cur[r][1], 0x5410), __byte_perm(cur[r][2], cur[r][3], 0x5410),
+                                   __byte_perm(cur[r][4], cur[r][5], 0x5410), __byte_perm(cur[r][6], cur[r][7], 0x5410));
+        const uint4 Lo = make_uint4(__byte_perm(cur[r][0], cur[r][1], 0x7632), __byte_perm(cur[r][2], cur[r][3], 0x7632),
+                                    __byte_perm(cur[r][4], cur[r][5], 0x7632), __byte_perm(cur[r][6], cur[r][7], 0x7632));
         // B column of this lane's hi and lo parts; core matrix (n-group, k-chunk q) at q*1024 + group*128,
         // row (n % 8) at 16 * (n % 8)
         const int nh = FUSED ? (lane < 16 ? lane : 16 + lane) : lane;
@@ -342,6 +345,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_vanka_mrhs_tc5(const __grid_con
       fence_async_smem();
       __syncwarp();
       if (lane == 0) mbar_arrive(bar(FULL_B + s));
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) cur[r][kk] = nxt[r][kk];
     }
   } else {
     // ---- epilogue: TMEM -> FP32 Y[c][row][32] ----------------------------------------------------
@@ -455,7 +462,7 @@ TcGeom tc_geom(int n, int ld) {
 bool mrhs_tc_supported(int n, int ld) { return ld % 8 == 0 && ld <= 192 && n <= ld && n >= 1; }
 bool mrhs_tc_fused_supported(int n, int ld) { return mrhs_tc_supported(n, ld); }
 
-stm_status mrhs_tc_apply(const Level& L, int ld, const double* T, float* Y, int* err, cudaStream_t s, bool fused) {
+stm_status mrhs_tc_apply(const Level& L, int ld, const uint32_t* T16, float* Y, int* err, cudaStream_t s, bool fused) {
   if (!mrhs_tc_supported(L.n, ld) || (fused && !mrhs_tc_fused_supported(L.n, ld))) {
     set_error("multi-RHS tensor-core product: unsupported local size");
     return STM_ERR_INVALID_ARG;
@@ -482,10 +489,10 @@ stm_status mrhs_tc_apply(const Level& L, int ld, const double* T, float* Y, int*
   const int blocks = std::min(L.C, sm_count());
   if (fused) {
     STM_CUDA(cudaFuncSetAttribute(k_vanka_mrhs_tc5<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    k_vanka_mrhs_tc5<true><<<blocks, kThreads, smem, s>>>(map, L.idx, T, Y, L.C, g, err);
+    k_vanka_mrhs_tc5<true><<<blocks, kThreads, smem, s>>>(map, L.idx, T16, Y, L.C, g, err);
   } else {
     STM_CUDA(cudaFuncSetAttribute(k_vanka_mrhs_tc5<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    k_vanka_mrhs_tc5<false><<<blocks, kThreads, smem, s>>>(map, L.idx, T, Y, L.C, g, err);
+    k_vanka_mrhs_tc5<false><<<blocks, kThreads, smem, s>>>(map, L.idx, T16, Y, L.C, g, err);
   }
   note_launch();
   STM_CUDA(cudaGetLastError());

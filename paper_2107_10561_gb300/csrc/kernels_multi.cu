@@ -92,7 +92,8 @@ __global__ void __launch_bounds__(256) k_spmm_struct(
     const long long* __restrict__ rowptr, const double* __restrict__ val, const int* __restrict__ nbr_ptr,
     const int* __restrict__ nbr, const int* __restrict__ ncell, const int* __restrict__ node_cells,
     const int* __restrict__ cell_nodes, long long block, int R, int C, int nv, const double* __restrict__ X,
-    const double* __restrict__ B, double* __restrict__ Y, int mode, const double* __restrict__ valT, int split) {
+    const double* __restrict__ B, double* __restrict__ Y, int mode, const double* __restrict__ valT, int split,
+    uint32_t* __restrict__ T16) {
   constexpr int KD = K * D;
   constexpr int NP = D + 1;
   constexpr int MAXC = 1 << D;
@@ -144,7 +145,13 @@ __global__ void __launch_bounds__(256) k_spmm_struct(
 #pragma unroll
         for (int l = 0; l < D; ++l) {
           const long long o = (a * block + (long long)l * R + i) * NR + lane;
-          Y[o] = mode == 1 ? B[o] - acc[a * D + l] : acc[a * D + l];
+          const double yv = mode == 1 ? B[o] - acc[a * D + l] : acc[a * D + l];
+          Y[o] = yv;
+          if (T16) {
+            uint32_t h, lo;
+            bf16_split_rn(yv, h, lo);
+            T16[o] = (lo << 16) | h;
+          }
         }
     } else {
       const long long c = job - R;
@@ -172,14 +179,20 @@ __global__ void __launch_bounds__(256) k_spmm_struct(
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
           const long long o = (a * block + (long long)D * R + c * NP + q) * NR + lane;
-          Y[o] = mode == 1 ? B[o] - acc[a * NP + q] : acc[a * NP + q];
+          const double yv = mode == 1 ? B[o] - acc[a * NP + q] : acc[a * NP + q];
+          Y[o] = yv;
+          if (T16) {
+            uint32_t h, lo;
+            bf16_split_rn(yv, h, lo);
+            T16[o] = (lo << 16) | h;
+          }
         }
     }
   }
 }
 
 stm_status spmm_structured(const Level& L, const double* X, const double* B, double* Y, int mode, cudaStream_t s,
-                           int split) {
+                           int split, uint32_t* T16) {
   if (split < NR && !L.valT) {
     set_error("multi-RHS SpMM: the values of J^T are not built");
     return STM_ERR_STATE;
@@ -189,7 +202,7 @@ stm_status spmm_structured(const Level& L, const double* X, const double* B, dou
   const int key = L.dim * 10 + L.K;
 #define SPMM(K, D) \
   k_spmm_struct<K, D><<<blocks, 256, 0, s>>>(L.rowptr, L.val, L.nbr_ptr, L.nbr, L.ncell, L.node_cells, L.cell_nodes, \
-                                             L.block, L.R, L.C, L.nv, X, B, Y, mode, L.valT, split)
+                                             L.block, L.R, L.C, L.nv, X, B, Y, mode, L.valT, split, T16)
   switch (key) {
     case 21: SPMM(1, 2); break;
     case 22: SPMM(2, 2); break;
@@ -228,6 +241,15 @@ stm_status csr_multi(const long long* rowptr, const int* col, const double* val,
   note_launch();
   STM_CUDA(cudaGetLastError());
   return STM_OK;
+}
+
+// Packed BF16 hi + lo parts (lo << 16 | hi) of an interleaved multi-vector, for the tensor-core smoother
+__global__ void k_pack_bf16_split(const double* __restrict__ X, uint32_t* __restrict__ P, long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    uint32_t h, lo;
+    bf16_split_rn(X[e], h, lo);
+    P[e] = (lo << 16) | h;
+  }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -285,13 +307,14 @@ __global__ void k_vanka_gather_multi(double* __restrict__ d, const A* __restrict
 
 stm_status ensure_multi(Hierarchy& H) {
   for (Level& L : H.L) {
-    if (L.mY && L.md) continue;
+    if (L.mY && L.md && (L.mt16 || H.p.inv_precision != STM_BF16)) continue;
     if (!L.md) {
       STM_CUDA(cudaMalloc(&L.md, sizeof(double) * (size_t)L.N * NR));
       STM_CUDA(cudaMalloc(&L.mr, sizeof(double) * (size_t)L.N * NR));
       STM_CUDA(cudaMalloc(&L.mt, sizeof(double) * (size_t)L.N * NR));
     }
     if (!L.mY) STM_CUDA(cudaMalloc(&L.mY, sizeof(double) * (size_t)L.C * L.n * NR));
+    if (!L.mt16 && H.p.inv_precision == STM_BF16) STM_CUDA(cudaMalloc(&L.mt16, sizeof(uint32_t) * (size_t)L.N * NR));
   }
   return STM_OK;
 }
@@ -301,11 +324,6 @@ stm_status vanka_step_multi(Hierarchy& H, int g, const double* R, double* Dm, bo
   Level& L = H.L[g];
   const double* T = R;
   if (split < NR) STM_TRY(ensure_transpose(H, g, s));
-  if (!d_is_zero) {
-    ProfScope ps(&H, STM_KCLASS_JACOBIAN_SPMV, s, 8.0 * (double)L.nnz + 24.0 * NR * (double)L.N, g);
-    STM_TRY(spmm_structured(L, Dm, R, L.mt, 1, s, split));
-    T = L.mt;
-  }
   const int prec = H.p.inv_precision;
   const InvLayout lay = inv_layout(L.n, prec);
   const bool fused = split == 16;
@@ -314,6 +332,13 @@ stm_status vanka_step_multi(Hierarchy& H, int g, const double* R, double* Dm, bo
     return STM_ERR_INVALID_ARG;
   }
   const bool tc = prec == STM_BF16 && (fused ? mrhs_tc_fused_supported(L.n, lay.ld) : mrhs_tc_supported(L.n, lay.ld));
+  // the tensor-core products read the residual block as packed BF16 hi + lo parts: the defect product
+  // writes them as it writes the block; a residual taken as it is gets a packing pass
+  if (!d_is_zero) {
+    ProfScope ps(&H, STM_KCLASS_JACOBIAN_SPMV, s, 8.0 * (double)L.nnz + 24.0 * NR * (double)L.N, g);
+    STM_TRY(spmm_structured(L, Dm, R, L.mt, 1, s, split, tc ? L.mt16 : nullptr));
+    T = L.mt;
+  }
   const bool y64 = prec == STM_F64;
   {
     // algorithmic bytes: the stored inverses, the index map, the 32 gathered FP64 columns of every
@@ -323,7 +348,13 @@ stm_status vanka_step_multi(Hierarchy& H, int g, const double* R, double* Dm, bo
                                 (8.0 + (y64 ? 8.0 : 4.0)) * NR * L.n),
                  g);
     if (tc) {
-      STM_TRY(mrhs_tc_apply(L, lay.ld, T, reinterpret_cast<float*>(L.mY), H.dkerr, s, fused));
+      if (d_is_zero) {
+        const long long ne = L.N * NR;
+        k_pack_bf16_split<<<(int)std::min<long long>((ne + 255) / 256, msms() * 16LL), 256, 0, s>>>(R, L.mt16, ne);
+        note_launch();
+        STM_CUDA(cudaGetLastError());
+      }
+      STM_TRY(mrhs_tc_apply(L, lay.ld, L.mt16, reinterpret_cast<float*>(L.mY), H.dkerr, s, fused));
     } else {
       const int blocks = std::min(L.C, msms() * 8);
 #define MRHS_CC(S_, A_)                                                                                          \
