@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(256, ((sizeof(TV) == 4 && VL > 8) || K < 3) ? 
 // sums go through the reduce-scatter above: with more accumulators than lanes (2D), each lane ends with
 // K*d/VL row sums (6 FP64 adds per node with VL = 4, K*d = 6), so the FP64 pipe spends its issue slots
 // on the 2 nnz FMAs.
-template <int VL, int K, int D>
+template <int VL, int K, int D, int U>
 __global__ void __launch_bounds__(256) k_spmv_nb_dyn(
     const double* __restrict__ nval, const double* __restrict__ pvalT, const long long* __restrict__ nbase,
     const int* __restrict__ nbr_ptr, const int* __restrict__ nbr, const int* __restrict__ ncell,
@@ -368,17 +368,38 @@ __global__ void __launch_bounds__(256) k_spmv_nb_dyn(
         const int p0 = nbr_ptr[i], nn = nbr_ptr[i + 1] - p0, nc = ncell[i];
         const double* blk = nval + nbase[i];
         const int npv = KD * nn;
-        int j = lane, bm = 0;
-        while (j >= nn) { j -= nn; ++bm; }
-        for (int p = lane; p < npv; p += VL) {
-          const int bb = bm / D, m = bm - bb * D;
-          const double xv = __ldg(x + bb * block + (long long)m * R + nbr[p0 + j]);
-          double vv[KD];
-          load_position<KD>(blk + (long long)p * KD, vv);
+        // U positions per step: the loads of all U are issued before the first FMA waits
+        int jk[U], bk[U];
+        jk[0] = lane;
+        bk[0] = 0;
+        while (jk[0] >= nn) { jk[0] -= nn; ++bk[0]; }
 #pragma unroll
-          for (int r = 0; r < KD; ++r) acc[r] = fma(vv[r], xv, acc[r]);
-          j += VL;
-          while (j >= nn) { j -= nn; ++bm; }
+        for (int k = 1; k < U; ++k) {
+          jk[k] = jk[k - 1] + VL;
+          bk[k] = bk[k - 1];
+          while (jk[k] >= nn) { jk[k] -= nn; ++bk[k]; }
+        }
+        for (int p = lane; p < npv; p += U * VL) {
+          double vv[U][KD], xk[U];
+#pragma unroll
+          for (int k = 0; k < U; ++k) {
+            const bool live = k == 0 || p + k * VL < npv;
+            const int bb = bk[k] / D, m = bk[k] - bb * D;
+            xk[k] = live ? __ldg(x + bb * block + (long long)m * R + nbr[p0 + jk[k]]) : 0.0;
+            if (live) load_position<KD>(blk + (long long)(p + k * VL) * KD, vv[k]);
+            else
+#pragma unroll
+              for (int r = 0; r < KD; ++r) vv[k][r] = 0.0;
+          }
+#pragma unroll
+          for (int k = 0; k < U; ++k)
+#pragma unroll
+            for (int r = 0; r < KD; ++r) acc[r] = fma(vv[k][r], xk[k], acc[r]);
+#pragma unroll
+          for (int k = 0; k < U; ++k) {
+            jk[k] += U * VL;
+            while (jk[k] >= nn) { jk[k] -= nn; ++bk[k]; }
+          }
         }
         for (int tq = lane; tq < NP * nc; tq += VL) {
           const int ci = tq / NP, q = tq - ci * NP;
@@ -418,13 +439,15 @@ __global__ void __launch_bounds__(256) k_spmv_nb_dyn(
         const double* vr = pvalT + ((pr >> 5) * (D * NV)) * 32 + (pr & 31);
         const int* cn = cell_nodes + c * NV;
         const double* xa = x + a * block;
-        double sacc = 0.0;
+        // three accumulators: three independent FMA chains per lane
+        double s3[3] = {0.0, 0.0, 0.0};
 #pragma unroll
         for (int m = 0; m < D; ++m) {
 #pragma unroll 9
           for (int jj = 0; jj < NV; ++jj)
-            sacc = fma(__ldcs(vr + (m * NV + jj) * 32), __ldg(xa + (long long)m * R + __ldg(cn + jj)), sacc);
+            s3[jj % 3] = fma(__ldcs(vr + (m * NV + jj) * 32), __ldg(xa + (long long)m * R + __ldg(cn + jj)), s3[jj % 3]);
         }
+        const double sacc = (s3[0] + s3[1]) + s3[2];
         if (mode == 0) y[row] = sacc;
         else if (mode == 1) y[row] = b[row] - sacc;
         else y[row] += sacc;
@@ -509,20 +532,20 @@ static stm_status spmv_nodeblock_t(const Level& L, const TV* nval, const TV* pva
   return STM_OK;
 }
 
-template <int VL, int K, int D>
+template <int VL, int K, int D, int U>
 static stm_status launch_nb_dyn(const Level& L, const double* nval, const double* pvalT, const double* x,
                                 const double* b, double* y, int mode, cudaStream_t s) {
   constexpr int GPW = 32 / VL;
   static int occ = 0;  // resident CTAs per SM of this instantiation
   if (!occ) {
-    STM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_nb_dyn<VL, K, D>, 256, 0));
+    STM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_nb_dyn<VL, K, D, U>, 256, 0));
     if (occ < 1) occ = 1;
   }
   const long long npr = (long long)K * L.C * (D + 1);
   const unsigned nvu = (unsigned)((L.R + GPW - 1) / GPW);
   const unsigned ntot = nvu + (unsigned)((npr + 31) / 32);
   const int blocks = (int)std::max<long long>(1, std::min<long long>((long long)occ * sms_count(), (ntot + 7) / 8));
-  k_spmv_nb_dyn<VL, K, D><<<blocks, 256, 0, s>>>(nval, pvalT, L.nbase, L.nbr_ptr, L.nbr, L.ncell, L.node_cells,
+  k_spmv_nb_dyn<VL, K, D, U><<<blocks, 256, 0, s>>>(nval, pvalT, L.nbase, L.nbr_ptr, L.nbr, L.ncell, L.node_cells,
                                                  L.cell_nodes, L.job_nodes, L.block, L.R, L.C, x, b, y, mode,
                                                  L.spmv_work, nvu, ntot);
   note_launch();
@@ -538,24 +561,24 @@ stm_status spmv_nodeblock(const Level& L, const double* nval, const double* pval
   if ((long long)L.R * (L.dim == 2 ? 4 : 8) < (long long)sms_count() * per_sm_threads) cls = 100;
   if ((long long)L.R * 16 < (long long)sms_count() * per_sm_threads / 4) cls = 200;
   switch (L.dim * 10 + L.K + cls) {
-    case 21: return launch_nb_dyn<4, 1, 2>(L, nval, pvalT, x, b, y, mode, s);
-    case 22: return launch_nb_dyn<4, 2, 2>(L, nval, pvalT, x, b, y, mode, s);
-    case 23: return launch_nb_dyn<4, 3, 2>(L, nval, pvalT, x, b, y, mode, s);
-    case 31: return launch_nb_dyn<8, 1, 3>(L, nval, pvalT, x, b, y, mode, s);
-    case 32: return launch_nb_dyn<8, 2, 3>(L, nval, pvalT, x, b, y, mode, s);
-    case 33: return launch_nb_dyn<8, 3, 3>(L, nval, pvalT, x, b, y, mode, s);
-    case 121: return launch_nb_dyn<16, 1, 2>(L, nval, pvalT, x, b, y, mode, s);
-    case 122: return launch_nb_dyn<16, 2, 2>(L, nval, pvalT, x, b, y, mode, s);
-    case 123: return launch_nb_dyn<16, 3, 2>(L, nval, pvalT, x, b, y, mode, s);
-    case 131: return launch_nb_dyn<16, 1, 3>(L, nval, pvalT, x, b, y, mode, s);
-    case 132: return launch_nb_dyn<16, 2, 3>(L, nval, pvalT, x, b, y, mode, s);
-    case 133: return launch_nb_dyn<16, 3, 3>(L, nval, pvalT, x, b, y, mode, s);
-    case 221: return launch_nb_dyn<32, 1, 2>(L, nval, pvalT, x, b, y, mode, s);
-    case 222: return launch_nb_dyn<32, 2, 2>(L, nval, pvalT, x, b, y, mode, s);
-    case 223: return launch_nb_dyn<32, 3, 2>(L, nval, pvalT, x, b, y, mode, s);
-    case 231: return launch_nb_dyn<32, 1, 3>(L, nval, pvalT, x, b, y, mode, s);
-    case 232: return launch_nb_dyn<32, 2, 3>(L, nval, pvalT, x, b, y, mode, s);
-    case 233: return launch_nb_dyn<32, 3, 3>(L, nval, pvalT, x, b, y, mode, s);
+    case 21: return launch_nb_dyn<4, 1, 2, 2>(L, nval, pvalT, x, b, y, mode, s);
+    case 22: return launch_nb_dyn<4, 2, 2, 2>(L, nval, pvalT, x, b, y, mode, s);
+    case 23: return launch_nb_dyn<4, 3, 2, 2>(L, nval, pvalT, x, b, y, mode, s);
+    case 31: return launch_nb_dyn<8, 1, 3, 2>(L, nval, pvalT, x, b, y, mode, s);
+    case 32: return launch_nb_dyn<8, 2, 3, 2>(L, nval, pvalT, x, b, y, mode, s);
+    case 33: return launch_nb_dyn<8, 3, 3, 2>(L, nval, pvalT, x, b, y, mode, s);
+    case 121: return launch_nb_dyn<16, 1, 2, 1>(L, nval, pvalT, x, b, y, mode, s);
+    case 122: return launch_nb_dyn<16, 2, 2, 1>(L, nval, pvalT, x, b, y, mode, s);
+    case 123: return launch_nb_dyn<16, 3, 2, 1>(L, nval, pvalT, x, b, y, mode, s);
+    case 131: return launch_nb_dyn<16, 1, 3, 1>(L, nval, pvalT, x, b, y, mode, s);
+    case 132: return launch_nb_dyn<16, 2, 3, 1>(L, nval, pvalT, x, b, y, mode, s);
+    case 133: return launch_nb_dyn<16, 3, 3, 1>(L, nval, pvalT, x, b, y, mode, s);
+    case 221: return launch_nb_dyn<32, 1, 2, 1>(L, nval, pvalT, x, b, y, mode, s);
+    case 222: return launch_nb_dyn<32, 2, 2, 1>(L, nval, pvalT, x, b, y, mode, s);
+    case 223: return launch_nb_dyn<32, 3, 2, 1>(L, nval, pvalT, x, b, y, mode, s);
+    case 231: return launch_nb_dyn<32, 1, 3, 1>(L, nval, pvalT, x, b, y, mode, s);
+    case 232: return launch_nb_dyn<32, 2, 3, 1>(L, nval, pvalT, x, b, y, mode, s);
+    case 233: return launch_nb_dyn<32, 3, 3, 1>(L, nval, pvalT, x, b, y, mode, s);
     default:
       set_error("node-block SpMV: unsupported (dim, k)");
       return STM_ERR_INVALID_ARG;
