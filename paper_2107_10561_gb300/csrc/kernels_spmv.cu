@@ -507,21 +507,21 @@ static stm_status spmv_nodeblock_t(const Level& L, const TV* nval, const TV* pva
   if ((long long)L.R * (L.dim == 2 ? 4 : 8) < (long long)sms_count() * per_sm_threads) cls = 100;
   if ((long long)L.R * 16 < (long long)sms_count() * per_sm_threads / 4) cls = 200;
   switch (L.dim * 10 + L.K + cls) {
-    case 21: launch_nodeblock<TV, 4, 1, 1>(L, nval, pvalT, x, b, y, mode, s); break;
-    case 22: launch_nodeblock<TV, 4, 2, 1>(L, nval, pvalT, x, b, y, mode, s); break;
-    case 23: launch_nodeblock<TV, 4, 3, 1>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 21: launch_nodeblock<TV, 4, 1, 2>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 22: launch_nodeblock<TV, 4, 2, 2>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 23: launch_nodeblock<TV, 4, 3, 2>(L, nval, pvalT, x, b, y, mode, s); break;
     case 31: launch_nodeblock<TV, 8, 1, 3>(L, nval, pvalT, x, b, y, mode, s); break;
     case 32: launch_nodeblock<TV, 8, 2, 3>(L, nval, pvalT, x, b, y, mode, s); break;
     case 33: launch_nodeblock<TV, 8, 3, 3>(L, nval, pvalT, x, b, y, mode, s); break;
-    case 121: launch_nodeblock<TV, 16, 1, 1>(L, nval, pvalT, x, b, y, mode, s); break;
-    case 122: launch_nodeblock<TV, 16, 2, 1>(L, nval, pvalT, x, b, y, mode, s); break;
-    case 123: launch_nodeblock<TV, 16, 3, 1>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 121: launch_nodeblock<TV, 16, 1, 2>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 122: launch_nodeblock<TV, 16, 2, 2>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 123: launch_nodeblock<TV, 16, 3, 2>(L, nval, pvalT, x, b, y, mode, s); break;
     case 131: launch_nodeblock<TV, 16, 1, 3>(L, nval, pvalT, x, b, y, mode, s); break;
     case 132: launch_nodeblock<TV, 16, 2, 3>(L, nval, pvalT, x, b, y, mode, s); break;
     case 133: launch_nodeblock<TV, 16, 3, 3>(L, nval, pvalT, x, b, y, mode, s); break;
-    case 221: launch_nodeblock<TV, 32, 1, 1>(L, nval, pvalT, x, b, y, mode, s); break;
-    case 222: launch_nodeblock<TV, 32, 2, 1>(L, nval, pvalT, x, b, y, mode, s); break;
-    case 223: launch_nodeblock<TV, 32, 3, 1>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 221: launch_nodeblock<TV, 32, 1, 2>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 222: launch_nodeblock<TV, 32, 2, 2>(L, nval, pvalT, x, b, y, mode, s); break;
+    case 223: launch_nodeblock<TV, 32, 3, 2>(L, nval, pvalT, x, b, y, mode, s); break;
     case 231: launch_nodeblock<TV, 32, 1, 3>(L, nval, pvalT, x, b, y, mode, s); break;
     case 232: launch_nodeblock<TV, 32, 2, 3>(L, nval, pvalT, x, b, y, mode, s); break;
     case 233: launch_nodeblock<TV, 32, 3, 3>(L, nval, pvalT, x, b, y, mode, s); break;
