@@ -17,7 +17,6 @@ namespace stm {
 constexpr int STM_KCLASS_COUNT = 8;
 
 constexpr int kMaxDim = 3;
-constexpr int kCoarseTChunk = 512;  // rows per partial sum of the transposed coarse solve
 constexpr int kQ1 = 4;  // Gauss points per direction (exact for every integrand of the forms)
 
 // Thread-local error message and helpers -----------------------------------------------------
@@ -238,7 +237,7 @@ struct Hierarchy {
   // coarse direct solver: explicit FP64 inverse of J_0, row-major [N0][N0]
   double* cinv = nullptr;
   long long N0 = 0;
-  double* cpart = nullptr;  // [ceil(N0 / kCoarseTChunk)][N0] partial sums of the transposed coarse solve
+  double* cinvT = nullptr;  // [N0][N0] its transpose, row-major (the adjoint coarse solve reads rows too)
   // coarse solve through the block LU factors in x-slab order (large coarse levels; cinv is then not
   // formed): cs_nx slabs, row offsets cs_off [nx + 1], block offsets cs_pos [6][nx] into cs_store
   // (S^{-1}, G, W, S^{-T}, P, Q), slab of every permuted row, permuted position of every row; work

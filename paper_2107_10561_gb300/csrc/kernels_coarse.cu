@@ -40,6 +40,24 @@ enum { M_SINV = 0, M_G = 1, M_W = 2, M_SINVT = 3, M_P = 4, M_Q = 5 };
 
 // y[row] (-)= sum_k M[row - off_b][k] x[off_c + k] for the rows of slab b (warp per row). NR = 1: one
 // vector; NR = 32: interleaved 32-column vectors, lane = column.
+// Dot product of a contiguous row with x over a warp: four independent load + FMA chains per lane
+// (128 consecutive entries per step), then a butterfly sum; the result is in every lane.
+__device__ __forceinline__ double row_dot(const double* __restrict__ m, const double* x, long long nc, int lane) {
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  long long k = lane;
+  for (; k + 96 < nc; k += 128) {
+    a0 = fma(__ldg(m + k), x[k], a0);
+    a1 = fma(__ldg(m + k + 32), x[k + 32], a1);
+    a2 = fma(__ldg(m + k + 64), x[k + 64], a2);
+    a3 = fma(__ldg(m + k + 96), x[k + 96], a3);
+  }
+  for (; k < nc; k += 32) a0 = fma(__ldg(m + k), x[k], a0);
+  double acc = (a0 + a1) + (a2 + a3);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  return acc;
+}
+
 template <int NR>
 __device__ __forceinline__ void slab_rows(const SlabView& S, const double* M, int b, int c, const double* x,
                                           double* y, bool subtract, long long w0, long long nw, int lane) {
@@ -49,9 +67,7 @@ __device__ __forceinline__ void slab_rows(const SlabView& S, const double* M, in
     const double* m = M + rr * nc;
     double acc = 0.0;
     if (NR == 1) {
-      for (long long k = lane; k < nc; k += 32) acc = fma(__ldg(m + k), x[c0 + k], acc);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      acc = row_dot(m, x + c0, nc, lane);
       if (lane == 0) y[r0 + rr] = subtract ? y[r0 + rr] - acc : acc;
     } else {
       for (long long k = 0; k < nc; ++k) acc = fma(__ldg(m + k), x[(c0 + k) * 32 + lane], acc);
@@ -73,7 +89,7 @@ __device__ __forceinline__ void slab_prefetch(const SlabView& S, const double* M
 }
 
 template <int NR>
-__global__ void __launch_bounds__(256) k_coarse_slab(SlabView S, const double* __restrict__ r, double* __restrict__ d,
+__global__ void __launch_bounds__(512) k_coarse_slab(SlabView S, const double* __restrict__ r, double* __restrict__ d,
                                                      double* __restrict__ u, double* __restrict__ v, int transpose) {
   cg::grid_group grid = cg::this_grid();
   const int lane = threadIdx.x & 31;
@@ -97,10 +113,7 @@ __global__ void __launch_bounds__(256) k_coarse_slab(SlabView S, const double* _
       const double* m = mat(M_SINV, b) + (row - S.off[b]) * nb;
       const long long c0 = S.off[b];
       if (NR == 1) {
-        double acc = 0.0;
-        for (long long k = lane; k < nb; k += 32) acc = fma(__ldg(m + k), u[c0 + k], acc);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        const double acc = row_dot(m, u + c0, nb, lane);
         if (lane == 0) v[row] = acc;
       } else {
         double acc = 0.0;
@@ -134,10 +147,7 @@ __global__ void __launch_bounds__(256) k_coarse_slab(SlabView S, const double* _
       const double* m = mat(M_SINVT, b) + (row - S.off[b]) * nb;
       const long long c0 = S.off[b];
       if (NR == 1) {
-        double acc = 0.0;
-        for (long long k = lane; k < nb; k += 32) acc = fma(__ldg(m + k), u[c0 + k], acc);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        const double acc = row_dot(m, u + c0, nb, lane);
         if (lane == 0) v[row] = acc;
       } else {
         double acc = 0.0;
@@ -164,7 +174,7 @@ template <int NR>
 stm_status launch_slab(Hierarchy& H, const double* r, double* d, int transpose, cudaStream_t s) {
   static int occ = 0;
   if (!occ) {
-    STM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_coarse_slab<NR>, 256, 0));
+    STM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_coarse_slab<NR>, 512, 0));
     if (occ < 1) {
       set_error("coarse slab solve: kernel does not fit on an SM");
       return STM_ERR_CUDA;
@@ -181,8 +191,10 @@ stm_status launch_slab(Hierarchy& H, const double* r, double* d, int transpose, 
   double* u = NR == 1 ? H.cs_u : H.cs_mu;
   double* v = NR == 1 ? H.cs_v : H.cs_mv;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(std::min(occ, 2) * sm_count()));
-  cfg.blockDim = dim3(256);
+  // one CTA of 16 warps per SM: the grid-wide barriers between the dependent slab steps are the
+  // largest cost, and they grow with the number of CTAs
+  cfg.gridDim = dim3((unsigned)sm_count());
+  cfg.blockDim = dim3(512);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];

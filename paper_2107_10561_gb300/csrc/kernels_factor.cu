@@ -510,8 +510,8 @@ stm_status factor_coarse(Hierarchy& H, cudaStream_t s) {
       fail(STM_ERR_OOM);
       break;
     }
-    // scratch of the transposed coarse solve, allocated here so that solves can be graph-captured
-    if (!use_slab && !H.cpart && cudaMalloc(&H.cpart, sizeof(double) * ((n + kCoarseTChunk - 1) / kCoarseTChunk) * n)) {
+    // the transposed inverse for the adjoint coarse solve
+    if (!use_slab && !H.cinvT && cudaMalloc(&H.cinvT, sizeof(double) * n * n)) {
       cudaGetLastError();
       set_error("coarse factorisation: out of device memory");
       fail(STM_ERR_OOM);
@@ -644,6 +644,7 @@ stm_status factor_coarse(Hierarchy& H, cudaStream_t s) {
     dim3 ug((unsigned)std::min<long long>((n + 255) / 256, 64), (unsigned)std::min<long long>(n, 65535));
     k_unpermute<<<ug, 256, 0, s>>>(Xp, d_iperm, n, H.cinv);
     note_launch();
+    transpose_block(H.cinv, n, n, H.cinvT, s);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
       set_error("coarse factorisation: CUDA error");
       fail(STM_ERR_CUDA);

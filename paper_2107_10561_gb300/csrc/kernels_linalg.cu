@@ -151,25 +151,6 @@ __global__ void k_dense_gemv(const double* __restrict__ A, long long n, const do
     if (lane == 0) y[row] = s;
   }
 }
-// d = Cinv^T r in two passes: CTA (x, y) takes 128 columns over one chunk of kCoarseTChunk rows (one
-// thread per column, coalesced rows), then every column adds its chunk partials in chunk order.
-__global__ void k_dense_gemv_t_part(const double* __restrict__ A, long long n, const double* __restrict__ x,
-                                    double* __restrict__ part) {
-  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  const long long i0 = (long long)blockIdx.y * kCoarseTChunk, i1 = min(n, i0 + (long long)kCoarseTChunk);
-  double s = 0.0;
-  for (long long i = i0; i < i1; ++i) s += A[i * n + j] * x[i];
-  part[(long long)blockIdx.y * n + j] = s;
-}
-__global__ void k_dense_gemv_t_sum(const double* __restrict__ part, long long n, int chunks, double* __restrict__ y) {
-  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int c = 0; c < chunks; ++c) s += part[(long long)c * n + j];
-    y[j] = s;
-  }
-}
-
 stm_status coarse_apply(Hierarchy& H, const double* r, double* d, int transpose, cudaStream_t s) {
   const long long n = H.N0;
   if (H.coarse_slab) {
@@ -177,17 +158,9 @@ stm_status coarse_apply(Hierarchy& H, const double* r, double* d, int transpose,
     return coarse_slab_apply(H, r, d, transpose, s);
   }
   ProfScope ps(&H, STM_KCLASS_COARSE, s, 8.0 * (double)n * (double)n + 16.0 * (double)n);
-  if (!transpose) {
-    const int blocks = (int)std::min<long long>((n + 7) / 8, (long long)sms() * 16);
-    k_dense_gemv<<<blocks, 256, 0, s>>>(H.cinv, n, r, d); note_launch();
-  } else {
-    const int chunks = (int)((n + kCoarseTChunk - 1) / kCoarseTChunk);
-    dim3 grid((unsigned)((n + 127) / 128), (unsigned)chunks);
-    k_dense_gemv_t_part<<<grid, 128, 0, s>>>(H.cinv, n, r, H.cpart); note_launch();
-    k_dense_gemv_t_sum<<<(int)std::min<long long>((n + 255) / 256, (long long)sms() * 8), 256, 0, s>>>(H.cpart, n, chunks,
-                                                                                                     d);
-    note_launch();
-  }
+  const int blocks = (int)std::min<long long>((n + 7) / 8, (long long)sms() * 16);
+  k_dense_gemv<<<blocks, 256, 0, s>>>(transpose ? H.cinvT : H.cinv, n, r, d);
+  note_launch();
   STM_CUDA(cudaGetLastError());
   return STM_OK;
 }
