@@ -765,7 +765,7 @@ void free_hierarchy(Hierarchy& H) {
   }
   void* hp[] = {H.cinv, H.cinvT, H.dflag, H.dkerr, H.dbad, H.V, H.Z, H.w, H.hcol, H.part, H.yvec, H.bbuf, H.xbuf,
                 H.nw_negF, H.nw_D, H.nw_Xt, H.nw_B, H.nw_Ft, H.ag_buf, H.ag_wnod,
-                H.cs_off, H.cs_pos, H.cs_rowslab, H.cs_perm, H.cs_store, H.cs_cnt, H.cs_u, H.cs_v, H.cs_mu, H.cs_mv,
+                H.cs_off, H.cs_pos, H.cs_rowslab, H.cs_perm, H.cs_store, H.cs_u, H.cs_v, H.cs_mu, H.cs_mv,
                 H.mV, H.mZ, H.mW, H.mB, H.mX, H.mh, H.mpart, H.mf, H.my};
   for (void* q : hp)
     if (q) cudaFree(q);

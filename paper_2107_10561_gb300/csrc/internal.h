@@ -247,7 +247,6 @@ struct Hierarchy {
   long long *cs_off = nullptr, *cs_pos = nullptr;
   int *cs_rowslab = nullptr, *cs_perm = nullptr;
   double *cs_store = nullptr, *cs_u = nullptr, *cs_v = nullptr, *cs_mu = nullptr, *cs_mv = nullptr;
-  unsigned* cs_cnt = nullptr;     // [3][nx] finished-row counters of the slab solve (zero between launches)
   int* dflag = nullptr;           // device flags: [0] singular flag, [1..2] bad cell (int64 split)
   int* dkerr = nullptr;           // device error word of the tensor-core pipelines (bounded waits)
   long long* dbad = nullptr;

@@ -609,8 +609,6 @@ stm_status factor_coarse(Hierarchy& H, cudaStream_t s) {
       if (!H.cs_pos) cudaMalloc(&H.cs_pos, sizeof(long long) * 6 * nx);
       if (!H.cs_rowslab) cudaMalloc(&H.cs_rowslab, sizeof(int) * n);
       if (!H.cs_perm) cudaMalloc(&H.cs_perm, sizeof(int) * n);
-      if (!H.cs_cnt && cudaMalloc(&H.cs_cnt, sizeof(unsigned) * 3 * nx) == cudaSuccess)
-        cudaMemsetAsync(H.cs_cnt, 0, sizeof(unsigned) * 3 * nx, s);
       cudaMemcpyAsync(H.cs_off, hoff.data(), sizeof(long long) * (nx + 1), cudaMemcpyHostToDevice, s);
       cudaMemcpyAsync(H.cs_pos, cpos.data(), sizeof(long long) * 6 * nx, cudaMemcpyHostToDevice, s);
       cudaMemcpyAsync(H.cs_rowslab, blk.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s);
