@@ -56,6 +56,10 @@ def parse():
                     help="FGMRES iterations of V(1,1) and V(4,4) as one coarse grid is refined (2D and 3D dG(1))")
     ap.add_argument("--newton", action="store_true",
                     help="time the damped Newton solve of the nonlinear slab problem instead of one linear solve")
+    ap.add_argument("--kernel-driver", choices=["product_sweep", "multi_sweep", "fused_sweep", "coarse"], default=None,
+                    help="small fixed launch sequence for a profiler: the finest-level FP64 product and single-RHS "
+                         "sweep, the 32-column or fused 16+16 sweep, or the coarse solve, --steps times each")
+    ap.add_argument("--levels", type=int, default=0, help="override the workload's number of levels")
     ap.add_argument("--oracle-child", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -664,12 +668,14 @@ def oracle_sample_check(args, wl, precs, x_oracle):
 
 def unique_sweep_bytes(size, prec):
     """HBM bytes a 32-column local-product launch must move at least: inverses as stored (n x ld per
-    cell), index map, the residual block once, the FP32 results (FP64 with FP64 inverses)."""
+    cell), index map, the residual block once (packed BF16 hi/lo pairs, 4 bytes per value, for BF16
+    inverses on the tensor cores; FP64 otherwise), the results (FP32; FP64 with FP64 inverses)."""
     s = {"f64": 8, "f32": 4, "bf16": 2}[prec]
     n, C, N = size["n_local"], size["n_cells"], size["n_dofs"]
     v = 16 // s
     ld = -(-n // v) * v
-    return C * n * ld * s + 4 * C * n + 256 * N + C * n * 32 * (8 if prec == "f64" else 4)
+    t_bytes = 4 if prec == "bf16" else 8
+    return C * n * ld * s + 4 * C * n + 32 * t_bytes * N + C * n * 32 * (8 if prec == "f64" else 4)
 
 
 def multi_row(args, name, steps, warmup, prec="bf16"):
@@ -766,9 +772,9 @@ def multi_row(args, name, steps, warmup, prec="bf16"):
                          "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm if ach else None,
                          "avg_launch_us": us_fin, "bytes_per_launch": ub,
                          "bytes_definition": "unique HBM bytes per launch: the stored inverses (C n ld s), the index "
-                                             "map (4 C n), the 32-column residual block once (256 N) and the FP32 "
-                                             "local results (128 C n); the gathered residual rows that several cells "
-                                             "share are counted once",
+                                             "map (4 C n), the 32-column residual block once (packed BF16 hi/lo "
+                                             "pairs, 128 N) and the FP32 local results (128 C n); the gathered "
+                                             "residual rows that several cells share are counted once",
                          "gathered_bytes_per_launch": fin["bytes"] / max(fin["launches"], 1)},
             "cpu_baseline_note": "the FP64 oracle of this workload needs ~70 GB of host memory and hours; not timed"}
 
@@ -1050,8 +1056,70 @@ def full_workload_dofs(wl):
     return (wl.k + 1) * (wl.dim * R + (wl.dim + 1) * C)
 
 
+def kernel_driver(args):
+    """Fixed launch sequences for ncu captures (one line of CUDA-event timings on stdout)."""
+    import dataclasses
+
+    import torch
+
+    import synth
+    from paper_2107_10561_gb300 import Hierarchy
+    from paper_2107_10561_gb300 import build as _build
+
+    torch.cuda.set_device(0)
+    _build.build()
+    wl = workload(args.workload)
+    if args.levels:
+        wl = dataclasses.replace(wl, n_levels=args.levels)
+    prec = args.precisions.split(",")[-1]
+    h = Hierarchy(hier_params(wl, prec, "additive"))
+    h.assemble_jacobian(lattice_vec(h, synth.linearisation_point(wl)))
+    h.factor_cells()
+    g = h.finest
+    n = h.n_dofs(g)
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    out = {"driver": args.kernel_driver, "workload": wl.name, "levels": wl.n_levels, "precision": prec,
+           "steps": args.steps}
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(args.steps):
+            fn()
+        ev1.record()
+        torch.cuda.synchronize()
+        return 1e3 * ev0.elapsed_time(ev1) / args.steps
+
+    if args.kernel_driver == "product_sweep":
+        x = torch.randn(n, dtype=torch.float64, device="cuda", generator=gen)
+        y, d = torch.empty_like(x), torch.zeros_like(x)
+        out["product_us"] = timed(lambda: h.spmv(g, x, y))
+        out["sweep_us"] = timed(lambda: h.vanka_sweep(g, x, d))
+    elif args.kernel_driver in ("multi_sweep", "fused_sweep"):
+        R = torch.randn(32, n, dtype=torch.float64, device="cuda", generator=gen)
+        D = torch.zeros_like(R)
+        if args.kernel_driver == "multi_sweep":
+            out["sweep_us"] = timed(lambda: h.vanka_sweep_multi(g, R, D))
+        else:
+            out["sweep_us"] = timed(lambda: h.vanka_sweep_fused(g, R[:16], D[:16], R[16:], D[16:]))
+    else:
+        n0 = h.n_dofs(0)
+        r0 = torch.randn(n0, dtype=torch.float64, device="cuda", generator=gen)
+        d0 = torch.empty_like(r0)
+        out["coarse_us"] = timed(lambda: h.coarse_solve(r0, d0))
+        out["coarse_transposed_us"] = timed(lambda: h.coarse_solve(r0, d0, transpose=True))
+    out["sizes"] = h.sizes(g)
+    h.close()
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
+    if args.kernel_driver:
+        kernel_driver(args)
+        return
     if args.oracle_child:
         oracle_child(args.oracle_child)
         return
