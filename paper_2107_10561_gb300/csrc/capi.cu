@@ -744,7 +744,11 @@ stm_status stm_gmres_solve_multi(stm_hierarchy* h, int nrhs, const double* B_dev
   for (;;) {
     // true residuals B - J X; a column counts as converged only when its true residual meets rtol
     // (a cycle that stopped on the recurrence estimate is checked here and restarted if needed)
-    STM_TRY(spmm_structured(F, H.mX, H.mB, H.mV, 1, s));
+    {
+      ProfScope ps(&H, STM_KCLASS_JACOBIAN_SPMV, s, 8.0 * (double)F.nnz + 24.0 * 32 * (double)F.N,
+                   (int)H.L.size() - 1);
+      STM_TRY(spmm_structured(F, H.mX, H.mB, H.mV, 1, s));
+    }
     STM_TRY(col_norms(H.mV, beta));
     bool any = false;
     std::vector<int> active(32, 0), jd(32, 0);
@@ -775,7 +779,11 @@ stm_status stm_gmres_solve_multi(stm_hierarchy* h, int nrhs, const double* B_dev
       double* vj = H.mV + j * VS;
       double* zj = H.mZ + j * VS;
       STM_TRY(vcycle_multi(H, vj, zj, s));
-      STM_TRY(spmm_structured(F, zj, nullptr, H.mW, 0, s));
+      {
+        ProfScope ps(&H, STM_KCLASS_JACOBIAN_SPMV, s, 8.0 * (double)F.nnz + 16.0 * 32 * (double)F.N,
+                     (int)H.L.size() - 1);
+        STM_TRY(spmm_structured(F, zj, nullptr, H.mW, 0, s));
+      }
       {
         ProfScope ps(&H, STM_KCLASS_KRYLOV, s, 8.0 * VS * (4.0 * (j + 1) + 4.0));
         STM_TRY(mdots(H.mV, j + 1, H.mW, N, H.mh, H.mpart, nb, s));

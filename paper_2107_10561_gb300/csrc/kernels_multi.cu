@@ -407,6 +407,7 @@ stm_status vcycle_multi(Hierarchy& H, const double* R_fine, double* D_fine, cuda
     STM_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * (size_t)L.N * NR, s));
     for (int it = 0; it < H.p.nu1; ++it) STM_TRY(vanka_step_multi(H, g, r, d, it == 0, s));
     if (H.p.nu1 > 0) {
+      ProfScope ps(&H, STM_KCLASS_JACOBIAN_SPMV, s, 8.0 * (double)L.nnz + 24.0 * NR * (double)L.N, g);
       STM_TRY(spmm_structured(L, d, r, L.mt, 1, s));
     } else {
       STM_CUDA(cudaMemcpyAsync(L.mt, r, sizeof(double) * (size_t)L.N * NR, cudaMemcpyDeviceToDevice, s));
