@@ -238,12 +238,13 @@ struct Hierarchy {
   double* cinv = nullptr;
   long long N0 = 0;
   double* cinvT = nullptr;  // [N0][N0] its transpose, row-major (the adjoint coarse solve reads rows too)
-  // coarse solve through the block LU factors in x-slab order (large coarse levels; cinv is then not
-  // formed): cs_nx slabs, row offsets cs_off [nx + 1], block offsets cs_pos [6][nx] into cs_store
-  // (S^{-1}, G, W, S^{-T}, P, Q), slab of every permuted row, permuted position of every row; work
+  // coarse solve through the twisted block factors in x-slab order (large coarse levels; cinv is then
+  // not formed): cs_nx slabs eliminated from both ends towards slab cs_t, row offsets cs_off [nx + 1],
+  // block offsets cs_pos [8][nx] into cs_store (inverse, lower and upper chain blocks, back-substitution
+  // block, for J_0 and for J_0^T), slab of every permuted row, permuted position of every row; work
   // vectors for one column and for 32 interleaved columns
   bool coarse_slab = false;
-  int cs_nx = 0;
+  int cs_nx = 0, cs_t = 0;
   long long *cs_off = nullptr, *cs_pos = nullptr;
   int *cs_rowslab = nullptr, *cs_perm = nullptr;
   double *cs_store = nullptr, *cs_u = nullptr, *cs_v = nullptr, *cs_mu = nullptr, *cs_mv = nullptr;

@@ -1,21 +1,24 @@
 // Direct coarse solve of Algorithm 1 (d_1 = J_1^{-1} r_1, or J_1^{-T} r_1 in the adjoint V-cycle) through
-// the block LU factors of J_1 in x-slab order (kernels_factor.cu), for coarse levels too large for the
-// dense explicit inverse to pay (3D: 18,000 DoFs, 2.6 GB as a dense inverse).
+// the twisted block factors of J_1 in x-slab order (kernels_factor.cu), for coarse levels too large for
+// the dense explicit inverse to pay (3D: 18,000 DoFs, 2.6 GB as a dense inverse).
 //
-// In slab order J_1 is block tridiagonal; with S_b the Schur complements and A_{b,c} its blocks,
-//   J_1 = L U,  L: diagonal S_b, sub-diagonal A_{b,b-1};  U: unit diagonal, super-diagonal W_b = S_b^{-1} A_{b,b+1}.
-// Forward solve  J_1 x = r:   z_b = S_b^{-1} r_b (all slabs at once);  y_b = z_b - G_b y_{b-1}, G_b = S_b^{-1} A_{b,b-1};
-//                              x_b = y_b - W_b x_{b+1}.
-// Transposed     J_1^T x = r: w_b = r_b - P_b w_{b-1}, P_b = W_{b-1}^T;  s_b = S_b^{-T} w_b (all slabs);
-//                              x_b = s_b - Q_b x_{b+1}, Q_b = S_b^{-T} A_{b+1,b}^T.
-// Every matrix is stored row-major per block, so each product is a warp-per-row dot product over
-// contiguous rows. The two dependent chains (nx - 1 steps each) run inside one cooperative kernel with
-// a grid-wide barrier between steps (the barrier also orders the vector written in one step before its
-// reads in the next); while a step waits at the barrier each warp prefetches into L2 the rows it will
-// read in the next step. About 5x fewer bytes and FP64 FMAs than the explicit inverse. Measured on the
-// 18,000-DoF 3D coarse level: 344 us per solve against 560 us for the explicit inverse; per-slab
-// completion counters polled by the waiting warps instead of the barriers (555 us), four FMA chains per
-// lane (413 us) and one 16-warp CTA per SM (421 us) were slower.
+// In slab order J_1 is block tridiagonal. Its slabs are eliminated from both ends towards the twist
+// slab t; with Sinv_b the inverse Schur complements, the solve of J_1 x = r is
+//   z_b = Sinv_b r_b                                         (all slabs at once)
+//   y_b = z_b - Lo_b y_{b-1},  b = 1 .. t-1   together with  y_b = z_b - Up_b y_{b+1},  b = nx-2 .. t+1
+//   x_t = z_t - Lo_t y_{t-1} - Up_t y_{t+1}
+//   x_b = y_b - Bk_b x_{b+1},  b = t-1 .. 0   together with  x_b = y_b - Bk_b x_{b-1},  b = t+1 .. nx-1
+// (Lo_b = Sinv_b A_{b,b-1}, Up_b = Sinv_b A_{b,b+1}, Bk_b the back-substitution block). J_1^T has its
+// own blocks of the same shapes (kinds 4..7), so both directions run the same kernel. Every block is
+// stored row-major, so each product is a warp-per-row dot product over contiguous rows. The dependent
+// steps (about nx instead of the 2 (nx - 1) of a one-sided block LU, each step working on the two slabs
+// at the ends of the chains) run inside one cooperative kernel with a grid-wide barrier between steps
+// (the barrier also orders the vector written in one step before its reads in the next); before a
+// step's barrier every thread prefetches into L2 a share of the blocks the next step reads.
+// Measured on the 18,000-DoF 3D coarse level with the one-sided factors: 344 us per solve against
+// 560 us for the explicit inverse; per-slab completion counters polled by the waiting warps instead of
+// the barriers (555 us), four FMA chains per lane (413 us) and one 16-warp CTA per SM (421 us) were
+// slower.
 // A 32-column variant (interleaved [N][32] multi-vectors, lane = column) serves the multi-RHS V-cycle.
 #include <cooperative_groups.h>
 
@@ -31,49 +34,96 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
 }
 
 struct SlabView {
-  int nx;
+  int nx, t;
   long long n;
   const long long* off;   // [nx + 1] first permuted row of every slab
-  const long long* pos;   // [6][nx] block offsets in store: Sinv, G, W, Sinvt, P, Q (-1: absent)
+  const long long* pos;   // [8][nx] block offsets in store (-1: absent)
   const int* rowslab;     // [n] slab of every permuted row
   const int* perm;        // [n] permuted position of every row of J_1
   const double* store;
 };
 
-enum { M_SINV = 0, M_G = 1, M_W = 2, M_SINVT = 3, M_P = 4, M_Q = 5 };
+enum { K_INV = 0, K_LO = 1, K_UP = 2, K_BACK = 3 };
 
-// y[row] (-)= sum_k M[row - off_b][k] x[off_c + k] for the rows of slab b (warp per row). NR = 1: one
-// vector; NR = 32: interleaved 32-column vectors, lane = column.
+// One product task of a step: rows of slab b, y_b (-)= M x_c (M: nb x nc, row-major).
+struct Task {
+  const double* M;
+  long long r0, nb, c0, nc;
+};
+
+__device__ __forceinline__ Task make_task(const SlabView& S, int kind, int b, int c) {
+  Task k;
+  k.M = S.store + S.pos[kind * S.nx + b];
+  k.r0 = S.off[b];
+  k.nb = S.off[b + 1] - k.r0;
+  k.c0 = S.off[c];
+  k.nc = S.off[c + 1] - k.c0;
+  return k;
+}
+__device__ __forceinline__ Task no_task() {
+  Task k;
+  k.M = nullptr;
+  k.r0 = k.nb = k.c0 = k.nc = 0;
+  return k;
+}
+
+// Dot product of one stored row m[0 .. nc) with the vector x (slab part starting at x). NR = 1: lanes
+// stride the row, result in every lane; NR = 32: lane = column of interleaved 32-column vectors.
 template <int NR>
-__device__ __forceinline__ void slab_rows(const SlabView& S, const double* M, int b, int c, const double* x,
-                                          double* y, bool subtract, long long w0, long long nw, int lane) {
-  const long long r0 = S.off[b], nb = S.off[b + 1] - r0;
-  const long long c0 = S.off[c], nc = S.off[c + 1] - c0;
-  for (long long rr = w0; rr < nb; rr += nw) {
-    const double* m = M + rr * nc;
+__device__ __forceinline__ double row_dot(const double* m, long long nc, const double* x, int lane) {
+  if (NR == 1) {
     double acc = 0.0;
-    if (NR == 1) {
-      for (long long k = lane; k < nc; k += 32) acc = fma(__ldg(m + k), x[c0 + k], acc);
+    for (long long k = lane; k < nc; k += 32) acc = fma(__ldg(m + k), x[k], acc);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) y[r0 + rr] = subtract ? y[r0 + rr] - acc : acc;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc;
+  } else {
+    double a0 = 0.0, a1 = 0.0;
+    long long k = 0;
+    for (; k + 1 < nc; k += 2) {
+      a0 = fma(__ldg(m + k), x[k * 32 + lane], a0);
+      a1 = fma(__ldg(m + k + 1), x[(k + 1) * 32 + lane], a1);
+    }
+    if (k < nc) a0 = fma(__ldg(m + k), x[k * 32 + lane], a0);
+    return a0 + a1;
+  }
+}
+
+// y_{b} -= M x_c for the rows of up to two tasks (warps stride the concatenated rows of both).
+template <int NR>
+__device__ __forceinline__ void pair_step(const Task& A, const Task& B, double* v, long long gw, long long nw,
+                                          int lane) {
+  const long long tot = A.nb + B.nb;
+  for (long long rr = gw; rr < tot; rr += nw) {
+    const Task& T = rr < A.nb ? A : B;
+    const long long r = rr < A.nb ? rr : rr - A.nb;
+    const double acc = row_dot<NR>(T.M + r * T.nc, T.nc, v + T.c0 * NR, lane);
+    if (NR == 1) {
+      if (lane == 0) v[T.r0 + r] -= acc;
     } else {
-      for (long long k = 0; k < nc; ++k) acc = fma(__ldg(m + k), x[(c0 + k) * 32 + lane], acc);
-      double* o = y + (r0 + rr) * 32 + lane;
-      *o = subtract ? *o - acc : acc;
+      v[(T.r0 + r) * 32 + lane] -= acc;
     }
   }
 }
 
-// Prefetch into L2 the rows of block M (slab b, columns of slab c) that warp w0 will read.
-__device__ __forceinline__ void slab_prefetch(const SlabView& S, const double* M, int b, int c, long long w0,
-                                              long long nw, int lane) {
-  const long long nb = S.off[b + 1] - S.off[b], nc = S.off[c + 1] - S.off[c];
-  for (long long rr = w0; rr < nb; rr += nw) {
-    const char* row = reinterpret_cast<const char*>(M + rr * nc);
-    const long long bytes = nc * 8;
-    for (long long o = (long long)lane * 128; o < bytes; o += 32 * 128) prefetch_l2(row + o);
-  }
+// Every thread of the grid prefetches a share of the 128-byte lines of the task's block into L2.
+__device__ __forceinline__ void task_prefetch(const Task& T, long long gt, long long nt) {
+  if (!T.M) return;
+  const char* p = reinterpret_cast<const char*>(T.M);
+  const long long bytes = T.nb * T.nc * 8;
+  for (long long o = gt * 128; o < bytes; o += nt * 128) prefetch_l2(p + o);
+}
+
+// Chain tasks of step s (1-based) of the forward elimination and of the back substitution.
+__device__ __forceinline__ void chain_tasks(const SlabView& S, int base, int s, Task& A, Task& B) {
+  const int t = S.t, nx = S.nx;
+  A = s <= t - 1 ? make_task(S, base + K_LO, s, s - 1) : no_task();
+  B = nx - 1 - s >= t + 1 ? make_task(S, base + K_UP, nx - 1 - s, nx - s) : no_task();
+}
+__device__ __forceinline__ void back_tasks(const SlabView& S, int base, int s, Task& A, Task& B) {
+  const int t = S.t, nx = S.nx;
+  A = t - s >= 0 ? make_task(S, base + K_BACK, t - s, t - s + 1) : no_task();
+  B = t + s <= nx - 1 ? make_task(S, base + K_BACK, t + s, t + s - 1) : no_task();
 }
 
 template <int NR>
@@ -85,77 +135,81 @@ __global__ void __launch_bounds__(256) k_coarse_slab(SlabView S, const double* _
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
   const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nt = (long long)gridDim.x * blockDim.x;
-  const int nx = S.nx;
-  auto mat = [&](int kind, int b) -> const double* { return S.store + S.pos[kind * nx + b]; };
+  const int nx = S.nx, t = S.t;
+  const int base = transpose ? 4 : 0;
+  const int nchain = max(t - 1, nx - 2 - t), nback = max(t, nx - 1 - t);
   // gather into slab order
   for (long long e = gt; e < S.n * NR; e += nt) {
     const long long i = e / NR;
     u[(long long)S.perm[i] * NR + (e - i * NR)] = r[e];
   }
   grid.sync();
-  if (!transpose) {
-    // z_b = S_b^{-1} r_b for every slab: every warp takes rows across all slabs
-    for (long long row = gw; row < S.n; row += nw) {
-      const int b = S.rowslab[row];
-      const long long nb = S.off[b + 1] - S.off[b];
-      const double* m = mat(M_SINV, b) + (row - S.off[b]) * nb;
-      const long long c0 = S.off[b];
+  // z_b = Sinv_b r_b for every slab: every warp takes rows across all slabs
+  for (long long row = gw; row < S.n; row += nw) {
+    const int b = S.rowslab[row];
+    const long long c0 = S.off[b], nb = S.off[b + 1] - c0;
+    const double acc = row_dot<NR>(S.store + S.pos[(base + K_INV) * nx + b] + (row - c0) * nb, nb, u + c0 * NR, lane);
+    if (NR == 1) {
+      if (lane == 0) v[row] = acc;
+    } else {
+      v[row * 32 + lane] = acc;
+    }
+  }
+  Task A, B;
+  if (nchain >= 1) {
+    chain_tasks(S, base, 1, A, B);
+    task_prefetch(A, gt, nt);
+    task_prefetch(B, gt, nt);
+  }
+  grid.sync();
+  // the two elimination chains, one step of each per barrier
+  for (int s = 1; s <= nchain; ++s) {
+    chain_tasks(S, base, s, A, B);
+    pair_step<NR>(A, B, v, gw, nw, lane);
+    Task nA, nB;
+    if (s < nchain) {
+      chain_tasks(S, base, s + 1, nA, nB);
+    } else {
+      nA = t >= 1 ? make_task(S, base + K_LO, t, t - 1) : no_task();
+      nB = t + 1 < nx ? make_task(S, base + K_UP, t, t + 1) : no_task();
+    }
+    task_prefetch(nA, gt, nt);
+    task_prefetch(nB, gt, nt);
+    grid.sync();
+  }
+  // the twist slab: x_t = z_t - Lo_t y_{t-1} - Up_t y_{t+1}
+  {
+    const Task lo = t >= 1 ? make_task(S, base + K_LO, t, t - 1) : no_task();
+    const Task up = t + 1 < nx ? make_task(S, base + K_UP, t, t + 1) : no_task();
+    const long long r0 = S.off[t], nb = S.off[t + 1] - r0;
+    for (long long rr = gw; rr < nb; rr += nw) {
+      double acc = 0.0;
+      if (lo.M) acc += row_dot<NR>(lo.M + rr * lo.nc, lo.nc, v + lo.c0 * NR, lane);
+      if (up.M) acc += row_dot<NR>(up.M + rr * up.nc, up.nc, v + up.c0 * NR, lane);
       if (NR == 1) {
-        double acc = 0.0;
-        for (long long k = lane; k < nb; k += 32) acc = fma(__ldg(m + k), u[c0 + k], acc);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) v[row] = acc;
+        if (lane == 0) v[r0 + rr] -= acc;
       } else {
-        double acc = 0.0;
-        for (long long k = 0; k < nb; ++k) acc = fma(__ldg(m + k), u[(c0 + k) * 32 + lane], acc);
-        v[row * 32 + lane] = acc;
+        v[(r0 + rr) * 32 + lane] -= acc;
       }
     }
-    if (nx > 1) slab_prefetch(S, mat(M_G, 1), 1, 0, gw, nw, lane);
+    if (nback >= 1) {
+      back_tasks(S, base, 1, A, B);
+      task_prefetch(A, gt, nt);
+      task_prefetch(B, gt, nt);
+    }
     grid.sync();
-    for (int b = 1; b < nx; ++b) {  // y_b = z_b - G_b y_{b-1}
-      slab_rows<NR>(S, mat(M_G, b), b, b - 1, v, v, true, gw, nw, lane);
-      if (b + 1 < nx) slab_prefetch(S, mat(M_G, b + 1), b + 1, b, gw, nw, lane);
-      else slab_prefetch(S, mat(M_W, nx - 2), nx - 2, nx - 1, gw, nw, lane);
-      grid.sync();
+  }
+  // back substitution away from the twist, both directions per barrier
+  for (int s = 1; s <= nback; ++s) {
+    back_tasks(S, base, s, A, B);
+    pair_step<NR>(A, B, v, gw, nw, lane);
+    if (s < nback) {
+      Task nA, nB;
+      back_tasks(S, base, s + 1, nA, nB);
+      task_prefetch(nA, gt, nt);
+      task_prefetch(nB, gt, nt);
     }
-    for (int b = nx - 2; b >= 0; --b) {  // x_b = y_b - W_b x_{b+1}
-      slab_rows<NR>(S, mat(M_W, b), b, b + 1, v, v, true, gw, nw, lane);
-      if (b > 0) slab_prefetch(S, mat(M_W, b - 1), b - 1, b, gw, nw, lane);
-      grid.sync();
-    }
-  } else {
-    if (nx > 1) slab_prefetch(S, mat(M_P, 1), 1, 0, gw, nw, lane);
-    for (int b = 1; b < nx; ++b) {  // w_b = r_b - P_b w_{b-1}
-      slab_rows<NR>(S, mat(M_P, b), b, b - 1, u, u, true, gw, nw, lane);
-      if (b + 1 < nx) slab_prefetch(S, mat(M_P, b + 1), b + 1, b, gw, nw, lane);
-      grid.sync();
-    }
-    for (long long row = gw; row < S.n; row += nw) {  // s_b = S_b^{-T} w_b
-      const int b = S.rowslab[row];
-      const long long nb = S.off[b + 1] - S.off[b];
-      const double* m = mat(M_SINVT, b) + (row - S.off[b]) * nb;
-      const long long c0 = S.off[b];
-      if (NR == 1) {
-        double acc = 0.0;
-        for (long long k = lane; k < nb; k += 32) acc = fma(__ldg(m + k), u[c0 + k], acc);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) v[row] = acc;
-      } else {
-        double acc = 0.0;
-        for (long long k = 0; k < nb; ++k) acc = fma(__ldg(m + k), u[(c0 + k) * 32 + lane], acc);
-        v[row * 32 + lane] = acc;
-      }
-    }
-    if (nx > 1) slab_prefetch(S, mat(M_Q, nx - 2), nx - 2, nx - 1, gw, nw, lane);
     grid.sync();
-    for (int b = nx - 2; b >= 0; --b) {  // x_b = s_b - Q_b x_{b+1}
-      slab_rows<NR>(S, mat(M_Q, b), b, b + 1, v, v, true, gw, nw, lane);
-      if (b > 0) slab_prefetch(S, mat(M_Q, b - 1), b - 1, b, gw, nw, lane);
-      grid.sync();
-    }
   }
   // back to the row order of J_1
   for (long long e = gt; e < S.n * NR; e += nt) {
@@ -176,6 +230,7 @@ stm_status launch_slab(Hierarchy& H, const double* r, double* d, int transpose, 
   }
   SlabView S;
   S.nx = H.cs_nx;
+  S.t = H.cs_t;
   S.n = H.N0;
   S.off = H.cs_off;
   S.pos = H.cs_pos;

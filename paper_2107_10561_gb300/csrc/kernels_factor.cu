@@ -429,13 +429,17 @@ static void transpose_block(const double* src, long long rows, long long cols, d
   note_launch();
 }
 
-// Coarse levels from this size on are solved through the slab block-LU factors instead of an explicit
+// Coarse levels from this size on are solved through the twisted slab factors instead of an explicit
 // inverse: the dense inverse costs N^2 FP64 FMAs per solve (0.5 ms at 18,000 DoFs), the factors about a
-// fifth of that plus two chains of nx - 1 dependent slab products.
+// fifth of that in about nx dependent slab steps.
 constexpr long long kCoarseSlabMinDofs = 8000;
 
-// Slab ordering of level 0 (host, once).
-static void coarse_slabs(const Level& L, std::vector<int>& iperm, std::vector<int>& blk, std::vector<long long>& off) {
+// Slab ordering of level 0 (host, once). The pressure of cell i goes to slab i + 1 (the last cell's to the
+// last slab) when the slabs are eliminated upwards (i < tw), and to slab i when they are eliminated
+// downwards (i >= tw, the lower half of the twisted factorisation): either way it is eliminated after the
+// velocities of the cell's far plane, which keeps the Schur complements regular.
+static void coarse_slabs(const Level& L, int tw, std::vector<int>& iperm, std::vector<int>& blk,
+                         std::vector<long long>& off) {
   const int d = L.dim, nx = L.cells[0];
   const long long n = L.N;
   std::vector<int> slab(n);
@@ -447,7 +451,8 @@ static void coarse_slabs(const Level& L, std::vector<int>& iperm, std::vector<in
       }
     for (int c = 0; c < L.C; ++c)
       for (int q = 0; q < L.np; ++q)
-        slab[a * L.block + (long long)d * L.R + (long long)c * L.np + q] = std::min(L.h_cell_xyz[3 * c] + 1, nx - 1);
+        slab[a * L.block + (long long)d * L.R + (long long)c * L.np + q] =
+            L.h_cell_xyz[3 * c] < tw ? std::min(L.h_cell_xyz[3 * c] + 1, nx - 1) : L.h_cell_xyz[3 * c];
   }
   off.assign(nx + 2, 0);
   for (long long r = 0; r < n; ++r) off[slab[r] + 1]++;
@@ -463,6 +468,121 @@ static void coarse_slabs(const Level& L, std::vector<int>& iperm, std::vector<in
   }
 }
 
+// In-place inverse of one dense FP64 block (Gauss-Jordan, partial pivoting): in shared memory when it
+// fits, else column by column in global memory.
+static void invert_block(double* Db, long long nb, int* piv, double* scal, int* flag, int maxsm, cudaStream_t s) {
+  const size_t smem = sizeof(double) * nb * nb + sizeof(short) * nb + 16;
+  if (smem + 64 <= (size_t)maxsm) {
+    cudaFuncSetAttribute(k_block_inverse_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_block_inverse_smem<<<1, 1024, smem, s>>>(Db, (int)nb, flag);
+    note_launch();
+  } else {
+    block_inverse_global(Db, nb, piv, scal, flag, s);
+  }
+}
+
+// Twisted block factorisation of J_0 in slab order, eliminated from both ends towards slab t = nx / 2
+// (A_bc the blocks of J_0, nb_b the rows of slab b):
+//   top    b < t :  S_b = A_bb - A_{b,b-1} W_{b-1},            W_b = S_b^{-1} A_{b,b+1},  G_b  = S_b^{-1} A_{b,b-1}
+//   bottom b > t :  S_b = A_bb - A_{b,b+1} V_{b+1},            V_b = S_b^{-1} A_{b,b-1},  G'_b = S_b^{-1} A_{b,b+1}
+//   middle b = t :  S_t = A_tt - A_{t,t-1} W_{t-1} - A_{t,t+1} V_{t+1},  G_t, G'_t as above.
+// Then J_0 x = r is z_b = S_b^{-1} r_b (all slabs); y_b = z_b - G_b y_{b-1} (b = 1 .. t-1) together with
+// y_b = z_b - G'_b y_{b+1} (b = nx-2 .. t+1); x_t = z_t - G_t y_{t-1} - G'_t y_{t+1}; x_b = y_b - W_b x_{b+1}
+// (b = t-1 .. 0) together with x_b = y_b - V_b x_{b-1} (b = t+1 .. nx-1): about half the dependent steps
+// of the one-sided block LU. The Schur complements of J_0^T in the same order are the S_b^T, so the
+// transposed system needs no inversion of its own: its blocks are S_b^{-T}, (A_{b-1,b} S_b^{-1})^T (lower
+// chain, or back-substitution below the twist) and (A_{b+1,b} S_b^{-1})^T (upper chain, or back-
+// substitution above the twist). Every block is kept row-major in H.cs_store at H.cs_pos[kind][b], kinds
+// 0..3 (inverse, lower chain G, upper chain G', back-substitution W or V) for J_0 and 4..7 for J_0^T.
+static stm_status twisted_slab_factors(Hierarchy& H, const Level& L, const std::vector<long long>& off,
+                                       const std::vector<int>& iperm, const std::vector<int>& blk, double* raw,
+                                       const std::vector<long long>& dpos, const std::vector<long long>& lpos,
+                                       const std::vector<long long>& upos, int* piv, double* scal, int maxsm,
+                                       cudaStream_t s) {
+  enum { K_INV = 0, K_LO = 1, K_UP = 2, K_BACK = 3, K_T = 4 };
+  const int nx = L.cells[0];
+  const long long n = L.N;
+  const int t = nx / 2;
+  auto rows = [&](int b) { return off[b + 1] - off[b]; };
+  std::vector<long long> cpos(8 * (size_t)nx, -1);
+  long long ct = 0, maxe = 0;
+  for (int b = 0; b < nx; ++b) {
+    const long long nb = rows(b), npv = b > 0 ? rows(b - 1) : 0, nnx = b + 1 < nx ? rows(b + 1) : 0;
+    for (int sys = 0; sys < 2; ++sys) {
+      const int k0 = sys * K_T;
+      cpos[(k0 + K_INV) * nx + b] = ct; ct += nb * nb;
+      if (b >= 1 && b <= t) { cpos[(k0 + K_LO) * nx + b] = ct; ct += nb * npv; }
+      if (b >= t && b + 1 < nx) { cpos[(k0 + K_UP) * nx + b] = ct; ct += nb * nnx; }
+      if (b < t) { cpos[(k0 + K_BACK) * nx + b] = ct; ct += nb * nnx; }
+      if (b > t) { cpos[(k0 + K_BACK) * nx + b] = ct; ct += nb * npv; }
+    }
+    maxe = std::max(maxe, std::max(npv, nnx) * nb);
+  }
+  double* E = nullptr;
+  if ((!H.cs_store && cudaMalloc(&H.cs_store, sizeof(double) * ct)) || cudaMalloc(&E, sizeof(double) * std::max(maxe, 1LL)) ||
+      (!H.cs_u && cudaMalloc(&H.cs_u, sizeof(double) * n)) || (!H.cs_v && cudaMalloc(&H.cs_v, sizeof(double) * n)) ||
+      (!H.cs_off && cudaMalloc(&H.cs_off, sizeof(long long) * (nx + 1))) ||
+      (!H.cs_pos && cudaMalloc(&H.cs_pos, sizeof(long long) * 8 * nx)) ||
+      (!H.cs_rowslab && cudaMalloc(&H.cs_rowslab, sizeof(int) * n)) || (!H.cs_perm && cudaMalloc(&H.cs_perm, sizeof(int) * n))) {
+    cudaGetLastError();
+    if (E) cudaFree(E);
+    set_error("coarse factorisation: out of device memory");
+    return STM_ERR_OOM;
+  }
+  double* cs = H.cs_store;
+  auto at = [&](int kind, int b) { return cs + cpos[kind * nx + b]; };
+  const double* D = raw;  // raw blocks: A_bb at dpos, A_{b,b-1} at lpos (b >= 1), A_{b,b+1} at upos (b < nx-1)
+  auto Lo = [&](int b) { return D + lpos[b]; };
+  auto Up = [&](int b) { return D + upos[b]; };
+  auto copy = [&](const double* src, long long r, long long c, double* dst) {
+    k_copy_block<<<(int)std::min<long long>((r * c + 255) / 256, sm_count() * 8LL), 256, 0, s>>>(src, r, c, c, dst, c);
+    note_launch();
+  };
+  // one slab: S_b from A_bb and the neighbours already eliminated, its inverse, then its chain blocks
+  auto slab = [&](int b) {
+    const long long nb = rows(b), npv = b > 0 ? rows(b - 1) : 0, nnx = b + 1 < nx ? rows(b + 1) : 0;
+    double* Sb = at(K_INV, b);
+    copy(D + dpos[b], nb, nb, Sb);
+    if (b > 0 && b <= t)  // - A_{b,b-1} W_{b-1}
+      dgemm((int)nb, (int)nb, (int)npv, -1.0, Lo(b), npv, at(K_BACK, b - 1), nb, 1.0, Sb, nb, s);
+    if (b + 1 < nx && b >= t)  // - A_{b,b+1} V_{b+1}
+      dgemm((int)nb, (int)nb, (int)nnx, -1.0, Up(b), nnx, at(K_BACK, b + 1), nb, 1.0, Sb, nb, s);
+    invert_block(Sb, nb, piv, scal, H.dflag + 1, maxsm, s);
+    if (b >= 1 && b <= t) dgemm((int)nb, (int)npv, (int)nb, 1.0, Sb, nb, Lo(b), npv, 0.0, at(K_LO, b), npv, s);
+    if (b >= t && b + 1 < nx) dgemm((int)nb, (int)nnx, (int)nb, 1.0, Sb, nb, Up(b), nnx, 0.0, at(K_UP, b), nnx, s);
+    if (b < t) dgemm((int)nb, (int)nnx, (int)nb, 1.0, Sb, nb, Up(b), nnx, 0.0, at(K_BACK, b), nnx, s);
+    if (b > t) dgemm((int)nb, (int)npv, (int)nb, 1.0, Sb, nb, Lo(b), npv, 0.0, at(K_BACK, b), npv, s);
+    // J_0^T: S_b^{-T}; (A_{b-1,b} S_b^{-1})^T and (A_{b+1,b} S_b^{-1})^T
+    transpose_block(Sb, nb, nb, at(K_T + K_INV, b), s);
+    if (b > 0) {
+      dgemm((int)npv, (int)nb, (int)nb, 1.0, Up(b - 1), nb, Sb, nb, 0.0, E, nb, s);
+      transpose_block(E, npv, nb, at(K_T + (b <= t ? K_LO : K_BACK), b), s);
+    }
+    if (b + 1 < nx) {
+      dgemm((int)nnx, (int)nb, (int)nb, 1.0, Lo(b + 1), nb, Sb, nb, 0.0, E, nb, s);
+      transpose_block(E, nnx, nb, at(K_T + (b < t ? K_BACK : K_UP), b), s);
+    }
+  };
+  for (int b = 0; b < t; ++b) slab(b);
+  for (int b = nx - 1; b > t; --b) slab(b);
+  slab(t);
+  std::vector<long long> hoff(off.begin(), off.begin() + nx + 1);
+  cudaMemcpyAsync(H.cs_off, hoff.data(), sizeof(long long) * (nx + 1), cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(H.cs_pos, cpos.data(), sizeof(long long) * 8 * nx, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(H.cs_rowslab, blk.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(H.cs_perm, iperm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s);
+  const cudaError_t e1 = cudaGetLastError(), e2 = cudaStreamSynchronize(s);
+  cudaFree(E);
+  if (e1 != cudaSuccess || e2 != cudaSuccess) {
+    set_error("coarse factorisation: CUDA error");
+    return STM_ERR_CUDA;
+  }
+  H.cs_nx = nx;
+  H.cs_t = t;
+  H.coarse_slab = true;
+  return STM_OK;
+}
+
 stm_status factor_coarse(Hierarchy& H, cudaStream_t s) {
   Level& L = H.L[0];
   const long long n = L.N;
@@ -471,7 +591,7 @@ stm_status factor_coarse(Hierarchy& H, cudaStream_t s) {
   const bool use_slab = n >= kCoarseSlabMinDofs && nx >= 2;
   std::vector<int> iperm, blk;
   std::vector<long long> off;
-  coarse_slabs(L, iperm, blk, off);
+  coarse_slabs(L, use_slab ? nx / 2 : nx, iperm, blk, off);
   // dense block storage: D_b, Lo_b (b >= 1), Up_b (b < nx-1), W_b, G_b
   std::vector<long long> dpos(nx), lpos(nx, 0), upos(nx, 0), wpos(nx, 0), gpos(nx, 0);
   long long tot = 0;
@@ -532,6 +652,10 @@ stm_status factor_coarse(Hierarchy& H, cudaStream_t s) {
     int dev = 0, maxsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (use_slab) {
+      st = twisted_slab_factors(H, L, off, iperm, blk, store, dpos, lpos, upos, piv, scal, maxsm, s);
+      break;
+    }
     // forward block LU
     for (int b = 0; b < nx; ++b) {
       const long long nb = off[b + 1] - off[b];
@@ -540,14 +664,7 @@ stm_status factor_coarse(Hierarchy& H, cudaStream_t s) {
         const long long np_ = off[b] - off[b - 1];
         dgemm((int)nb, (int)nb, (int)np_, -1.0, store + lpos[b], np_, store + wpos[b - 1], nb, 1.0, Db, nb, s);
       }
-      const size_t smem = sizeof(double) * nb * nb + sizeof(short) * nb + 16;
-      if (smem + 64 <= (size_t)maxsm) {
-        cudaFuncSetAttribute(k_block_inverse_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_block_inverse_smem<<<1, 1024, smem, s>>>(Db, (int)nb, H.dflag + 1);
-        note_launch();
-      } else {
-        block_inverse_global(Db, nb, piv, scal, H.dflag + 1, s);
-      }
+      invert_block(Db, nb, piv, scal, H.dflag + 1, maxsm, s);
       if (b + 1 < nx) {  // W_b = S_b^{-1} A_{b,b+1}
         const long long nn_ = off[b + 2] - off[b + 1];
         dgemm((int)nb, (int)nn_, (int)nb, 1.0, Db, nb, store + upos[b], nn_, 0.0, store + wpos[b], nn_, s);
@@ -556,73 +673,6 @@ stm_status factor_coarse(Hierarchy& H, cudaStream_t s) {
         const long long np_ = off[b] - off[b - 1];
         dgemm((int)nb, (int)np_, (int)nb, 1.0, Db, nb, store + lpos[b], np_, 0.0, store + gpos[b], np_, s);
       }
-    }
-    if (use_slab) {
-      // keep the factors: S_b^{-1}, G_b, W_b for J_0 x = r and S_b^{-T}, P_b = W_{b-1}^T,
-      // Q_b = (A_{b+1,b} S_b^{-1})^T for J_0^T x = r, row-major per block
-      enum { M_SINV = 0, M_G, M_W, M_SINVT, M_P, M_Q };
-      std::vector<long long> cpos(6 * (size_t)nx, -1);
-      long long ct = 0, maxe = 0;
-      for (int b = 0; b < nx; ++b) {
-        const long long nb = off[b + 1] - off[b];
-        const long long npv = b > 0 ? off[b] - off[b - 1] : 0, nnx = b + 1 < nx ? off[b + 2] - off[b + 1] : 0;
-        cpos[M_SINV * nx + b] = ct; ct += nb * nb;
-        if (npv) { cpos[M_G * nx + b] = ct; ct += nb * npv; }
-        if (nnx) { cpos[M_W * nx + b] = ct; ct += nb * nnx; }
-        cpos[M_SINVT * nx + b] = ct; ct += nb * nb;
-        if (npv) { cpos[M_P * nx + b] = ct; ct += nb * npv; }
-        if (nnx) { cpos[M_Q * nx + b] = ct; ct += nb * nnx; maxe = std::max(maxe, nb * nnx); }
-      }
-      double* E = nullptr;
-      if ((!H.cs_store && cudaMalloc(&H.cs_store, sizeof(double) * ct)) || cudaMalloc(&E, sizeof(double) * std::max(maxe, 1LL)) ||
-          (!H.cs_u && cudaMalloc(&H.cs_u, sizeof(double) * n)) || (!H.cs_v && cudaMalloc(&H.cs_v, sizeof(double) * n))) {
-        cudaGetLastError();
-        if (E) cudaFree(E);
-        set_error("coarse factorisation: out of device memory");
-        fail(STM_ERR_OOM);
-        break;
-      }
-      for (int b = 0; b < nx; ++b) {
-        const long long nb = off[b + 1] - off[b];
-        const long long npv = b > 0 ? off[b] - off[b - 1] : 0, nnx = b + 1 < nx ? off[b + 2] - off[b + 1] : 0;
-        double* cs = H.cs_store;
-        const int cb = (int)std::min<long long>((nb * nb + 255) / 256, sm_count() * 8LL);
-        k_copy_block<<<cb, 256, 0, s>>>(store + dpos[b], nb, nb, nb, cs + cpos[M_SINV * nx + b], nb);
-        note_launch();
-        transpose_block(store + dpos[b], nb, nb, cs + cpos[M_SINVT * nx + b], s);
-        if (npv) {
-          k_copy_block<<<cb, 256, 0, s>>>(store + gpos[b], nb, npv, npv, cs + cpos[M_G * nx + b], npv);
-          note_launch();
-          // P_b = W_{b-1}^T: W_{b-1} is nb_{b-1} x nb_b
-          transpose_block(store + wpos[b - 1], npv, nb, cs + cpos[M_P * nx + b], s);
-        }
-        if (nnx) {
-          k_copy_block<<<cb, 256, 0, s>>>(store + wpos[b], nb, nnx, nnx, cs + cpos[M_W * nx + b], nnx);
-          note_launch();
-          // E = A_{b+1,b} S_b^{-1} (nb_{b+1} x nb_b), Q_b = E^T
-          dgemm((int)nnx, (int)nb, (int)nb, 1.0, store + lpos[b + 1], nb, store + dpos[b], nb, 0.0, E, nb, s);
-          transpose_block(E, nnx, nb, cs + cpos[M_Q * nx + b], s);
-        }
-      }
-      std::vector<long long> hoff(off.begin(), off.begin() + nx + 1);
-      if (!H.cs_off) cudaMalloc(&H.cs_off, sizeof(long long) * (nx + 1));
-      if (!H.cs_pos) cudaMalloc(&H.cs_pos, sizeof(long long) * 6 * nx);
-      if (!H.cs_rowslab) cudaMalloc(&H.cs_rowslab, sizeof(int) * n);
-      if (!H.cs_perm) cudaMalloc(&H.cs_perm, sizeof(int) * n);
-      cudaMemcpyAsync(H.cs_off, hoff.data(), sizeof(long long) * (nx + 1), cudaMemcpyHostToDevice, s);
-      cudaMemcpyAsync(H.cs_pos, cpos.data(), sizeof(long long) * 6 * nx, cudaMemcpyHostToDevice, s);
-      cudaMemcpyAsync(H.cs_rowslab, blk.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s);
-      cudaMemcpyAsync(H.cs_perm, iperm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s);
-      const cudaError_t e1 = cudaGetLastError(), e2 = cudaStreamSynchronize(s);
-      cudaFree(E);
-      if (e1 != cudaSuccess || e2 != cudaSuccess) {
-        set_error("coarse factorisation: CUDA error");
-        fail(STM_ERR_CUDA);
-        break;
-      }
-      H.cs_nx = nx;
-      H.coarse_slab = true;
-      break;
     }
     // Z = L^{-1} (block lower triangular) into the block rows of Xp
     for (int b = 0; b < nx; ++b) {
