@@ -280,7 +280,7 @@ def recorded_traffic(workload_name, kernel, prec=None):
     for e in rec.get("captures", []):
         if e.get("workload") != workload_name or e.get("kernel") != kernel:
             continue
-        if prec is not None and e.get("precision") != prec:
+        if prec is not None and e.get("precision") not in (prec, "any"):
             continue
         try:
             sha = hashlib.sha256(open(os.path.join(ROOT, e["source"]), "rb").read()).hexdigest()

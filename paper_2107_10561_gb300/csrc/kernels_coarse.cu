@@ -15,10 +15,10 @@
 // at the ends of the chains) run inside one cooperative kernel with a grid-wide barrier between steps
 // (the barrier also orders the vector written in one step before its reads in the next); before a
 // step's barrier every thread prefetches into L2 a share of the blocks the next step reads.
-// Measured on the 18,000-DoF 3D coarse level with the one-sided factors: 344 us per solve against
-// 560 us for the explicit inverse; per-slab completion counters polled by the waiting warps instead of
-// the barriers (555 us), four FMA chains per lane (413 us) and one 16-warp CTA per SM (421 us) were
-// slower.
+// Measured on the 18,000-DoF 3D coarse level (16 slabs): 325 us per solve, against 347 us with the
+// one-sided factors and 560 us for the explicit inverse. Per-slab completion counters polled by the
+// waiting warps instead of the barriers (555 us), four FMA chains per lane (413 us one-sided, 329 us
+// twisted) and one 16-warp CTA per SM (421 us) were slower.
 // A 32-column variant (interleaved [N][32] multi-vectors, lane = column) serves the multi-RHS V-cycle.
 #include <cooperative_groups.h>
 
