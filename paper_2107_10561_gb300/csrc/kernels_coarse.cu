@@ -15,10 +15,15 @@
 // at the ends of the chains) run inside one cooperative kernel with a grid-wide barrier between steps
 // (the barrier also orders the vector written in one step before its reads in the next); before a
 // step's barrier every thread prefetches into L2 a share of the blocks the next step reads.
-// Measured on the 18,000-DoF 3D coarse level (16 slabs): 325 us per solve, against 347 us with the
-// one-sided factors and 560 us for the explicit inverse. Per-slab completion counters polled by the
-// waiting warps instead of the barriers (555 us), four FMA chains per lane (413 us one-sided, 329 us
-// twisted) and one 16-warp CTA per SM (421 us) were slower.
+// Measured on the 18,000-DoF 3D coarse level (16 slabs): 312 us per solve with every resident CTA in
+// the grid (325 us with two per SM), against 347 us with the one-sided factors and 560 us for the
+// explicit inverse. Of the 312 us, the barriers with the gather and scatter take about 57 us and the
+// batched products z_b about 72 us; each dependent step about 11 us. Slower variants:
+//   - per-slab completion counters polled by the waiting warps instead of the barriers: 555 us;
+//   - four FMA chains per lane: 413 us one-sided, 329 us twisted;
+//   - one 16-warp CTA per SM: 421 us;
+//   - requesting the blocks two steps ahead at the start of each step: 473 us;
+//   - no L2 requests at all: 315 us.
 // A 32-column variant (interleaved [N][32] multi-vectors, lane = column) serves the multi-RHS V-cycle.
 #include <cooperative_groups.h>
 
@@ -240,7 +245,7 @@ stm_status launch_slab(Hierarchy& H, const double* r, double* d, int transpose, 
   double* u = NR == 1 ? H.cs_u : H.cs_mu;
   double* v = NR == 1 ? H.cs_v : H.cs_mv;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(std::min(occ, 2) * sm_count()));
+  cfg.gridDim = dim3((unsigned)(std::min(occ, 4) * sm_count()));
   cfg.blockDim = dim3(256);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
