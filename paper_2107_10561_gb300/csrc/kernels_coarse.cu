@@ -15,10 +15,11 @@
 // at the ends of the chains) run inside one cooperative kernel with a grid-wide barrier between steps
 // (the barrier also orders the vector written in one step before its reads in the next); before a
 // step's barrier every thread prefetches into L2 a share of the blocks the next step reads.
-// Measured on the 18,000-DoF 3D coarse level (16 slabs): 312 us per solve with every resident CTA in
-// the grid (325 us with two per SM), against 347 us with the one-sided factors and 560 us for the
-// explicit inverse. Of the 312 us, the barriers with the gather and scatter take about 57 us and the
-// batched products z_b about 72 us; each dependent step about 11 us. Slower variants:
+// Measured on the 18,000-DoF 3D coarse level (16 slabs): 290 us per solve, against 347 us with the
+// one-sided factors and 560 us for the explicit inverse. With four loads per lane in flight (312 us)
+// the barriers with the gather and scatter took about 57 us, the batched products z_b about 72 us and
+// each dependent step about 11 us: a row's dot product waits on memory round trips, so eight
+// independent loads per lane are issued before the first FMA (sixteen: 317 us). Slower variants:
 //   - per-slab completion counters polled by the waiting warps instead of the barriers: 555 us;
 //   - four FMA chains per lane: 413 us one-sided, 329 us twisted;
 //   - one 16-warp CTA per SM: 421 us;
@@ -77,8 +78,26 @@ __device__ __forceinline__ Task no_task() {
 template <int NR>
 __device__ __forceinline__ double row_dot(const double* m, long long nc, const double* x, int lane) {
   if (NR == 1) {
-    double acc = 0.0;
-    for (long long k = lane; k < nc; k += 32) acc = fma(__ldg(m + k), x[k], acc);
+    // 8 independent loads of the row and of x per lane are in flight before the first FMA waits
+    constexpr int UR = 8;
+    double a[UR];
+#pragma unroll
+    for (int q = 0; q < UR; ++q) a[q] = 0.0;
+    long long k = lane;
+    for (; k + 32 * (UR - 1) < nc; k += 32 * UR) {
+      double mv[UR], xv[UR];
+#pragma unroll
+      for (int q = 0; q < UR; ++q) {
+        mv[q] = __ldg(m + k + 32 * q);
+        xv[q] = x[k + 32 * q];
+      }
+#pragma unroll
+      for (int q = 0; q < UR; ++q) a[q] = fma(mv[q], xv[q], a[q]);
+    }
+    for (; k < nc; k += 32) a[0] = fma(__ldg(m + k), x[k], a[0]);
+#pragma unroll
+    for (int q = 1; q < UR; ++q) a[0] += a[q];
+    double acc = a[0];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     return acc;
