@@ -94,7 +94,7 @@ template <int VB> struct Conv<__nv_bfloat16, VB> {
 // CTA = P cell slots of T threads; thread (rc, cg) of a slot accumulates rows rc*V..rc*V+V-1 over
 // the columns j = cg (mod Q); the Q partial sums of a row are added through shared memory.
 template <typename S, int VB>
-__global__ void __launch_bounds__(256) k_vanka_local(const S* __restrict__ inv, const int* __restrict__ idx,
+__global__ void __launch_bounds__(256, sizeof(S) == 2 ? 5 : 4) k_vanka_local(const S* __restrict__ inv, const int* __restrict__ idx,
                                                      const double* __restrict__ t, double* __restrict__ Y,
                                                      const int* __restrict__ cell_list, int ncells, VGeom g,
                                                      double* __restrict__ d_scatter, double omega) {
@@ -337,6 +337,54 @@ static void launch_warp(const Level& L, const void* inv, const VGeom& g, const d
                                             omega);
 }
 
+// Cells per CTA for the block-per-cells kernel. All resident CTAs run rounds of P cells in lockstep
+// with the memory system, so the launch takes ceil(rounds) rounds with rounds = ncells / (P x resident
+// CTAs): among the P that keep at least 85 % of the largest resident thread count, take the one whose
+// rounds come closest below a whole number (3D dG(1), 16,128 cells: P = 11 at five CTAs per SM gives
+// 1.93 rounds, against 2.41 at four). Cached per (n, cells) of a level.
+template <typename S, int VB>
+static void launch_local_fwd(const Level& L, const void* inv, VGeom g, const double* t, const int* cells, int nc,
+                             double* scatter, double omega, cudaStream_t s) {
+  using A = typename Acc<S>::T;
+  struct Pick { int n, nc, P, blocks; };
+  static std::vector<Pick> memo;
+  auto smem_of = [&](int P) { return sizeof(A) * ((size_t)P * g.n + (size_t)P * g.Q * g.ld) + 16; };
+  int P = g.P, blocks = 0;
+  bool found = false;
+  for (const Pick& m : memo)
+    if (m.n == g.n && m.nc == nc) { P = m.P; blocks = m.blocks; found = true; break; }
+  if (!found) {
+    const int pmax = std::max(1, 256 / g.T);
+    std::vector<int> occ(pmax + 1, 0);
+    int best_threads = 0;
+    for (int p = 1; p <= pmax; ++p) {
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[p], k_vanka_local<S, VB>, g.T * p, smem_of(p)) != cudaSuccess)
+        occ[p] = 0;
+      best_threads = std::max(best_threads, occ[p] * g.T * p);
+    }
+    double best_eff = -1.0;
+    for (int p = 1; p <= pmax; ++p) {
+      if (occ[p] <= 0 || occ[p] * g.T * p * 100 < best_threads * 85) continue;
+      const double slots = (double)occ[p] * sm_count();
+      const double rounds = std::max(1.0, (double)((nc + p - 1) / p) / slots);
+      const double eff = rounds / std::ceil(rounds);
+      if (eff > best_eff + 1e-9 || (eff > best_eff - 1e-9 && p == g.P)) {
+        best_eff = eff;
+        P = p;
+        blocks = (int)std::max(1.0, std::min(slots, (double)((nc + p - 1) / p)));
+      }
+    }
+    if (blocks <= 0) {  // no occupancy answer: the default geometry, one CTA per group up to 8 per SM
+      P = g.P;
+      blocks = std::min((nc + P - 1) / P, sm_count() * 8);
+    }
+    memo.push_back(Pick{g.n, nc, P, blocks});
+  }
+  g.P = P;
+  k_vanka_local<S, VB><<<blocks, g.T * P, smem_of(P), s>>>((const S*)inv, L.idx, t, L.Y, cells, nc, g, scatter,
+                                                          omega);
+}
+
 template <typename S>
 static void launch_fwd(const Level& L, const void* inv, int vb, const VGeom& g, const double* t, const int* cells,
                        int nc, double* scatter, double omega, cudaStream_t s) {
@@ -347,16 +395,12 @@ static void launch_fwd(const Level& L, const void* inv, int vb, const VGeom& g, 
     else if constexpr (sizeof(S) < 8) launch_warp<S, 4>(L, inv, g, t, cells, nc, scatter, omega, s);
     return;
   }
-  const size_t smem = sizeof(A) * ((size_t)g.P * g.n + (size_t)g.P * g.Q * g.ld) + 16;
-  const int groups = (nc + g.P - 1) / g.P;
-  const int blocks = std::min(groups, sm_count() * 8);
-  const int threads = g.T * g.P;
   if (vb == 16) {
-    k_vanka_local<S, 16><<<blocks, threads, smem, s>>>((const S*)inv, L.idx, t, L.Y, cells, nc, g, scatter, omega);
+    launch_local_fwd<S, 16>(L, inv, g, t, cells, nc, scatter, omega, s);
   } else if (vb == 8 || sizeof(S) == 8) {
-    k_vanka_local<S, 8><<<blocks, threads, smem, s>>>((const S*)inv, L.idx, t, L.Y, cells, nc, g, scatter, omega);
+    launch_local_fwd<S, 8>(L, inv, g, t, cells, nc, scatter, omega, s);
   } else if constexpr (sizeof(S) < 8) {
-    k_vanka_local<S, 4><<<blocks, threads, smem, s>>>((const S*)inv, L.idx, t, L.Y, cells, nc, g, scatter, omega);
+    launch_local_fwd<S, 4>(L, inv, g, t, cells, nc, scatter, omega, s);
   }
 }
 
