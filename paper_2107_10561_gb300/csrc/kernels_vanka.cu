@@ -332,7 +332,12 @@ static void launch_warp(const Level& L, const void* inv, const VGeom& g, const d
   }
   int Q = 1;
   while (2 * Q * g.LDV <= 32) Q *= 2;
-  const int blocks = std::max(1, std::min((nc + 7) / 8, sm_count() * per_sm));
+  // one warp per cell in rounds of the resident warps: as few warps as give the same number of rounds,
+  // so that every warp streams the same number of cells and none idles through a last partial round
+  const long long maxw = 8LL * sm_count() * per_sm;
+  const long long rounds = std::max(1LL, ((long long)nc + maxw - 1) / maxw);
+  const long long warps = ((long long)nc + rounds - 1) / rounds;
+  const int blocks = (int)std::max(1LL, (warps + 7) / 8);
   k_vanka_warp<S, VB><<<blocks, 256, 0, s>>>((const S*)inv, L.idx, t, L.Y, cells, nc, g.n, g.ld, g.LDV, Q, scatter,
                                             omega);
 }
