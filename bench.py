@@ -363,6 +363,14 @@ def max_over_ranks(value, dist, device):
     return float(t.item())
 
 
+def mode_precision(args):
+    """Precision of the single-precision study modes (Newton, marching, mesh and robustness studies):
+    the last requested one whose V-cycle defects stay FP64, else the last one."""
+    toks = args.precisions.split(",")
+    keep = [t for t in toks if "+f32d" not in t]
+    return keep[-1] if keep else toks[-1]
+
+
 def split_precision(tok):
     """'bf16+f32d' -> ('bf16', 'f32'): cell-inverse storage and V-cycle defect precision."""
     inv, sep, d = tok.partition("+")
@@ -868,7 +876,7 @@ def gpu_leg_newton(args, local_rank):
         out[prec] = {"ms": ev0.elapsed_time(ev1) / args.steps, "info": info,
                      "launches": (Hierarchy.kernel_launches() - launches0) / args.steps}
         h.close()
-    head = args.precisions.split(",")[-1]
+    head = mode_precision(args)
     r = out[head]
     cfg = {"workload": f"{wl.name}: damped Newton for one slab, U = {wl.inflow_u}, from the seeded state",
            "stop": "||F|| <= max(1e-10, ||F_0|| / 1e4)", "linear_rtol": args.rtol, "parallelism": "single GPU"}
@@ -897,7 +905,7 @@ def gpu_leg_march(args, local_rank):
     torch.cuda.set_device(local_rank)
     _build.build()
     wl = workload(args.workload)
-    prec = args.precisions.split(",")[-1]
+    prec = mode_precision(args)
     p = hier_params(wl, prec, "additive")
     h = Hierarchy(p)
     idx = h.dof_lattice_index()
@@ -947,7 +955,7 @@ def gpu_leg_robustness(args, local_rank):
     torch.cuda.set_device(local_rank)
     _build.build()
     base = workload(args.workload)
-    prec = args.precisions.split(",")[-1]
+    prec = mode_precision(args)
     table = []
     t_all = time.perf_counter()
     for nu in (1e-3, 5e-4, 3e-4, 2e-4, 1e-4):
@@ -994,7 +1002,7 @@ def gpu_leg_mesh(args, local_rank):
 
     torch.cuda.set_device(local_rank)
     _build.build()
-    prec = args.precisions.split(",")[-1]
+    prec = mode_precision(args)
     table = []
     t_all = time.perf_counter()
     for base_name, levels in (("c4_2d_k1", (3, 4, 5, 6)), ("c3_3d_k1", (2, 3, 4))):
@@ -1099,7 +1107,7 @@ def kernel_driver(args):
     wl = workload(args.workload)
     if args.levels:
         wl = dataclasses.replace(wl, n_levels=args.levels)
-    prec = args.precisions.split(",")[-1]
+    prec = mode_precision(args)
     h = Hierarchy(hier_params(wl, prec, "additive"))
     h.assemble_jacobian(lattice_vec(h, synth.linearisation_point(wl)))
     h.factor_cells()

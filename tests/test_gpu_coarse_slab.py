@@ -1,7 +1,10 @@
-"""Direct coarse solve of Algorithm 1 on a coarse level large enough for the slab block-LU path (the 3D
-channel's 16x4x4 level-1 grid minus the obstacle: 18,000 DoFs): d = J_1^{-1} r and d = J_1^{-T} r against
-a sparse direct solve of the oracle's J_1 (1e-10 relative), for one vector and for 32 columns inside the
-multi-right-hand-side V-cycle (through the coarse solve of a two-level V(0,0) cycle: P J_1^{-1} P^T r).
+"""Direct coarse solve of Algorithm 1 on coarse levels large enough for the twisted slab factors: d =
+J_1^{-1} r and d = J_1^{-T} r against a sparse direct solve of the oracle's J_1 (1e-10 relative), for one
+vector and for 32 columns inside the multi-right-hand-side V-cycle (through the coarse solve of a
+two-level V(0,0) cycle: P J_1^{-1} P^T r). Coarse grids (all minus the obstacle):
+  - 16x4x4 (the 3D channel's level 1, 18,000 DoFs): 16 slabs, twist at slab 8, chains of 7 and 6 steps;
+  - 9x4x4: an odd slab count, twist at slab 4, chains of equal length;
+  - 2x8x8: two slabs, no chain step, one back-substitution step.
 Small coarse levels keep the explicit inverse and are covered by test_gpu_parity.test_coarse_solve."""
 import dataclasses
 
@@ -16,10 +19,10 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def pair():
+@pytest.fixture(scope="module", params=[(16, 4, 4), (9, 4, 4), (2, 8, 8)], ids=["16x4x4", "9x4x4", "2x8x8"])
+def pair(request):
     from oracle import fem
-    wl = dataclasses.replace(synth.WORKLOADS["c3_3d_k1"], n_levels=2)
+    wl = dataclasses.replace(synth.WORKLOADS["c3_3d_k1"], n_levels=2, coarse_cells=request.param)
     lev0 = fem.Level(wl.dim, wl.k, wl.coarse_cells, wl.length, wl.obstacle_lo, wl.obstacle_hi)
     st = fem.fine_lattice_to_level(synth.linearisation_point(wl), wl.fine_cells, lev0)
     J0 = fem.assemble_jacobian(lev0, lev0.dofs_from_lattice(st), wl.tau, wl.nu, wl.gamma1, wl.gamma2)
