@@ -1136,10 +1136,16 @@ def kernel_driver(args):
     elif args.kernel_driver in ("multi_sweep", "fused_sweep"):
         R = torch.randn(32, n, dtype=torch.float64, device="cuda", generator=gen)
         D = torch.zeros_like(R)
-        if args.kernel_driver == "multi_sweep":
-            out["sweep_us"] = timed(lambda: h.vanka_sweep_multi(g, R, D))
-        else:
-            out["sweep_us"] = timed(lambda: h.vanka_sweep_fused(g, R[:16], D[:16], R[16:], D[16:]))
+        fn = ((lambda: h.vanka_sweep_multi(g, R, D)) if args.kernel_driver == "multi_sweep"
+              else (lambda: h.vanka_sweep_fused(g, R[:16], D[:16], R[16:], D[16:])))
+        out["sweep_us"] = timed(fn)
+        # the local products alone: event pairs around each launch inside the library
+        h.profile_enable(True)
+        for _ in range(args.steps):
+            fn()
+        loc = h.profile_read("vanka_local", g)
+        h.profile_enable(False)
+        out["local_us"] = 1e3 * loc["ms"] / max(loc["launches"], 1)
     else:
         n0 = h.n_dofs(0)
         r0 = torch.randn(n0, dtype=torch.float64, device="cuda", generator=gen)
