@@ -295,7 +295,12 @@ static stm_status gmres_core(Hierarchy& H, const double* b, double* x, const stm
   for (;;) {
     // r = b - J x  -> V[0]. The stopping decision is taken on this true residual: a cycle that ends
     // because the recurrence estimate met rtol comes back here, and restarts if b - J x does not.
-    STM_TRY(jacobian_apply(H, G - 1, x, b, H.V, 1, tr, s));
+    // From x = 0 the first residual is b itself (exactly), so no product is needed.
+    if (cycles == 0 && !o.use_x0) {
+      STM_CUDA(cudaMemcpyAsync(H.V, b, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    } else {
+      STM_TRY(jacobian_apply(H, G - 1, x, b, H.V, 1, tr, s));
+    }
     double beta = 0.0;
     STM_TRY(host_norm(H.V, &beta));
     if (!std::isfinite(beta)) {
@@ -744,7 +749,10 @@ stm_status stm_gmres_solve_multi(stm_hierarchy* h, int nrhs, const double* B_dev
   for (;;) {
     // true residuals B - J X; a column counts as converged only when its true residual meets rtol
     // (a cycle that stopped on the recurrence estimate is checked here and restarted if needed)
-    {
+    if (it == 0 && !opts->use_x0) {
+      // from X = 0 the first residuals are the right-hand sides themselves (exactly)
+      STM_CUDA(cudaMemcpyAsync(H.mV, H.mB, sizeof(double) * VS, cudaMemcpyDeviceToDevice, s));
+    } else {
       ProfScope ps(&H, STM_KCLASS_JACOBIAN_SPMV, s, 8.0 * (double)F.nnz + 24.0 * 32 * (double)F.N,
                    (int)H.L.size() - 1);
       STM_TRY(spmm_structured(F, H.mX, H.mB, H.mV, 1, s));
