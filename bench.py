@@ -333,7 +333,7 @@ def defect_roofline(r, sizes, hbm, peak_source, workload_name):
             "peak_source": peak_source, "bytes_per_launch": by, "avg_launch_us": us}
 
 
-def spmm_roofline(f, nnz, fp64_peak, kern):
+def spmm_roofline(f, nnz, fp64_peak, kern, workload_name):
     """The multi-RHS FP64 SpMM Y = J_g X (32 columns), finest level, FP64-pipe bound.
 
     achieved = 2 * nnz * 32 FLOP per launch (every stored value meets all 32 columns) / average event
@@ -345,10 +345,12 @@ def spmm_roofline(f, nnz, fp64_peak, kern):
     flops = 2.0 * nnz * 32
     achieved = flops / (us * 1e-6) / 1e12
     total = sum(v["ms"] for v in kern.values())
+    traffic = recorded_traffic(workload_name, "k_spmm_struct")
     return {"kernel": "k_spmm_struct (Y = J_g X, 32 columns, finest level, FP64)", "bound": "alu",
             "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-            "frac": achieved / fp64_peak if fp64_peak else None, "traffic": None,
-            "traffic_source": "no capture of this kernel",
+            "frac": achieved / fp64_peak if fp64_peak else None,
+            "traffic": traffic["per_launch_bytes"] if traffic else None,
+            "traffic_source": traffic["source"] if traffic else "no capture of the current kernel source",
             "peak_source": "FP64 FMA rate measured in this run (stm_measure_fp64_peak)",
             "flops_per_launch": flops, "avg_launch_us": us, "launches_per_solve": f["launches"],
             "share_of_profiled_solve": f["ms"] / total if total > 0 else None}
@@ -788,7 +790,7 @@ def multi_row(args, name, steps, warmup, prec="bf16"):
     us_fin = 1e3 * fin["ms"] / max(fin["launches"], 1)
     ach = ub / (us_fin * 1e-6) / 1e9 if fin["ms"] > 0 else None
     fp64_peak = Hierarchy.measure_fp64_peak()
-    spmm = spmm_roofline(fin_spmm, sizes[-1]["nnz"], fp64_peak, kern)
+    spmm = spmm_roofline(fin_spmm, sizes[-1]["nnz"], fp64_peak, kern, name)
     vanka = {"kernel": f"k_vanka_mrhs_tc5 (multi-RHS Vanka local products, {prec} inverses on tcgen05), "
                        f"finest level, 32 columns", "bound": "hbm",
              "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm if ach else None,
