@@ -367,6 +367,12 @@ stm_status stm_profile_read(stm_hierarchy* h, int kernel_class, int level, doubl
 /* Measured FP64 FMA throughput of the current device in TFLOP/s (8 independent FMA chains per thread,
  * best of two timed runs). The FP64 products with J are bound by this rate on GB300. Synchronous. */
 stm_status stm_measure_fp64_peak(double* tflops, void* stream);
+/* Verification of the bounded waits of the pipelined kernels (the tensor-core smoother): one thread
+ * waits on an mbarrier phase that nothing completes, with the same helper the pipelines use. The wait
+ * gives up after one second of wall time and sets bit 128 of a device error word; the kernel then
+ * returns normally and the context stays usable. *timed_out = 1 when the bit was set, *ms = the
+ * kernel's CUDA-event time. Synchronous; allocates and frees 4 bytes of device memory. */
+stm_status stm_selftest_bounded_wait(int* timed_out, double* ms, void* stream);
 
 /* Number of kernel launches issued by this library in this process so far. */
 long long stm_kernel_launches(void);

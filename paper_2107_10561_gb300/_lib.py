@@ -87,6 +87,7 @@ SIGNATURES = {
     "stm_profile_read": ([_P, _I, _I, _DP, _LP, _DP], _I),
     "stm_kernel_launches": ([], C.c_longlong),
     "stm_measure_fp64_peak": ([_DP, _P], _I),
+    "stm_selftest_bounded_wait": ([_IP, _DP, _P], _I),
     "stm_destroy": ([_P], None),
     "stm_last_error": ([], C.c_char_p),
 }

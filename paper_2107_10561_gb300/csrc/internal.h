@@ -374,6 +374,7 @@ stm_status vanka_step_multi(Hierarchy& H, int g, const double* R, double* Dm, bo
 // (kernels_mrhs_tc.cu); err: device word set when a pipeline wait times out
 // fused = true: columns 0-15 get Y = J^{-1} T, columns 16-31 Y = J^{-T} T from the same inverse tile
 bool mrhs_tc_supported(int n, int ld);
+stm_status bounded_wait_selftest(int* err, cudaStream_t s);  // error word bit 128 after ~1 s
 bool mrhs_tc_fused_supported(int n, int ld);
 // T16: the residual block as packed BF16 hi + lo parts (lo << 16 | hi), [N][32]
 stm_status mrhs_tc_apply(const Level& L, int ld, const uint32_t* T16, float* Y, int* err, cudaStream_t s,

@@ -458,6 +458,18 @@ TcGeom tc_geom(int n, int ld) {
   return g;
 }
 
+
+// Self-test of the bounded wait: one thread waits for a phase of an mbarrier that nothing arrives on.
+// The wait gives up after kWaitNs, sets the error word and the kernel returns normally.
+__global__ void k_bounded_wait_selftest(int* err) {
+  __shared__ uint64_t never;
+  if (threadIdx.x == 0) {
+    mbar_init(saddr(&never), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_wait(saddr(&never), 0u, err, 128);
+  }
+}
+
 }  // namespace
 
 // The tensor-core path applies when the stored BF16 columns are whole 16-byte units (TMA strides) and
@@ -497,6 +509,13 @@ stm_status mrhs_tc_apply(const Level& L, int ld, const uint32_t* T16, float* Y, 
     STM_CUDA(cudaFuncSetAttribute(k_vanka_mrhs_tc5<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     k_vanka_mrhs_tc5<false><<<blocks, kThreads, smem, s>>>(map, L.idx, T16, Y, L.C, g, err);
   }
+  note_launch();
+  STM_CUDA(cudaGetLastError());
+  return STM_OK;
+}
+
+stm_status bounded_wait_selftest(int* err, cudaStream_t s) {
+  k_bounded_wait_selftest<<<1, 32, 0, s>>>(err);
   note_launch();
   STM_CUDA(cudaGetLastError());
   return STM_OK;

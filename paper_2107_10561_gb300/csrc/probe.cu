@@ -1,6 +1,8 @@
 // Measurement support: FP64 FMA throughput of the current device (the peak against which the
 // FP64-pipe-bound kernels of the solve are reported). Eight independent FMA chains per thread,
 // 8 CTAs of 256 threads per SM; the result is FLOP/s = 2 x FMAs / CUDA-event time.
+// Verification support: the bounded mbarrier wait of the pipelined kernels, run against a barrier
+// that nothing completes.
 #include "internal.h"
 
 namespace stm {
@@ -48,4 +50,38 @@ extern "C" stm_status stm_measure_fp64_peak(double* tflops, void* stream) {
   cudaFree(out);
   *tflops = 2.0 * 8.0 * iters * (double)blocks * threads / (best * 1e-3) / 1e12;
   return STM_OK;
+}
+
+extern "C" stm_status stm_selftest_bounded_wait(int* timed_out, double* ms, void* stream) {
+  if (!timed_out || !ms) {
+    set_error("stm_selftest_bounded_wait: NULL argument");
+    return STM_ERR_INVALID_ARG;
+  }
+  int* err = nullptr;
+  STM_CUDA(cudaMalloc(&err, sizeof(int)));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  stm_status st = STM_OK;
+  int e = 0;
+  float t = 0.f;
+  if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess) {
+    set_error("stm_selftest_bounded_wait: CUDA error");
+    cudaFree(err);
+    return STM_ERR_CUDA;
+  }
+  cudaEventRecord(e0, s);
+  st = bounded_wait_selftest(err, s);
+  cudaEventRecord(e1, s);
+  if (st == STM_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess ||
+                       cudaMemcpy(&e, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)) {
+    set_error("stm_selftest_bounded_wait: CUDA error");
+    st = STM_ERR_CUDA;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(err);
+  *timed_out = (e & 128) ? 1 : 0;
+  *ms = t;
+  return st;
 }

@@ -317,6 +317,15 @@ class Hierarchy:
         return out.value
 
     @staticmethod
+    def selftest_bounded_wait(stream=None):
+        """(timed_out, ms) of the bounded-wait self-test (stm_selftest_bounded_wait)."""
+        t, ms = C.c_int(), C.c_double()
+        lib = _lib.load()
+        _lib.check(lib.stm_selftest_bounded_wait(C.byref(t), C.byref(ms), _stream(stream)),
+                   "stm_selftest_bounded_wait")
+        return bool(t.value), ms.value
+
+    @staticmethod
     def kernel_launches():
         return int(_lib.load().stm_kernel_launches())
 
