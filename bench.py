@@ -470,6 +470,7 @@ def time_precisions(wl, precs, state, rhs_lat, steps, warmup, rtol, dist=None, p
         r["launches_per_step"] = (Hierarchy.kernel_launches() - launches0) / steps
         r["iters_timed"] = info["iters"]
         r["rel_res_true_timed"] = info["rel_res_true"]
+        r["graphs_timed"] = info.get("graphs")
         if not profile:
             continue
         # profiled pass over the same steps: CUDA events around every launch of the library, recorded
@@ -517,7 +518,8 @@ def by_precision_rows(results, errs, steps):
     for p, v in results.items():
         inv, dp = split_precision(p)
         row = {"s_per_solve": v["ms_per_solve"] / 1e3, "iters": v["iters_timed"],
-               "rel_res_true": v["rel_res_true_timed"], "setup_ms": v["setup"],
+               "rel_res_true": v["rel_res_true_timed"], "vcycle_graphs": v.get("graphs_timed"),
+               "setup_ms": v["setup"],
                "fp64_residual_products": dp == "f64",
                "err_vs_fp64_solution": errs.get(p)}
         if dp != "f64":

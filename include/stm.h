@@ -169,6 +169,9 @@ typedef struct {
                             until the next solve on the same hierarchy                  */
   int n_history;       /* entries of history                                          */
   double ms_total;     /* host wall time of the call in ms (the call synchronises)    */
+  int graphs;          /* 1 if the V-cycles of this call were replayed from CUDA graphs
+                          (0 with profiling on, for the 32-column solve, or if capture
+                          was refused and the V-cycles were launched directly)          */
 } stm_solve_info;
 
 /* Right-preconditioned flexible GMRES (Sec. 3) on the finest level, preconditioned by one

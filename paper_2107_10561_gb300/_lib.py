@@ -32,7 +32,8 @@ class GmresOpts(C.Structure):
 class SolveInfo(C.Structure):
     _fields_ = [("iters", C.c_int), ("restarts", C.c_int), ("converged", C.c_int),
                 ("rel_res_true", C.c_double), ("rel_res_est", C.c_double),
-                ("history", C.POINTER(C.c_double)), ("n_history", C.c_int), ("ms_total", C.c_double)]
+                ("history", C.POINTER(C.c_double)), ("n_history", C.c_int), ("ms_total", C.c_double),
+                ("graphs", C.c_int)]
 
 
 NEWTON_MAX_STEPS = 32  # STM_NEWTON_MAX_STEPS

@@ -389,6 +389,7 @@ static stm_status gmres_core(Hierarchy& H, const double* b, double* x, const stm
   inf.rel_res_est = est;
   inf.history = H.hist.data();
   inf.n_history = (int)H.hist.size();
+  inf.graphs = (H.use_graphs && !H.prof.on) ? 1 : 0;
   if (info) *info = inf;
   if (!converged) {
     set_error(breakdown ? "FGMRES breakdown: zero column in the Hessenberg matrix before rtol was met"
@@ -880,6 +881,7 @@ stm_status stm_gmres_solve_multi(stm_hierarchy* h, int nrhs, const double* B_dev
       infos[c].rel_res_est = est[c];
       infos[c].history = H.mhist[c].data();
       infos[c].n_history = (int)H.mhist[c].size();
+      infos[c].graphs = 0;
     }
   }
   if (!all) {

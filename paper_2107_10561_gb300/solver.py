@@ -149,7 +149,7 @@ class Hierarchy:
         hist = [inf.history[i] for i in range(inf.n_history)] if inf.history and inf.n_history > 0 else []
         return dict(iters=inf.iters, restarts=inf.restarts, converged=bool(inf.converged),
                     rel_res_true=inf.rel_res_true, rel_res_est=inf.rel_res_est, history=hist,
-                    ms_total=inf.ms_total)
+                    ms_total=inf.ms_total, graphs=bool(inf.graphs))
 
     def gmres_solve(self, b, x, rtol=1e-10, restart=30, max_iter=1000, transpose=False, use_x0=False,
                     stream=None, raise_on_fail=True):

@@ -268,3 +268,16 @@ def test_single_sweep_mixed_precision(name, prec):
     dg = dev(d)
     h.vanka_sweep(g, dev(r), dg)
     assert rel_max(dg.cpu().numpy(), expect) < 1e-5
+
+
+def test_vcycles_replayed_as_graphs():
+    """A plain solve replays its V-cycles from CUDA graphs (a refused capture would fall back to direct
+    launches silently otherwise); with event profiling on they are launched directly."""
+    wl, o, h = pair("3d_k1_obs")
+    b = dev(np.random.default_rng(41).standard_normal(o.fine.N))
+    x = torch.zeros_like(b)
+    assert h.gmres_solve(b, x)["graphs"]
+    h.profile_enable(True)
+    x.zero_()
+    assert not h.gmres_solve(b, x)["graphs"]
+    h.profile_enable(False)
