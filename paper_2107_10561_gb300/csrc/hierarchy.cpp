@@ -507,6 +507,23 @@ static stm_status build_level(const stm_params& p, int g, Level& L, std::vector<
     return nn[a] != nn[b] ? nn[a] < nn[b] : ncell[a] < ncell[b];
   });
   STM_TRY(upload(&L.job_nodes, job_nodes));
+  // per colour, the nodes touched by its cells, in job order: the coloured smoother's defect needs
+  // only their velocity rows (and the pressure rows) before the local solves of that colour
+  {
+    std::vector<int> colour_jobs;
+    std::vector<char> touched(R);
+    for (int col = 0; col < (1 << d); ++col) {
+      std::fill(touched.begin(), touched.end(), 0);
+      for (int k = L.colour_off[col]; k < L.colour_off[col + 1]; ++k)
+        for (int i = 0; i < nv; ++i) touched[L.h_cell_nodes[(size_t)colour_cells[k] * nv + i]] = 1;
+      L.colour_job_off[col] = (int)colour_jobs.size();
+      for (int nd : job_nodes)
+        if (touched[nd]) colour_jobs.push_back(nd);
+    }
+    for (int col = (1 << d); col < 9; ++col) L.colour_job_off[col] = (int)colour_jobs.size();
+    if (colour_jobs.empty()) colour_jobs.push_back(0);
+    STM_TRY(upload(&L.colour_jobs, colour_jobs));
+  }
   STM_TRY(upload(&L.idx, idx));
   STM_TRY(upload(&L.cell_nodes, L.h_cell_nodes));
   STM_TRY(upload(&L.cell_xyz, L.h_cell_xyz));
@@ -757,7 +774,7 @@ void free_hierarchy(Hierarchy& H) {
                     L.node_cells, L.job_nodes, L.nbase, L.spmv_work, L.nval, L.pvalT, L.nvalJT, L.pvalJT, L.nval32, L.pval32,
                     L.nvalJT32, L.pvalJT32, L.x32,
                     L.colidx, L.val, L.valT, L.ref, L.inj, L.wnod, L.inv, L.wmult, L.own_ptr,
-                    L.own_pos, L.last_owner, L.colour_cells, L.Y, L.P_rowptr, L.P_col, L.P_val,
+                    L.own_pos, L.last_owner, L.colour_cells, L.colour_jobs, L.Y, L.P_rowptr, L.P_col, L.P_val,
                     L.Rt_rowptr, L.Rt_col, L.Rt_val, L.tv_ptr, L.tv_node, L.tv_w, L.tc_ptr, L.tc_node,
                     L.tc_w, L.cparent, L.cbits, L.cchildren, L.d, L.r, L.t, L.md, L.mr, L.mt, L.mY, L.mt16};
     for (void* q : ptrs)

@@ -207,6 +207,8 @@ struct Level {
   int* last_owner = nullptr;      // [N] flat position of the highest-index owning cell
   int* colour_cells = nullptr;    // cells sorted by colour
   int colour_off[9] = {0};
+  int* colour_jobs = nullptr;     // per colour, the nodes its cells touch, in job_nodes order
+  int colour_job_off[9] = {0};
   double* Y = nullptr;            // [C][n] per-cell local corrections (scratch)
 
   // transfer from level g-1 (coarse) to this level: P [N x N_c], P^T [N_c x N]
@@ -324,7 +326,8 @@ stm_status transfer_restrict(const Level& F, const Level& Cl, const double* fine
 stm_status transfer_prolong_add(const Level& F, const Level& Cl, const double* coarse, double* fine, cudaStream_t s,
                                 float* fine32 = nullptr);
 stm_status spmv_nodeblock(const Level& L, const double* nval, const double* pvalT, const double* x, const double* b,
-                          double* y, int mode, cudaStream_t s);
+                          double* y, int mode, cudaStream_t s,
+                          const int* jobs = nullptr, int njobs = -1);
 stm_status build_nodeblock(Level& L, cudaStream_t s);
 // node-block and warp-transposed pressure-row copies of any value array on J's pattern (J or J^T)
 stm_status build_nodeblock_from(const Level& L, const double* val, double* nval, double* pvalT, cudaStream_t s);
@@ -337,6 +340,10 @@ stm_status defect_f32(Hierarchy& H, int g, int transpose, const double* x, const
 stm_status build_values_f32(Level& L, int transpose, cudaStream_t s);
 stm_status jacobian_apply(Hierarchy& H, int g, const double* x, const double* b, double* y,
                           int mode, int transpose, cudaStream_t s);
+// y = b - J_g x (or J_g^T) in FP64 on the velocity rows of the nodes that the cells of one colour
+// touch and on every pressure row; the other rows of y are left as they are
+stm_status jacobian_defect_colour(Hierarchy& H, int g, int colour, const double* x, const double* b, double* y,
+                                  int transpose, cudaStream_t s);
 // the V-cycle's defect y = b - J_g x (or J_g^T): over the FP32 copies with defect_precision =
 // STM_F32, else jacobian_apply in FP64
 stm_status smoother_defect(Hierarchy& H, int g, const double* x, const double* b, double* y, int transpose,

@@ -126,6 +126,16 @@ stm_status jacobian_apply(Hierarchy& H, int g, const double* x, const double* b,
   return spmv_nodeblock(L, L.nvalJT, L.pvalJT, x, b, y, mode, s);
 }
 
+stm_status jacobian_defect_colour(Hierarchy& H, int g, int colour, const double* x, const double* b, double* y,
+                                  int transpose, cudaStream_t s) {
+  Level& L = H.L[g];
+  if (transpose) STM_TRY(ensure_transpose(H, g, s));
+  const int j0 = L.colour_job_off[colour], nj = L.colour_job_off[colour + 1] - j0;
+  ProfScope ps(&H, STM_KCLASS_JACOBIAN_SPMV, s, 8.0 * (double)L.nnz * nj / std::max(L.R, 1) + 24.0 * (double)L.N, g);
+  return spmv_nodeblock(L, transpose ? L.nvalJT : L.nval, transpose ? L.pvalJT : L.pvalT, x, b, y, 1, s,
+                        L.colour_jobs + j0, nj);
+}
+
 // The outer solver is flexible GMRES (Sec. 3): it keeps every preconditioned vector z_j = V(v_j), so
 // the V-cycle need not be an exact fixed linear map. With defect_precision = STM_F32 the V-cycle's
 // defects run over FP32 copies of J_g: half the bytes and no FP64 arithmetic, with rounding (about

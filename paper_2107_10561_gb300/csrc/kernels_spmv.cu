@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(256) k_spmv_nb_dyn(
     const int* __restrict__ nbr_ptr, const int* __restrict__ nbr, const int* __restrict__ ncell,
     const int* __restrict__ node_cells, const int* __restrict__ cell_nodes, const int* __restrict__ job_nodes,
     long long block, int R, int C, const double* __restrict__ x, const double* __restrict__ b,
-    double* __restrict__ y, int mode, unsigned* __restrict__ work, unsigned nvu, unsigned ntot) {
+    double* __restrict__ y, int mode, unsigned* __restrict__ work, unsigned nvu, unsigned ntot, int njobs) {
   constexpr int GPW = 32 / VL;
   constexpr int KD = K * D;
   constexpr int NP = D + 1;
@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(256) k_spmv_nb_dyn(
     if (u >= ntot) break;
     if (u < nvu) {
       const long long job = (long long)(nvu - 1 - u) * GPW + gw;
-      const bool ok = job < R;
+      const bool ok = job < njobs;
       const int i = ok ? job_nodes[job] : 0;
       double acc[NAV];
 #pragma unroll
@@ -536,7 +536,7 @@ static stm_status spmv_nodeblock_t(const Level& L, const TV* nval, const TV* pva
 
 template <int VL, int K, int D, int U>
 static stm_status launch_nb_dyn(const Level& L, const double* nval, const double* pvalT, const double* x,
-                                const double* b, double* y, int mode, cudaStream_t s) {
+                                const double* b, double* y, int mode, cudaStream_t s, const int* jobs, int njobs) {
   constexpr int GPW = 32 / VL;
   static int occ = 0;  // resident CTAs per SM of this instantiation
   if (!occ) {
@@ -544,43 +544,47 @@ static stm_status launch_nb_dyn(const Level& L, const double* nval, const double
     if (occ < 1) occ = 1;
   }
   const long long npr = (long long)K * L.C * (D + 1);
-  const unsigned nvu = (unsigned)((L.R + GPW - 1) / GPW);
+  const unsigned nvu = (unsigned)((njobs + GPW - 1) / GPW);
   const unsigned ntot = nvu + (unsigned)((npr + 31) / 32);
   const int blocks = (int)std::max<long long>(1, std::min<long long>((long long)occ * sms_count(), (ntot + 7) / 8));
   k_spmv_nb_dyn<VL, K, D, U><<<blocks, 256, 0, s>>>(nval, pvalT, L.nbase, L.nbr_ptr, L.nbr, L.ncell, L.node_cells,
-                                                 L.cell_nodes, L.job_nodes, L.block, L.R, L.C, x, b, y, mode,
-                                                 L.spmv_work, nvu, ntot);
+                                                 L.cell_nodes, jobs, L.block, L.R, L.C, x, b, y, mode,
+                                                 L.spmv_work, nvu, ntot, njobs);
   note_launch();
   STM_CUDA(cudaGetLastError());
   return STM_OK;
 }
 
 stm_status spmv_nodeblock(const Level& L, const double* nval, const double* pvalT, const double* x, const double* b,
-                          double* y, int mode, cudaStream_t s) {
+                          double* y, int mode, cudaStream_t s, const int* jobs, int njobs) {
+  if (!jobs) {
+    jobs = L.job_nodes;
+    njobs = L.R;
+  }
   // lanes per node as for the static product: short groups on large levels, 16 / 32 on small ones
   const long long per_sm_threads = 1024;
   int cls = 0;
   if ((long long)L.R * (L.dim == 2 ? 4 : 8) < (long long)sms_count() * per_sm_threads) cls = 100;
   if ((long long)L.R * 16 < (long long)sms_count() * per_sm_threads / 4) cls = 200;
   switch (L.dim * 10 + L.K + cls) {
-    case 21: return launch_nb_dyn<4, 1, 2, 1>(L, nval, pvalT, x, b, y, mode, s);
-    case 22: return launch_nb_dyn<4, 2, 2, 1>(L, nval, pvalT, x, b, y, mode, s);
-    case 23: return launch_nb_dyn<4, 3, 2, 1>(L, nval, pvalT, x, b, y, mode, s);
-    case 31: return launch_nb_dyn<8, 1, 3, 1>(L, nval, pvalT, x, b, y, mode, s);
-    case 32: return launch_nb_dyn<8, 2, 3, 1>(L, nval, pvalT, x, b, y, mode, s);
-    case 33: return launch_nb_dyn<8, 3, 3, 1>(L, nval, pvalT, x, b, y, mode, s);
-    case 121: return launch_nb_dyn<16, 1, 2, 1>(L, nval, pvalT, x, b, y, mode, s);
-    case 122: return launch_nb_dyn<16, 2, 2, 1>(L, nval, pvalT, x, b, y, mode, s);
-    case 123: return launch_nb_dyn<16, 3, 2, 1>(L, nval, pvalT, x, b, y, mode, s);
-    case 131: return launch_nb_dyn<16, 1, 3, 1>(L, nval, pvalT, x, b, y, mode, s);
-    case 132: return launch_nb_dyn<16, 2, 3, 1>(L, nval, pvalT, x, b, y, mode, s);
-    case 133: return launch_nb_dyn<16, 3, 3, 1>(L, nval, pvalT, x, b, y, mode, s);
-    case 221: return launch_nb_dyn<32, 1, 2, 1>(L, nval, pvalT, x, b, y, mode, s);
-    case 222: return launch_nb_dyn<32, 2, 2, 1>(L, nval, pvalT, x, b, y, mode, s);
-    case 223: return launch_nb_dyn<32, 3, 2, 1>(L, nval, pvalT, x, b, y, mode, s);
-    case 231: return launch_nb_dyn<32, 1, 3, 1>(L, nval, pvalT, x, b, y, mode, s);
-    case 232: return launch_nb_dyn<32, 2, 3, 1>(L, nval, pvalT, x, b, y, mode, s);
-    case 233: return launch_nb_dyn<32, 3, 3, 1>(L, nval, pvalT, x, b, y, mode, s);
+    case 21: return launch_nb_dyn<4, 1, 2, 1>(L, nval, pvalT, x, b, y, mode, s, jobs, njobs);
+    case 22: return launch_nb_dyn<4, 2, 2, 1>(L, nval, pvalT, x, b, y, mode, s, jobs, njobs);
+    case 23: return launch_nb_dyn<4, 3, 2, 1>(L, nval, pvalT, x, b, y, mode, s, jobs, njobs);
+    case 31: return launch_nb_dyn<8, 1, 3, 1>(L, nval, pvalT, x, b, y, mode, s, jobs, njobs);
+    case 32: return launch_nb_dyn<8, 2, 3, 1>(L, nval, pvalT, x, b, y, mode, s, jobs, njobs);
+    case 33: return launch_nb_dyn<8, 3, 3, 1>(L, nval, pvalT, x, b, y, mode, s, jobs, njobs);
+    case 121: return launch_nb_dyn<16, 1, 2, 1>(L, nval, pvalT, x, b, y, mode, s, jobs, njobs);
+    case 122: return launch_nb_dyn<16, 2, 2, 1>(L, nval, pvalT, x, b, y, mode, s, jobs, njobs);
+    case 123: return launch_nb_dyn<16, 3, 2, 1>(L, nval, pvalT, x, b, y, mode, s, jobs, njobs);
+    case 131: return launch_nb_dyn<16, 1, 3, 1>(L, nval, pvalT, x, b, y, mode, s, jobs, njobs);
+    case 132: return launch_nb_dyn<16, 2, 3, 1>(L, nval, pvalT, x, b, y, mode, s, jobs, njobs);
+    case 133: return launch_nb_dyn<16, 3, 3, 1>(L, nval, pvalT, x, b, y, mode, s, jobs, njobs);
+    case 221: return launch_nb_dyn<32, 1, 2, 1>(L, nval, pvalT, x, b, y, mode, s, jobs, njobs);
+    case 222: return launch_nb_dyn<32, 2, 2, 1>(L, nval, pvalT, x, b, y, mode, s, jobs, njobs);
+    case 223: return launch_nb_dyn<32, 3, 2, 1>(L, nval, pvalT, x, b, y, mode, s, jobs, njobs);
+    case 231: return launch_nb_dyn<32, 1, 3, 1>(L, nval, pvalT, x, b, y, mode, s, jobs, njobs);
+    case 232: return launch_nb_dyn<32, 2, 3, 1>(L, nval, pvalT, x, b, y, mode, s, jobs, njobs);
+    case 233: return launch_nb_dyn<32, 3, 3, 1>(L, nval, pvalT, x, b, y, mode, s, jobs, njobs);
     default:
       set_error("node-block SpMV: unsupported (dim, k)");
       return STM_ERR_INVALID_ARG;

@@ -473,7 +473,10 @@ stm_status vanka_step(Hierarchy& H, int g, const double* r, double* d, int trans
       const int nc = L.colour_off[col + 1] - L.colour_off[col];
       const double* t = r;
       if (!(d_is_zero && col == 0)) {
-        stm_status st = smoother_defect(H, g, d, r, L.t, transpose, s);
+        // the colour's local solves read t only at the DoFs of its cells: with FP64 defects only
+        // those velocity rows (and the pressure rows) are formed
+        stm_status st = H.p.defect_precision == STM_F32 ? smoother_defect(H, g, d, r, L.t, transpose, s)
+                                                         : jacobian_defect_colour(H, g, col, d, r, L.t, transpose, s);
         if (st != STM_OK) return st;
         t = L.t;
       }
